@@ -1,0 +1,423 @@
+"""Plain CPU oracle of MRCQR (Algorithm 2 of "Numerically Stable Cholesky-QR on
+GPU via Mixed-Precision Randomized Preconditioning", Garrison, Chen, Ipsen).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this module; only
+``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference
+legs of ``bench.py`` use it.  It shares no code, tables or constants with the
+CUDA path: every step is written out again here from its definition, slowly
+and in FP64 (numpy), so that it can be read against the paper.
+
+Steps, in the paper's order and notation:
+
+* Algorithm 2 step 1 (Sec. II-A): Rademacher signs D and c sampled row indices
+  S.  The paper leaves the random generator open; here both come from
+  Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from that
+  paper's round function and constants:
+    d_i = 1 - 2 * (Philox(key=seed, ctr=(i, 0, 0, 0)).word0 & 1)
+    S   = Floyd's sampling of c distinct values of {0..m-1}, the draw for
+          j in [m-c, m) being r = (Philox(key=seed, ctr=(j, 1, 0, 0)).word0
+          * (j + 1)) >> 32, sorted ascending.
+* Algorithm 2 steps 2-4 (DiagMult, transform, Select; Sec. II-A): the sketch
+  Y = sqrt(m/c) * P F D A with F the orthonormal DCT-II
+    F_kj = sqrt(2/m) * c_k * cos(pi * k * (2j + 1) / (2m)),
+    c_0 = 1/sqrt(2), c_k = 1 otherwise,
+  built here as an explicit dense matrix, row by row, with the phase reduced
+  exactly as an integer r = k (2j + 1) mod 4m.  (The paper's transform is the
+  real part of a column-wise real FFT with scale sqrt(c/m); the orthonormal
+  DCT-II with scale sqrt(m/c) is the reading used by this project.  A scalar
+  scale of the sketch cancels in R_s^{-1} ... R, see ``mrcqr``.)
+* Algorithm 2 step 5 (SketchQR): Householder QR of Y, normalised to
+  diag(R_s) > 0.
+* Algorithm 2 steps 6-8 (Stage 2, Algorithm 1 on A R_s^{-1}, Sec. II-A):
+  W = A R_s^{-1} by substitution, G = W^T W, Cholesky G = R_c^T R_c,
+  Q = W R_c^{-1} by substitution.
+* Algorithm 2 step 9: R = R_c R_s.
+* Checks (Eq. 1, Fig. 1): ||I - Q^T Q|| and ||A - QR|| / ||A|| with the sums
+  in double-double (``ddcheck.c``), Theorem 1's bound and the CholQR probe
+  bound (Sec. II-C).
+
+Reduced-precision sketches (Sec. II-B) are emulated by rounding the
+sign-flipped input and the transform entries to the sketch precision's
+significand before an FP64 product: an error model of fl_p, used only to
+separate rounding error from defects.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+U_FP64 = 2.0 ** -53
+# unit roundoff of the sketch precisions (round to nearest)
+UNIT_ROUNDOFF = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8, "fp32": 2.0 ** -24, "fp64": 2.0 ** -53}
+SIGNIFICAND_BITS = {"fp16": 11, "bf16": 8, "fp32": 24, "fp64": 53}
+PRECISIONS = ("fp16", "bf16", "fp32", "fp64")
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11, Sec. 4 "Philox"): 10 rounds of the
+# 4x32 round function with multipliers M0, M1 and Weyl key increments W0, W1.
+_M0 = 0xD2511F53
+_M1 = 0xCD9E8D57
+_W0 = 0x9E3779B9
+_W1 = 0xBB67AE85
+_MASK32 = 0xFFFFFFFF
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox4x32-10 of counter (c0, c1, c2, c3) under key (k0, k1).
+
+    Inputs are scalars or uint arrays (broadcast); returns four uint32 arrays.
+    Each round: (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2 as 64-bit
+    products, then c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); the key is
+    bumped by (W0, W1) between rounds."""
+    c0 = np.asarray(c0, dtype=np.uint64) & _MASK32
+    c1 = np.asarray(c1, dtype=np.uint64) & _MASK32
+    c2 = np.asarray(c2, dtype=np.uint64) & _MASK32
+    c3 = np.asarray(c3, dtype=np.uint64) & _MASK32
+    c0, c1, c2, c3 = np.broadcast_arrays(c0, c1, c2, c3)
+    k0 = int(k0) & _MASK32
+    k1 = int(k1) & _MASK32
+    m0 = np.uint64(_M0)
+    m1 = np.uint64(_M1)
+    sh = np.uint64(32)
+    msk = np.uint64(_MASK32)
+    for rnd in range(10):
+        if rnd > 0:
+            k0 = (k0 + _W0) & _MASK32
+            k1 = (k1 + _W1) & _MASK32
+        p0 = m0 * c0
+        p1 = m1 * c2
+        hi0, lo0 = p0 >> sh, p0 & msk
+        hi1, lo1 = p1 >> sh, p1 & msk
+        c0, c1, c2, c3 = (hi1 ^ c1 ^ np.uint64(k0), lo1, hi0 ^ c3 ^ np.uint64(k1), lo0)
+    return (c0.astype(np.uint32), c1.astype(np.uint32), c2.astype(np.uint32), c3.astype(np.uint32))
+
+
+def seed_key(seed: int):
+    """The 64-bit sketch seed as the Philox key (low word, high word)."""
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    return seed & _MASK32, seed >> 32
+
+
+def rademacher(m: int, seed: int) -> np.ndarray:
+    """Diagonal of D (Algorithm 2 step 1): d_i in {+1, -1}, i < m."""
+    k0, k1 = seed_key(seed)
+    w0, _, _, _ = philox4x32_10(np.arange(m, dtype=np.uint64), 0, 0, 0, k0, k1)
+    return 1.0 - 2.0 * (w0 & 1).astype(np.float64)
+
+
+def sample_rows(m: int, s: int, seed: int) -> np.ndarray:
+    """The sample set S (Algorithm 2 step 1): s distinct row indices of the
+    transformed matrix, uniform without replacement (Floyd's algorithm),
+    sorted ascending.  Pure-Python loop: s is at most a few thousand."""
+    if not (0 < s <= m):
+        raise ValueError("need 0 < s <= m")
+    k0, k1 = seed_key(seed)
+    js = np.arange(m - s, m, dtype=np.uint64)
+    u, _, _, _ = philox4x32_10(js, 1, 0, 0, k0, k1)
+    chosen = set()
+    for j, uj in zip(js.tolist(), u.tolist()):
+        r = (uj * (j + 1)) >> 32          # uniform on {0, ..., j}
+        chosen.add(j if r in chosen else r)
+    return np.array(sorted(chosen), dtype=np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Orthonormal DCT-II and the dense sketch operator (Algorithm 2 steps 2-4)
+
+def dct_coefficient(k: int, m: int) -> float:
+    return math.sqrt(2.0 / m) * (1.0 / math.sqrt(2.0) if k == 0 else 1.0)
+
+
+def dct_row(k: int, m: int) -> np.ndarray:
+    """Row k of the orthonormal DCT-II matrix F (length m)."""
+    j = np.arange(m, dtype=np.int64)
+    r = (np.int64(k) * (2 * j + 1)) % (4 * m)           # exact integer phase
+    return dct_coefficient(k, m) * np.cos(np.pi * r.astype(np.float64) / (2.0 * m))
+
+
+def dct_matrix(m: int) -> np.ndarray:
+    return np.stack([dct_row(k, m) for k in range(m)])
+
+
+def sketch_row(k: int, m: int, s: int, signs: np.ndarray) -> np.ndarray:
+    """One row of S = sqrt(m/s) P F D: sqrt(m/s) * F[k, :] * d."""
+    return math.sqrt(m / s) * dct_row(k, m) * signs
+
+
+def sketch(A: np.ndarray, idx: np.ndarray, signs: np.ndarray, rows_per_block: int = 16) -> np.ndarray:
+    """Y = S A in FP64.  S is built explicitly row by row; each block of rows
+    is applied with one matrix product."""
+    m, n = A.shape
+    s = len(idx)
+    Y = np.empty((s, n))
+    for b in range(0, s, rows_per_block):
+        ks = idx[b:b + rows_per_block]
+        Sb = np.stack([sketch_row(int(k), m, s, signs) for k in ks])
+        Y[b:b + len(ks)] = Sb @ A
+    return Y
+
+
+def round_significand(x: np.ndarray, bits: int) -> np.ndarray:
+    """Round FP64 values to ``bits`` significand bits, round-to-nearest-even,
+    directly from the FP64 bit pattern (no intermediate rounding).  The
+    exponent range of the target format is not modelled: callers scale the
+    values into its normal range first."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if bits >= 53:
+        return x.copy()
+    drop = np.uint64(53 - bits)
+    b = x.view(np.uint64)
+    one = np.uint64(1)
+    half = one << (drop - one)
+    lsb = (b >> drop) & one
+    r = ((b + (half - one) + lsb) >> drop) << drop
+    out = r.view(np.float64).copy()
+    out[~np.isfinite(x)] = x[~np.isfinite(x)]
+    out[x == 0] = x[x == 0]
+    return out
+
+
+def column_scale_exponents(A: np.ndarray, target_exp: int = 13) -> np.ndarray:
+    """Per-column power-of-two exponents e_j with max_i |a_ij| 2^e_j in
+    [2^target_exp, 2^(target_exp+1)); zero columns get e_j = 0.  (Keeps the
+    FP16 sketch clear of underflow, the breakdown mode named in Fig. 1.)"""
+    amax = np.max(np.abs(A), axis=0)
+    e = np.zeros(A.shape[1], dtype=np.int64)
+    nz = amax > 0
+    _, ex = np.frexp(amax[nz])               # amax = f * 2^ex, f in [0.5, 1)
+    e[nz] = target_exp + 1 - ex
+    return e
+
+
+def sketch_emulated(A: np.ndarray, idx: np.ndarray, signs: np.ndarray, prec: str) -> np.ndarray:
+    """Error model of the precision-p sketch: fl_p(D A 2^e) and fl_p(S entries),
+    products and sums exact-ish in FP64, then the scale 2^-e undone."""
+    bits = SIGNIFICAND_BITS[prec]
+    m, n = A.shape
+    s = len(idx)
+    e = column_scale_exponents(A)
+    X = round_significand(signs[:, None] * np.ldexp(A, e[None, :]), bits).reshape(m, n)
+    c = math.sqrt(m / s)
+    Y = np.empty((s, n))
+    for i, k in enumerate(idx):
+        row = round_significand(dct_row(int(k), m), bits)
+        Y[i] = c * (row @ X)
+    return np.ldexp(Y, -e[None, :])
+
+
+# ---------------------------------------------------------------------------
+# Small dense factorizations (Algorithm 1 and Algorithm 2 steps 5-9)
+
+def householder_qr(Y: np.ndarray, want_q: bool = False, dtype=np.float64):
+    """Thin QR of Y (c x n, c >= n) by Householder reflections, R normalised
+    to a positive diagonal (rows of R, columns of Q flipped)."""
+    R = np.array(Y, dtype=dtype, copy=True)
+    c, n = R.shape
+    vs = []
+    for j in range(n):
+        x = R[j:, j].copy()
+        normx = np.sqrt(np.dot(x, x))
+        v = x
+        if normx == 0:
+            vs.append(None)
+            continue
+        alpha = -normx if x[0] >= 0 else normx
+        v[0] = x[0] - alpha
+        vnorm = np.sqrt(np.dot(v, v))
+        if vnorm == 0:
+            vs.append(None)
+            continue
+        v = v / vnorm
+        R[j:, j:] -= dtype(2) * np.outer(v, v @ R[j:, j:])
+        vs.append(v)
+    Rn = np.triu(R[:n, :]).astype(np.float64)
+    sgn = np.where(np.diag(Rn) < 0, -1.0, 1.0)
+    Rn = Rn * sgn[:, None]
+    if not want_q:
+        return Rn
+    Q = np.zeros((c, n))
+    Q[:n, :n] = np.eye(n)
+    for j in reversed(range(n)):
+        v = vs[j]
+        if v is None:
+            continue
+        v = v.astype(np.float64)
+        Q[j:, :] -= 2.0 * np.outer(v, v @ Q[j:, :])
+    return Q * sgn[None, :], Rn
+
+
+def trsm_right_upper(A: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """W with W R = A (R upper triangular) by substitution: for each row a of
+    A, w_j = (a_j - sum_{k<j} w_k R_kj) / R_jj, all rows at once."""
+    m, n = A.shape
+    W = np.empty((m, n))
+    for j in range(n):
+        acc = A[:, j] - W[:, :j] @ R[:j, j] if j else A[:, j].copy()
+        W[:, j] = acc / R[j, j]
+    return W
+
+
+class CholeskyBreakdown(ArithmeticError):
+    pass
+
+
+def cholesky_upper(G: np.ndarray) -> np.ndarray:
+    """Upper R with R^T R = G (Algorithm 1 step 2), column by column.
+    Raises CholeskyBreakdown on a non-positive or non-finite pivot."""
+    n = G.shape[0]
+    R = np.zeros((n, n))
+    for j in range(n):
+        d = G[j, j] - np.dot(R[:j, j], R[:j, j])
+        if not (d > 0) or not np.isfinite(d):
+            raise CholeskyBreakdown(f"pivot {j}: {d}")
+        R[j, j] = math.sqrt(d)
+        for i in range(j + 1, n):
+            R[j, i] = (G[j, i] - np.dot(R[:j, j], R[:j, i])) / R[j, j]
+    return R
+
+
+def cholqr(A: np.ndarray):
+    """Algorithm 1: G = A^T A, G = R^T R, Q = A R^{-1}."""
+    G = A.T @ A
+    R = cholesky_upper(G)
+    Q = trsm_right_upper(A, R)
+    return Q, R
+
+
+@dataclass
+class MRCQRResult:
+    Q: np.ndarray
+    R: np.ndarray
+    Rs: np.ndarray
+    Rc: np.ndarray
+    Y: np.ndarray
+    idx: np.ndarray
+    signs: np.ndarray
+    extra: dict = field(default_factory=dict)
+
+
+def sketch_rows_for(n: int, s_factor: int = 2) -> int:
+    return s_factor * n
+
+
+def mrcqr(A: np.ndarray, seed: int = 0, prec: str = "fp64", s: int | None = None,
+          sketch_scale: float = 1.0) -> MRCQRResult:
+    """Algorithm 2 with sketch precision ``prec`` (fp64: the exact FP64 sketch;
+    otherwise the fl_p error model of ``sketch_emulated`` and a sketch QR in
+    FP32 as the paper does for half precision, Sec. II-A)."""
+    m, n = A.shape
+    if s is None:
+        s = sketch_rows_for(n)
+    signs = rademacher(m, seed)
+    idx = sample_rows(m, s, seed)
+    if prec == "fp64":
+        Y = sketch(A, idx, signs)
+        Rs = householder_qr(Y * sketch_scale)
+    else:
+        Y = sketch_emulated(A, idx, signs, prec)
+        Rs = householder_qr((Y * sketch_scale).astype(np.float32), dtype=np.float32)
+    W = trsm_right_upper(A, Rs)
+    G = W.T @ W
+    Rc = cholesky_upper(G)
+    Q = trsm_right_upper(W, Rc)
+    R = Rc @ Rs
+    return MRCQRResult(Q=Q, R=np.triu(R), Rs=Rs, Rc=Rc, Y=Y, idx=idx, signs=signs)
+
+
+def precision_rule(kappa: float) -> str:
+    """Sketch precision from the regime of kappa_2(A) (Sec. II-B/II-C):
+    half up to 1e4, single up to 1e8, double above (boundaries inclusive)."""
+    if kappa <= 1e4:
+        return "fp16"
+    if kappa <= 1e8:
+        return "fp32"
+    return "fp64"
+
+
+def theorem1_bound(kappa_A1: float, eps: float, kappa_Rs: float) -> float:
+    """Theorem 1: kappa(A (R_s + E)^{-1}) <= kappa(A R_s^{-1}) (1 + eps k)/(1 - eps k)
+    with eps = ||E||_2 / ||R_s||_2 and k = kappa_2(R_s); needs eps k < 1."""
+    t = eps * kappa_Rs
+    if t >= 1:
+        return math.inf
+    return kappa_A1 * (1 + t) / (1 - t)
+
+
+def probe_kappa_lower(q: float, u: float = U_FP64) -> float:
+    """CholQR probe (Sec. II-C): kappa_2(A) >= sqrt(q / (u (1 + q))) with
+    q = ||I - Q^T Q||_2 of a CholQR run."""
+    return math.sqrt(q / (u * (1.0 + q)))
+
+
+def cond2(A: np.ndarray) -> float:
+    sv = np.linalg.svd(A, compute_uv=False)
+    return float(sv[0] / sv[-1])
+
+
+# ---------------------------------------------------------------------------
+# Double-double checks (compiled C, see ddcheck.c)
+
+_DD = None
+
+
+def _dd_lib():
+    global _DD
+    if _DD is None:
+        here = os.path.dirname(os.path.abspath(__file__))
+        path = os.path.join(here, "libddcheck.so")
+        if not os.path.exists(path):
+            from . import build as _b
+            _b.build_oracle()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64 = ctypes.c_int64
+        lib.dd_gram_minus_identity.argtypes = [i64, i64, dp, i64, dp]
+        lib.dd_gram_minus_identity.restype = None
+        lib.dd_residual_columns.argtypes = [i64, i64, dp, i64, dp, i64, dp, i64, dp]
+        lib.dd_residual_columns.restype = None
+        lib.dd_dot.argtypes = [i64, dp, dp]
+        lib.dd_dot.restype = ctypes.c_double
+        _DD = lib
+    return _DD
+
+
+def _f64_fortran(X):
+    return np.asfortranarray(X, dtype=np.float64)
+
+
+def _ptr(X):
+    return X.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def orthogonality_error(Q: np.ndarray):
+    """(||I - Q^T Q||_2, ||I - Q^T Q||_F) with Q^T Q - I summed in
+    double-double (Dot2 of Ogita, Rump, Oishi 2005) and rounded once."""
+    Q = _f64_fortran(Q)
+    m, n = Q.shape
+    E = np.zeros((n, n), order="F")
+    _dd_lib().dd_gram_minus_identity(m, n, _ptr(Q), m, _ptr(E))
+    return float(np.linalg.norm(E, 2)), float(np.linalg.norm(E, "fro")), E
+
+
+def residual_error(A: np.ndarray, Q: np.ndarray, R: np.ndarray):
+    """(||A - QR||_F / ||A||_F, ||A - QR||_2 / ||A||_2) with each entry of
+    A - QR accumulated in double-double (R upper triangular)."""
+    A = _f64_fortran(A)
+    Q = _f64_fortran(Q)
+    R = _f64_fortran(np.triu(R))
+    m, n = A.shape
+    Rres = np.zeros((m, n), order="F")
+    _dd_lib().dd_residual_columns(m, n, _ptr(A), m, _ptr(Q), m, _ptr(R), n, _ptr(Rres))
+    fro = float(np.linalg.norm(Rres) / np.linalg.norm(A))
+    two = float(np.linalg.norm(Rres, 2) / np.linalg.norm(A, 2))
+    return fro, two
+
+
+def dd_dot(x: np.ndarray, y: np.ndarray) -> float:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return float(_dd_lib().dd_dot(len(x), _ptr(x), _ptr(y)))

@@ -1,0 +1,351 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix
+(no GPU).  Each test names the passage it follows."""
+from __future__ import annotations
+
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.fft
+import scipy.linalg
+
+import oracle as O
+from paper_2606_18411_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --- Algorithm 2 step 1: random signs and sample set (Philox, Floyd) ---------
+
+def test_philox_known_answers():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox4x32_10(v[0], v[1], v[2], v[3], v[4], v[5])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_philox_vectorised_matches_scalar():
+    ctr = np.arange(1000, 1016, dtype=np.uint64)
+    vec = O.philox4x32_10(ctr, 7, 0, 3, 0x12345678, 0x9abcdef0)
+    for i, c in enumerate(ctr.tolist()):
+        sc = O.philox4x32_10(c, 7, 0, 3, 0x12345678, 0x9abcdef0)
+        assert [int(x[i]) for x in vec] == [int(x) for x in sc]
+
+
+@pytest.mark.parametrize("m", [1, 7, 4096, 1 << 16])
+def test_rademacher_signs(m):
+    d = O.rademacher(m, seed=11)
+    assert d.shape == (m,)
+    assert set(np.unique(d).tolist()) <= {-1.0, 1.0}
+    assert abs(d.sum()) <= 5 * math.sqrt(m) + 1
+    # different seeds give different sign vectors
+    if m >= 64:
+        assert not np.array_equal(d, O.rademacher(m, seed=12))
+
+
+@pytest.mark.parametrize("m,s", [(1, 1), (5, 5), (64, 64), (4096, 64), (1 << 20, 256), (3001, 2048)])
+def test_sample_rows_valid(m, s):
+    idx = O.sample_rows(m, s, seed=3)
+    assert idx.shape == (s,)
+    assert np.all(np.diff(idx) > 0)          # sorted, distinct
+    assert idx[0] >= 0 and idx[-1] < m
+    if s == m:
+        assert np.array_equal(idx, np.arange(m))
+
+
+def test_sample_rows_uniform_subsets():
+    # Floyd's algorithm draws every s-subset with probability 1/C(m,s).
+    m, s, trials = 5, 2, 6000
+    counts = {}
+    for seed in range(trials):
+        key = tuple(O.sample_rows(m, s, seed).tolist())
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == math.comb(m, s)
+    exp = trials / math.comb(m, s)
+    chi2 = sum((c - exp) ** 2 / exp for c in counts.values())
+    assert chi2 < 30.0          # 9 dof; p ~ 4e-4
+
+
+def test_sample_rows_deterministic():
+    assert np.array_equal(O.sample_rows(10000, 100, 5), O.sample_rows(10000, 100, 5))
+    assert not np.array_equal(O.sample_rows(10000, 100, 5), O.sample_rows(10000, 100, 6))
+
+
+# --- Algorithm 2 steps 2-4: the orthonormal DCT-II sketch ---------------------
+
+@pytest.mark.parametrize("m", [8, 64, 256, 300])
+def test_dct_matches_library_and_is_orthonormal(m):
+    F = O.dct_matrix(m)
+    np.testing.assert_allclose(F @ F.T, np.eye(m), atol=1e-13)
+    x = inputs.gaussian(m, 3, seed=m)
+    ref = scipy.fft.dct(x, type=2, norm="ortho", axis=0)
+    np.testing.assert_allclose(F @ x, ref, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("m,n", [(256, 8), (300, 5), (1024, 16)])
+def test_sketch_equals_fast_transform(m, n):
+    # Y = sqrt(m/s) P F D A, computed independently with scipy's DCT
+    s = 2 * n
+    A = inputs.gaussian(m, n, seed=1)
+    d = O.rademacher(m, 9)
+    idx = O.sample_rows(m, s, 9)
+    Y = O.sketch(A, idx, d)
+    ref = math.sqrt(m / s) * scipy.fft.dct(d[:, None] * A, type=2, norm="ortho", axis=0)[idx]
+    np.testing.assert_allclose(Y, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_sketch_full_sample_preserves_gram():
+    # with s = m and every row sampled, S^T S = (m/s) I = I: Y^T Y = A^T A
+    m, n = 128, 6
+    A = inputs.gaussian(m, n, seed=2)
+    Y = O.sketch(A, O.sample_rows(m, m, 1), O.rademacher(m, 1))
+    np.testing.assert_allclose(Y.T @ Y, A.T @ A, atol=1e-12)
+
+
+# --- fl_p: rounding to the sketch precision (Algorithm 2 step 2) --------------
+
+def test_round_significand_fp16_fp32_match_casts():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(20000) * np.exp2(rng.integers(-10, 12, 20000))
+    x = x[(np.abs(x) >= 2.0 ** -14) & (np.abs(x) <= 65504.0)]   # FP16 normal range
+    np.testing.assert_array_equal(O.round_significand(x, 11), x.astype(np.float16).astype(np.float64))
+    y = rng.standard_normal(20000) * np.exp2(rng.integers(-100, 100, 20000))
+    np.testing.assert_array_equal(O.round_significand(y, 24), y.astype(np.float32).astype(np.float64))
+
+
+def test_round_significand_bf16_matches_torch_on_fp32_values():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    x = (rng.standard_normal(20000) * np.exp2(rng.integers(-30, 30, 20000))).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(O.round_significand(x.astype(np.float64), 8), ref)
+
+
+def test_round_significand_ties_to_even():
+    one = 1.0
+    ulp16 = 2.0 ** -10
+    assert O.round_significand(np.array([one + ulp16 / 2]), 11)[0] == one
+    assert O.round_significand(np.array([one + 1.5 * ulp16]), 11)[0] == one + 2 * ulp16
+    assert O.round_significand(np.array([-(one + 1.5 * ulp16)]), 11)[0] == -(one + 2 * ulp16)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16", 5e-3), ("bf16", 5e-3), ("fp32", 1e-5)])
+def test_emulated_sketch_within_precision_tolerance(prec, tol):
+    m, n = 4096, 32
+    A = inputs.make_matrix(m, n, 1e8, seed=4)
+    d, idx = O.rademacher(m, 0), O.sample_rows(m, 2 * n, 0)
+    Y = O.sketch(A, idx, d)
+    Yp = O.sketch_emulated(A, idx, d, prec)
+    err = np.linalg.norm(Yp - Y) / np.linalg.norm(Y)
+    assert err < tol
+    assert err > O.UNIT_ROUNDOFF[prec] / 100     # really rounded
+
+
+# --- SketchQR, Cholesky, substitution (Algorithm 1, Algorithm 2 steps 5-9) ----
+
+@pytest.mark.parametrize("c,n", [(8, 8), (64, 32), (300, 50)])
+def test_householder_matches_library_qr(c, n):
+    Y = inputs.gaussian(c, n, seed=c + n)
+    Q, R = O.householder_qr(Y, want_q=True)
+    assert np.all(np.diag(R) > 0)
+    np.testing.assert_allclose(np.tril(R, -1), 0)
+    np.testing.assert_allclose(Q @ R, Y, atol=1e-13 * np.abs(Y).max())
+    np.testing.assert_allclose(Q.T @ Q, np.eye(n), atol=1e-13)
+    _, Rl = np.linalg.qr(Y)
+    Rl = Rl * np.sign(np.diag(Rl))[:, None]
+    np.testing.assert_allclose(R, Rl, atol=1e-12 * np.abs(Rl).max())
+
+
+def test_householder_fp32_and_row_permutation():
+    Y = inputs.gaussian(96, 32, seed=5)
+    R = O.householder_qr(Y)
+    R32 = O.householder_qr(Y.astype(np.float32), dtype=np.float32)
+    assert np.linalg.norm(R32 - R) / np.linalg.norm(R) < 1e-5
+    perm = np.random.default_rng(0).permutation(96)
+    np.testing.assert_allclose(O.householder_qr(Y[perm]), R, atol=1e-12 * np.abs(R).max())
+
+
+def test_trsm_matches_library_and_identity():
+    A = inputs.gaussian(500, 24, seed=6)
+    R = inputs.upper_with_positive_diag(24, 1e3, seed=6)
+    W = O.trsm_right_upper(A, R)
+    ref = scipy.linalg.solve_triangular(R, A.T, trans="T", lower=False).T
+    np.testing.assert_allclose(W, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+    np.testing.assert_array_equal(O.trsm_right_upper(A, np.eye(24)), A)
+
+
+def test_cholesky_matches_library_and_breaks_down():
+    X = inputs.gaussian(200, 30, seed=7)
+    G = X.T @ X
+    R = O.cholesky_upper(G)
+    np.testing.assert_allclose(R, np.linalg.cholesky(G).T, rtol=1e-12, atol=1e-12)
+    with pytest.raises(O.CholeskyBreakdown):
+        O.cholesky_upper(np.array([[1.0, 2.0], [2.0, 1.0]]))
+    with pytest.raises(O.CholeskyBreakdown):
+        Z = X.copy()
+        Z[:, 3] = Z[:, 5]
+        O.cholesky_upper(Z.T @ Z)
+
+
+def test_cholqr_instability_and_probe_bound():
+    # Algorithm 1: orthogonality O(kappa^2 u) (Sec. I-A); breakdown near 1e8
+    m, n = 4096, 16
+    q1 = O.orthogonality_error(O.cholqr(inputs.make_matrix(m, n, 1.0, seed=1))[0])[0]
+    assert q1 < 1e-14
+    for kappa in (1e2, 1e4, 1e6, 1e7):
+        Q, _ = O.cholqr(inputs.make_matrix(m, n, kappa, seed=2))
+        q = O.orthogonality_error(Q)[0]
+        assert q < 100 * kappa ** 2 * O.U_FP64
+        # probe of Sec. II-C: kappa >= sqrt(q / (u (1 + q)))
+        assert O.probe_kappa_lower(q) <= kappa * 1.0000001
+    if True:
+        with pytest.raises(O.CholeskyBreakdown):
+            O.cholqr(inputs.make_matrix(m, n, 1e10, seed=3))
+
+
+# --- Algorithm 2 end to end ---------------------------------------------------
+
+@pytest.mark.parametrize("kappa", [1e0, 1e4, 1e8, 1e12, 1e16])
+def test_mrcqr_fp64_sketch_orthogonal_and_backward_stable(kappa):
+    m, n = 4096, 32
+    A, U, sig, V = inputs.make_matrix(m, n, kappa, seed=10, return_factors=True)
+    res = O.mrcqr(A, seed=0, prec="fp64")
+    o2, of, _ = O.orthogonality_error(res.Q)
+    rf, r2 = O.residual_error(A, res.Q, res.R)
+    assert o2 <= 1e-13 and rf <= 1e-13
+    assert np.all(np.diag(res.R) > 0)
+    np.testing.assert_array_equal(np.tril(res.R, -1), 0)
+    # Q spans range(A) = range(U)
+    assert np.linalg.norm(res.Q - U @ (U.T @ res.Q)) < 1e-13 * kappa + 1e-12
+    # R against the exact R of A = U (Sigma V^T), Sigma V^T = Q1 R0
+    if kappa <= 1e8:
+        _, R0 = np.linalg.qr(sig[:, None] * V.T)
+        R0 = R0 * np.sign(np.diag(R0))[:, None]
+        assert np.linalg.norm(res.R - R0) / np.linalg.norm(R0) < 100 * kappa * O.U_FP64 * n
+
+
+def test_mrcqr_exact_factors():
+    # A = U R0 with orthonormal U and upper R0 (positive diagonal) is its own QR
+    U = inputs.orthonormal_matrix(2048, 20, seed=4)
+    # R0 = diag(d) (I + 0.1 N), d graded 1 .. 1e-6: kappa(R0) ~ 1e6
+    N = inputs.upper_with_positive_diag(20, 1.0, seed=4)
+    d = np.exp(-np.log(1e6) * np.arange(20) / 19)
+    R0 = d[:, None] * (np.eye(20) + 0.1 * np.triu(N, 1))
+    kappa = O.cond2(R0)
+    res = O.mrcqr(U @ R0, seed=1)
+    # QR perturbation theory: forward errors O(kappa u)
+    assert np.abs(res.Q - U).max() < 100 * kappa * O.U_FP64
+    assert np.linalg.norm(res.R - R0) / np.linalg.norm(R0) < 100 * kappa * O.U_FP64
+
+
+def test_mrcqr_stage2_reduces_to_cholqr():
+    # with R_s = I Stage 2 is Algorithm 1 itself
+    A = inputs.make_matrix(1024, 12, 10.0, seed=8)
+    W = O.trsm_right_upper(A, np.eye(12))
+    Rc = O.cholesky_upper(W.T @ W)
+    Q = O.trsm_right_upper(W, Rc)
+    Qc, Rcq = O.cholqr(A)
+    np.testing.assert_array_equal(Q, Qc)
+    np.testing.assert_array_equal(Rc, Rcq)
+
+
+def test_mrcqr_invariant_to_sketch_scale():
+    A = inputs.make_matrix(2048, 16, 1e6, seed=9)
+    r1 = O.mrcqr(A, seed=2)
+    r2 = O.mrcqr(A, seed=2, sketch_scale=3.0 * 2.0 ** -9)
+    # equal in exact arithmetic; in FP64 within the forward error O(kappa u)
+    tol = 100 * 1e6 * O.U_FP64
+    assert np.abs(r2.Q - r1.Q).max() < tol
+    assert np.linalg.norm(r2.R - r1.R) / np.linalg.norm(r1.R) < tol
+
+
+@pytest.mark.parametrize("prec,kappa", [("fp16", 1e2), ("fp16", 1e4), ("bf16", 1e2), ("fp32", 1e4),
+                                        ("fp32", 1e8)])
+def test_reduced_precision_sketch_within_threshold(prec, kappa):
+    # Sec. II-B: u_p * kappa <~ 1 keeps O(u) orthogonality
+    A = inputs.make_matrix(4096, 32, kappa, seed=12)
+    res = O.mrcqr(A, seed=0, prec=prec)
+    assert O.orthogonality_error(res.Q)[0] <= 1e-13
+    assert O.residual_error(A, res.Q, res.R)[0] <= 1e-13
+
+
+@pytest.mark.parametrize("prec,kappa", [("fp16", 1e8), ("bf16", 1e6), ("fp32", 1e13)])
+def test_reduced_precision_sketch_degrades_beyond_threshold(prec, kappa):
+    # Fig. 1 / Sec. IV-B: past the threshold orthogonality leaves O(u)
+    A = inputs.make_matrix(4096, 32, kappa, seed=13)
+    try:
+        res = O.mrcqr(A, seed=0, prec=prec)
+    except O.CholeskyBreakdown:
+        return
+    assert O.orthogonality_error(res.Q)[0] > 1e-13
+
+
+@pytest.mark.parametrize("prec,kappa", [("fp16", 1e2), ("fp16", 1e3), ("fp32", 1e5), ("fp32", 1e6)])
+def test_theorem1_bound_holds(prec, kappa):
+    # Theorem 1 with E = R_hat_s - R_s, R_s from the FP64 sketch of the same S
+    A = inputs.make_matrix(4096, 24, kappa, seed=14)
+    ref = O.mrcqr(A, seed=5, prec="fp64")
+    low = O.mrcqr(A, seed=5, prec=prec)
+    Rs, Rh = ref.Rs, low.Rs
+    eps = np.linalg.norm(Rh - Rs, 2) / np.linalg.norm(Rs, 2)
+    kRs = O.cond2(Rs)
+    assert eps * kRs < 1
+    k1 = O.cond2(O.trsm_right_upper(A, Rs))
+    k1h = O.cond2(O.trsm_right_upper(A, Rh))
+    assert k1h <= O.theorem1_bound(k1, eps, kRs) * (1 + 1e-9)
+    assert k1 < 10          # SRTT preconditioning: kappa(A R_s^-1) = O(1)
+
+
+def test_precision_rule_boundaries():
+    assert O.precision_rule(1e4) == "fp16"
+    assert O.precision_rule(1.0001e4) == "fp32"
+    assert O.precision_rule(1e8) == "fp32"
+    assert O.precision_rule(1e12) == "fp64"
+
+
+# --- the double-double checks ---------------------------------------------------
+
+def _exact_gram_minus_identity(Q):
+    m, n = Q.shape
+    F = [[Fraction(float(Q[i, j])) for j in range(n)] for i in range(m)]
+    return [[sum(F[k][i] * F[k][j] for k in range(m)) - (1 if i == j else 0) for j in range(n)]
+            for i in range(n)]
+
+
+def test_dd_gram_is_correctly_rounded_sum():
+    rng = np.random.default_rng(3)
+    Q = np.linalg.qr(rng.standard_normal((40, 4)))[0]
+    Q[5, 1] += 1e-9
+    _, _, E = O.orthogonality_error(Q)
+    ex = _exact_gram_minus_identity(Q)
+    for i in range(4):
+        for j in range(4):
+            exact = ex[i][j]
+            assert abs(Fraction(float(E[i, j])) - exact) <= abs(exact) * Fraction(2.0 ** -50) + Fraction(2.0 ** -100)
+
+
+def test_dd_residual_exact_on_small_case():
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((30, 3))
+    Q = rng.standard_normal((30, 3))
+    R = np.triu(rng.standard_normal((3, 3)))
+    fro, _ = O.residual_error(A, Q, R)
+    tot = Fraction(0)
+    for i in range(30):
+        for j in range(3):
+            r = Fraction(float(A[i, j])) - sum(Fraction(float(Q[i, k])) * Fraction(float(R[k, j]))
+                                               for k in range(j + 1))
+            tot += Fraction(float(r)) ** 2
+    exact = math.sqrt(float(tot)) / np.linalg.norm(A)
+    assert abs(fro - exact) <= 1e-14 * exact
+
+
+def test_dd_dot_beats_naive_on_cancellation():
+    x = np.array([1e16, 1.0, -1e16])
+    y = np.array([1.0, 1.0, 1.0])
+    assert O.dd_dot(x, y) == 1.0
