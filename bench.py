@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""MRCQR benchmark on GB300.
+
+One step = MRCQR (Algorithm 2) of the five m x n matrices of the large-
+factorization workload -- m = 2^20, n = 128, geometric spectra with
+kappa_2 in {1e2, 1e4, 1e8, 1e12, 1e16}, sketch precision by the paper's
+bounds (FP16 up to 1e4, FP32 up to 1e8, FP64 above), s = 2n, sketch seed 0 --
+with the device-side ||I - Q^T Q|| judge on.  Inputs are synthetic (seeded
+generator, U from the QR of a Gaussian, Haar V), 1 GiB each, so every step
+streams more than L2 holds.
+
+Prints one JSON line (rank 0): factorizations/s over all ranks (weak scaling:
+every rank factors its own five matrices, no data-path collective), the
+FP64-sketch MRCQR on the same GPU as the in-GPU baseline, the end-to-end
+rate with host buffers, the dominant kernel's roofline, clocks and the CPU
+oracle baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+KAPPAS = [1e2, 1e4, 1e8, 1e12, 1e16]
+METRIC = "factorizations/s (MRCQR, ||I-Q^TQ||<=1e-13)"
+UNIT = "factorizations/s"
+# FP64 pipe of GB300: 152 SMs x 2 DFMA/clk/SM (4 flops) x 2.07 GHz max clock
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def rule(kappa: float) -> str:
+    if kappa <= 1e4:
+        return "fp16"
+    if kappa <= 1e8:
+        return "fp32"
+    return "fp64"
+
+
+def fp64eq_flops(m: int, n: int) -> float:
+    """Effective FP64-equivalent work of one factorization: 2mn^2 plus the
+    nominal real-transform count 2.5 n m log2 m."""
+    return 2.0 * m * n * n + 2.5 * n * m * math.log2(m)
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        th = [d.get("num_threads", 0) for d in threadpool_info() if d.get("user_api") == "blas"]
+        if th:
+            return int(max(th))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes per row of the kernel from a committed ncu summary, valid
+    only while the kernel's source is unchanged."""
+    try:
+        d = json.load(open(PROFILE_TRAFFIC))
+    except Exception:
+        return None
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2606_18411_gb300", "csrc", ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if h != ent.get("source_sha256"):
+        return None
+    return ent
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2606_18411_gb300 import build as _build
+    from paper_2606_18411_gb300 import inputs, _lib
+    from paper_2606_18411_gb300 import mrcqr as M
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    lib = _lib.load()
+    dev = torch.device("cuda", local)
+    m, n, K, W = args.m, args.n, args.steps, args.warmup
+    precs = [rule(k) for k in KAPPAS]
+    As = [inputs.make_matrix_device(m, n, k, seed=2000 + 17 * rank + i, device=dev) for i, k in enumerate(KAPPAS)]
+    Qs = [M.empty_colmajor(m, n, device=dev) for _ in KAPPAS]
+    Rs = [M.empty_colmajor(n, n, device=dev) for _ in KAPPAS]
+    stats = torch.zeros((len(KAPPAS), 8), dtype=torch.float64, device=dev)   # 64 B per mrcqr_stats_t
+    torch.cuda.synchronize()
+
+    def step(pl):
+        for i in range(len(As)):
+            M.factor_ex(As[i], Qs[i], Rs[i], prec=pl[i], seed=0, stats_device=stats[i])
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(pl, steps, profile=False):
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            lib.mrcqr_profile_begin()
+        c0 = lib.mrcqr_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step(pl)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        launches = lib.mrcqr_launch_count() - c0
+        recs = None
+        if profile:
+            import ctypes
+            cnt = ctypes.c_int32()
+            cap = 100000
+            st = (ctypes.c_int32 * cap)()
+            lv = (ctypes.c_int32 * cap)()
+            ms = (ctypes.c_float * cap)()
+            lib.mrcqr_profile_end(cap, st, lv, ms, ctypes.byref(cnt))
+            recs = [(st[i], lv[i], ms[i]) for i in range(min(cnt.value, cap))]
+        t = e0.elapsed_time(e1) / 1000.0
+        if world > 1:
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t, launches, recs
+
+    def read_stats():
+        import ctypes
+        raw = stats.cpu().numpy().tobytes()
+        out = []
+        for i in range(len(As)):
+            s = _lib.Stats.from_buffer_copy(raw[64 * i:64 * (i + 1)])
+            out.append(s.as_dict())
+        return out
+
+    for _ in range(W):
+        step(precs)
+    torch.cuda.synchronize()
+    st_ours = read_stats()
+    ok = all(s["status"] == "OK" and s["retries"] == 0 for s in st_ours)
+
+    smi = ClockSampler(local)
+    t_ours, launches, recs = timed(precs, K, profile=True)
+    clocks = smi.stop()
+    st_after = read_stats()
+    ok = ok and all(s["status"] == "OK" for s in st_after)
+    units = len(As) * world * K
+    value = units / t_ours
+
+    # dominant kernel of the step (level 0 launches; no escalation happens here)
+    per = {}
+    for sid, lv, ms in recs or []:
+        if lv != 0:
+            continue
+        name = lib.mrcqr_stage_name(sid).decode()
+        d = per.setdefault(name, [0.0, 0])
+        d[0] += ms
+        d[1] += 1
+    flops_per_launch = {"trsm": m * n * n, "syrk": m * n * (n + 1), "finalize": m * n * (n + 1),
+                        "check": m * n * (n + 1)}
+    stage2 = {k: v for k, v in per.items() if k in flops_per_launch}
+    dom = max(stage2, key=lambda k: stage2[k][0]) if stage2 else None
+    roofline = None
+    if dom:
+        avg_ms = stage2[dom][0] / stage2[dom][1]
+        ach = flops_per_launch[dom] / (avg_ms / 1000.0) / 1e12
+        tr = load_traffic(dom)
+        traffic = None
+        if tr and tr.get("n") == n:
+            traffic = tr["bytes_per_row"] * m
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                    "peak_source": "derived FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
+                    "avg_launch_ms": round(avg_ms, 4)}
+    step_ms_by_kernel = {k: round(v[0] / K, 3) for k, v in sorted(per.items(), key=lambda kv: -kv[1][0])}
+
+    # in-GPU baseline: the same step with every sketch in FP64
+    fp64 = ["fp64"] * len(As)
+    step(fp64)
+    torch.cuda.synchronize()
+    kb = max(1, min(K, 3))
+    t_b, _, _ = timed(fp64, kb)
+    baseline_value = len(As) * world * kb / t_b
+    st_b = read_stats()
+
+    # end to end through the public API with host buffers
+    hA = [a.t().contiguous().cpu().pin_memory() for a in As]       # n x m row-major = column-major m x n
+    hQ = [torch.empty((n, m), dtype=torch.float64).pin_memory() for _ in As]
+    hR = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in As]
+    dA = [M.empty_colmajor(m, n, device=dev) for _ in As]
+
+    def e2e_step():
+        for i in range(len(As)):
+            dA[i].t().copy_(hA[i], non_blocking=True)
+            M.factor_ex(dA[i], Qs[i], Rs[i], prec=precs[i], seed=0, stats_device=stats[i])
+            hQ[i].copy_(Qs[i].t(), non_blocking=True)
+            hR[i].copy_(Rs[i].t(), non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    ke = max(1, min(K, 3))
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(ke):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    t_e = e0.elapsed_time(e1) / 1000.0
+    if world > 1:
+        tt = torch.tensor([t_e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e = float(tt.item())
+    e2e = {"value": round(len(As) * world * ke / t_e, 4), "unit": UNIT,
+           "h2d_bytes_per_step": int(len(As) * 8 * m * n),
+           "d2h_bytes_per_step": int(len(As) * 8 * (m * n + n * n))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n, m)
+
+    if rank == 0:
+        flops = sum(fp64eq_flops(m, n) for _ in As) * world * K
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": round(t_ours * 1000.0 / K, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded A = U diag(sigma) V^T)",
+            "config": {"workload": f"MRCQR m=2^{int(math.log2(m))} n={n} geometric kappa in "
+                                   "{1e2,1e4,1e8,1e12,1e16}, sketch precision by rule, s=2n",
+                       "m": m, "n": n, "kappas": KAPPAS, "sketch_precisions": precs, "s": 2 * n,
+                       "factorizations_per_step": len(As), "l2": "inputs larger than L2 (1 GiB per matrix)",
+                       "parallelism": f"replicas x{world}"},
+            "fp64eq_gflops": round(flops / t_ours / 1e9, 2),
+            "fp64_sketch_baseline": {"value": round(baseline_value, 4), "unit": UNIT,
+                                     "speedup_of_rule_precision": round(value / baseline_value, 3),
+                                     "all_ok": all(s["status"] == "OK" for s in st_b)},
+            "all_ok": ok, "ortho_fro": [s["ortho_fro"] for s in st_after],
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+            "step_ms_by_kernel": step_ms_by_kernel, "clocks": clocks, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(n: int, m_full: int, m_sample: int = 1 << 18):
+    """The CPU oracle, as it stands, on one matrix of the workload cut to
+    m_sample rows (its cost is linear in m), scaled to factorizations/s of
+    the full m."""
+    import oracle
+    from paper_2606_18411_gb300 import inputs
+    A = inputs.make_matrix(m_sample, n, 1e8, seed=4242)
+    t0 = time.perf_counter()
+    oracle.mrcqr(A, seed=0, prec=rule(1e8))
+    t = time.perf_counter() - t0
+    return {"value": round((m_sample / m_full) / t, 6), "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": f"1 factorization, m={m_sample} n={n} kappa=1e8 fp32-emulated sketch, {t:.2f} s; "
+                      f"scaled by m/{m_full} (oracle cost is linear in m)"}
+
+
+def run_reference(args):
+    """The oracle on the host cores: each step one factorization of the
+    workload cut to 2^16 rows, scaled to the full m."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2606_18411_gb300 import inputs
+    m_s, n = 1 << 16, args.n
+    mats = [inputs.make_matrix(m_s, n, k, seed=3000 + i) for i, k in enumerate(KAPPAS)]
+    for w in range(args.warmup):
+        oracle.mrcqr(mats[w % len(mats)], seed=0, prec=rule(KAPPAS[w % len(mats)]))
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        i = k % len(mats)
+        oracle.mrcqr(mats[i], seed=0, prec=rule(KAPPAS[i]))
+    t = time.perf_counter() - t0
+    value = args.steps * (m_s / args.m) / t
+    sample = f"each step 1 factorization, m={m_s} n={n}, kappa cycling {KAPPAS}, scaled by m/{args.m}"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1000 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded A = U diag(sigma) V^T)",
+            "config": {"workload": f"MRCQR m=2^{int(math.log2(args.m))} n={n} geometric kappa in "
+                                   "{1e2,1e4,1e8,1e12,1e16}, sketch precision by rule, s=2n", "m": args.m, "n": n},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--m", type=int, default=1 << 20)
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * mrcqr.h -- C ABI of the GB300 MRCQR library (libmrcqr.so).
+ *
+ * MRCQR (Garrison, Chen, Ipsen, "Numerically Stable Cholesky-QR on GPU via
+ * Mixed-Precision Randomized Preconditioning") computes the thin QR
+ * factorization A = QR of a tall-skinny FP64 matrix (m >> n, full column
+ * rank) with an explicit Q, ||I - Q^T Q||_2 = O(u) for kappa_2(A) up to 1e16
+ * (Sec. I, Eq. 1).  Algorithm 2: a randomized trigonometric sketch
+ * Y = sqrt(m/s) P F D A taken in a reduced precision p gives a preconditioner
+ * R_s (the R of Y); Cholesky-QR (Algorithm 1) of W = A R_s^{-1} runs in FP64;
+ * R = R_c R_s.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are DEVICE memory, column-major (LAPACK/cuBLAS convention), on
+ *    the device that is current when the call is made.  The caller owns A, Q
+ *    and R.  A is read only and must not overlap Q or R.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; 0 = legacy default
+ *    stream).  Argument errors return at once, before anything is enqueued.
+ *    Errors found on the device (breakdown, non-finite input, failed
+ *    orthogonality) go to a device status record read by
+ *    mrcqr_get_last_status() or written to opts->stats_device.
+ *  - The library allocates its workspace with the stream-ordered allocator
+ *    (cudaMallocAsync / cudaFreeAsync on `stream`) inside each call.
+ *  - Results are deterministic for a fixed seed, shape, precision and build:
+ *    every reduction runs in a fixed order, no floating-point atomics.
+ *  - Return value: an mrcqr_status_t (MRCQR_OK when the work was enqueued).
+ */
+#ifndef MRCQR_H
+#define MRCQR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mrcqr_stream_t; /* same type as cudaStream_t */
+
+/* Sketch precision p of Algorithm 2 (Sec. II-B: half suffices for
+ * kappa <~ 1e4, single for kappa <~ 1e8, double beyond).  BF16 is an extra
+ * tier (unit roundoff 2^-8: safe for kappa <~ 1e2).  AUTO lets the learned
+ * selector pick from an FP16 sketch's R_s (see mrcqr_selector_load). */
+typedef enum {
+  MRCQR_PREC_FP16 = 0,
+  MRCQR_PREC_BF16 = 1,
+  MRCQR_PREC_FP32 = 2,
+  MRCQR_PREC_FP64 = 3,
+  MRCQR_PREC_AUTO = 4
+} mrcqr_prec_t;
+
+typedef enum {
+  MRCQR_OK = 0,
+  MRCQR_ERR_INVALID = 1,   /* bad argument; nothing enqueued */
+  MRCQR_ERR_BREAKDOWN = 2, /* Cholesky of the Gram matrix met a non-positive pivot (Sec. I-A) */
+  MRCQR_ERR_NONFINITE = 3, /* A holds NaN or Inf */
+  MRCQR_ERR_ORTHO = 4,     /* ||I - Q^T Q||_F above tolerance at the highest precision tried */
+  MRCQR_ERR_ALLOC = 5,     /* workspace allocation failed */
+  MRCQR_ERR_CUDA = 6,      /* a CUDA call or launch failed */
+  MRCQR_ERR_TIMEOUT = 7    /* a bounded device wait gave up (batched persistent kernels) */
+} mrcqr_status_t;
+
+typedef struct mrcqr_opts {
+  int32_t s_factor;   /* sketch rows s = s_factor * n (default 2; the paper uses 3, Sec. II-A) */
+  int32_t check;      /* 1 (default): measure ||I - Q^T Q||_F on device and judge the result */
+  int32_t escalate;   /* 1 (default): on failure re-run at the next precision (Sec. II-C),
+                         FP16/BF16 -> FP32 -> FP64 */
+  int32_t reserved0;
+  double ortho_tol;   /* acceptance threshold on ||I - Q^T Q||_F (default 1e-13) */
+  void* stats_device; /* optional DEVICE pointer to an mrcqr_stats_t written at the end */
+} mrcqr_opts_t;
+
+typedef struct mrcqr_stats {
+  int32_t status;          /* mrcqr_status_t of the device-side result */
+  int32_t prec_used;       /* sketch precision of the accepted (or last) run */
+  int32_t retries;         /* re-runs at a higher precision */
+  int32_t prec_first;      /* precision of the first run (AUTO: the selector's choice) */
+  int32_t selector_choice; /* AUTO only: 0 fp16, 1 fp32, 2 fp64; else -1 */
+  int32_t reserved[3];
+  double ortho_fro;        /* measured ||I - Q^T Q||_F of the accepted (or last) run */
+} mrcqr_stats_t;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int mrcqr_version(void);
+
+/* Static text for a status code. */
+const char* mrcqr_status_string(int status);
+
+/* Algorithm 2 (MRCQR) on one matrix.
+ *   m, n        : A is m x n, 1 <= n <= 512, m >= s = 2n, m < 2^31.
+ *   A, lda      : input, lda >= m.  Read only.
+ *   Q, ldq      : output m x n with orthonormal columns, ldq >= m.  Also
+ *                 used as scratch for W = A R_s^{-1}.
+ *   R           : output n x n upper triangular (ld = n), positive diagonal,
+ *                 strict lower triangle set to zero.
+ *   sketch_prec : mrcqr_prec_t; with the default options a failed check
+ *                 re-runs at the next precision.
+ *   seed        : Philox key of the random signs D and the sample set S.
+ * Same as mrcqr_factor_ex(..., ldr = n, opts = NULL, stream). */
+int mrcqr_factor(int64_t m, int64_t n, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
+                 int sketch_prec, uint64_t seed, mrcqr_stream_t stream);
+
+/* As mrcqr_factor with an explicit ldr (>= n) and options (NULL = defaults). */
+int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
+                    int64_t ldr, int sketch_prec, uint64_t seed, const mrcqr_opts_t* opts, mrcqr_stream_t stream);
+
+/* Synchronizes `stream` and returns the device status record of the last
+ * factorization enqueued on it by this process (MRCQR_ERR_INVALID if none). */
+int mrcqr_get_last_status(mrcqr_stream_t stream, mrcqr_stats_t* out);
+
+/* Many independent factorizations (the repeated QRs of block Krylov and
+ * randomized-SVD power steps, Sec. II-C) in grouped launches.
+ *   count          : number of problems (>= 1).
+ *   m, n, lda, ldq : HOST arrays[count] (used for planning).
+ *   A, Q, R        : HOST arrays[count] of DEVICE pointers; R_i is n_i x n_i, ld n_i.
+ *   sketch_prec    : HOST array[count] of mrcqr_prec_t (AUTO not accepted here).
+ *   seeds          : HOST array[count].
+ *   status         : DEVICE int32[count] receiving each problem's mrcqr_status_t.
+ * Per-problem rules are those of mrcqr_factor; problems are independent. */
+int mrcqr_factor_batched(int count, const int64_t* m, const int64_t* n, const double* const* A, const int64_t* lda,
+                         double* const* Q, const int64_t* ldq, double* const* R, const int* sketch_prec,
+                         const uint64_t* seeds, int32_t* status, mrcqr_stream_t stream);
+
+/* ---- step-level entry points (each is one step of Algorithm 2) ---------- */
+
+/* Algorithm 2 step 1: d[i] = +-1, i < m (DEVICE double[m]). */
+int mrcqr_signs(int64_t m, uint64_t seed, double* d, mrcqr_stream_t stream);
+
+/* Algorithm 2 step 1: the sample set, s distinct rows of {0..m-1} sorted
+ * ascending (DEVICE uint32[s]); 1 <= s <= min(m, 8192). */
+int mrcqr_sample_rows(int64_t m, int64_t s, uint64_t seed, uint32_t* idx, mrcqr_stream_t stream);
+
+/* Algorithm 2 steps 1-4: Y = sqrt(m/s) P F D A in precision sketch_prec
+ * (FP16/BF16/FP32/FP64), returned widened to FP64 (DEVICE double s x n,
+ * ld = s). */
+int mrcqr_sketch(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, int sketch_prec, uint64_t seed,
+                 double* Y, mrcqr_stream_t stream);
+
+/* Algorithm 2 steps 5-6: R_s of Y (DEVICE double s x n, ld = s) by
+ * Householder QR in FP32 (prec FP16/BF16/FP32) or FP64, diag(R_s) > 0,
+ * written to Rs (DEVICE double n x n, ld = n). */
+int mrcqr_sketch_qr(int64_t n, int64_t s, const double* Y, int prec, double* Rs, mrcqr_stream_t stream);
+
+/* Algorithm 2 steps 7-9 with a given preconditioner: Q, R_c = CholQR(A R_s^{-1})
+ * (Algorithm 1) and R = R_c R_s.  With Rs = I this is Algorithm 1 on A.
+ * Status (breakdown) through mrcqr_get_last_status. */
+int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, const double* Rs, double* Q,
+                         int64_t ldq, double* R, int64_t ldr, mrcqr_stream_t stream);
+
+/* ---- instrumentation (per-kernel timing) ------ */
+
+/* Number of kernels this library has launched in this process. */
+uint64_t mrcqr_launch_count(void);
+
+/* Name of a profiling stage id (sketch, trsm, syrk, ...). */
+const char* mrcqr_stage_name(int stage);
+
+/* From now on bracket every kernel launch with a pair of CUDA events on its
+ * stream (adds ~2 event records per launch). */
+int mrcqr_profile_begin(void);
+
+/* Stops recording, waits for the recorded events and returns up to
+ * max_records (stage id, escalation level, milliseconds) triples in launch
+ * order; *count receives the number recorded.  Arrays are HOST memory. */
+int mrcqr_profile_end(int max_records, int32_t* stage, int32_t* level, float* ms, int32_t* count);
+
+/* Releases per-stream status records.  Optional at exit. */
+int mrcqr_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRCQR_H */

@@ -1,0 +1,483 @@
+// C ABI of the MRCQR library: argument checks, the workspace plan, the
+// escalation ladder of Sec. II-C and the per-stream status records.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "../../include/mrcqr.h"
+#include "kernels.h"
+
+using namespace mrcqr;
+
+namespace {
+
+constexpr int kVersion = 10000;
+constexpr int kMaxN = 512;
+constexpr double kDefaultTol = 1e-13;
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Workspace of one factorization.
+struct Plan {
+  int64_t m = 0;
+  int n = 0, s = 0, npad = 0, chunks = 0, splits = 0;
+  size_t off_ctl = 0, off_idx = 0, off_tab = 0, off_ypart = 0, off_y = 0, off_sqr = 0, off_rs = 0, off_rst = 0,
+         off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, total = 0;
+};
+
+Plan make_plan(int64_t m, int n, int s) {
+  Plan p;
+  p.m = m;
+  p.n = n;
+  p.s = s;
+  p.npad = (n + 31) / 32 * 32;
+  p.chunks = sketch_chunks(m, n, s);
+  p.splits = syrk_splits(m, n);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  p.off_ctl = take(sizeof(Ctl));
+  p.off_idx = take(sizeof(uint32_t) * (size_t)s);
+  p.off_tab = take(sizeof(double) * (size_t)(m + 1));
+  p.off_ypart = take(sizeof(double) * (size_t)p.chunks * s * n);
+  p.off_y = take(sizeof(double) * (size_t)s * n);
+  p.off_sqr = take(sqr_workspace_bytes(n, s));
+  p.off_rs = take(sizeof(double) * (size_t)n * n);
+  p.off_rst = take(sizeof(double) * (size_t)n * p.npad);
+  p.off_rinv = take(sizeof(double) * (size_t)p.npad);
+  p.off_gpart = take(sizeof(double) * (size_t)p.splits * n * n);
+  p.off_rc = take(sizeof(double) * (size_t)n * n);
+  p.off_xt = take(sizeof(double) * (size_t)n * p.npad);
+  p.off_e = take(sizeof(double) * (size_t)n * n);
+  p.total = o;
+  return p;
+}
+
+template <typename T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+__global__ void k_init_ctl(Ctl* ctl, int nlevels, int p0, int p1, int p2, int p3, double tol) {
+  ctl->active = 0;
+  ctl->lvl_status = 0;
+  ctl->final_status = ST_OK;
+  ctl->prec_used = p0;
+  ctl->retries = 0;
+  ctl->prec_first = p0;
+  ctl->nlevels = nlevels;
+  ctl->input_nonfinite = 0;
+  ctl->lvl_prec[0] = p0;
+  ctl->lvl_prec[1] = p1;
+  ctl->lvl_prec[2] = p2;
+  ctl->lvl_prec[3] = p3;
+  ctl->mlp_choice = -1;
+  ctl->pad0 = 0;
+  ctl->tol = tol;
+  ctl->ortho_fro = 0.0;
+  for (int i = 0; i < kNumFeatures; ++i) ctl->features[i] = 0.f;
+}
+
+__global__ void k_write_stats(const Ctl* ctl, mrcqr_stats_t* out) {
+  out->status = ctl->final_status;
+  out->prec_used = ctl->prec_used;
+  out->retries = ctl->retries;
+  out->prec_first = ctl->prec_first;
+  out->selector_choice = ctl->mlp_choice;
+  out->reserved[0] = out->reserved[1] = out->reserved[2] = 0;
+  out->ortho_fro = ctl->ortho_fro;
+}
+
+// Instrumentation: a host-side count of kernel launches and, between
+// mrcqr_profile_begin/end, a CUDA-event pair around every launch.
+std::atomic<uint64_t> g_launches{0};
+
+struct ProfRec {
+  int stage, level;
+  cudaEvent_t a, b;
+};
+
+struct Prof {
+  std::mutex mu;
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+} g_prof;
+
+template <typename F>
+void launch(int stage, int level, cudaStream_t st, F&& f) {
+  if (g_prof.on) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    ProfRec r{stage, level, g_prof.get(), g_prof.get()};
+    cudaEventRecord(r.a, st);
+    f();
+    cudaEventRecord(r.b, st);
+    g_prof.recs.push_back(r);
+  } else {
+    f();
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+enum Stage {
+  SG_INIT = 0, SG_SAMPLE, SG_COSTAB, SG_SKETCH, SG_SKREDUCE, SG_SQR, SG_TRSM, SG_SYRK, SG_CHOL, SG_TRINV, SG_RMUL,
+  SG_FINALIZE, SG_CHECK, SG_JUDGE, SG_STATS, SG_PREP, SG_GREDUCE, SG_EREDUCE, SG_COUNT
+};
+const char* kStageNames[SG_COUNT] = {"init", "sample", "costab", "sketch", "sketch_reduce", "sketch_qr", "trsm",
+                                     "syrk", "chol", "trinv", "rmul", "finalize", "check", "judge", "stats",
+                                     "prepare", "gram_reduce", "check_reduce"};
+
+// Per-(device, stream) status records for mrcqr_get_last_status.
+std::mutex g_mu;
+std::map<std::pair<int, void*>, mrcqr_stats_t*> g_slots;
+
+mrcqr_stats_t* status_slot(cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto key = std::make_pair(dev, (void*)st);
+  auto it = g_slots.find(key);
+  if (it != g_slots.end()) return it->second;
+  mrcqr_stats_t* p = nullptr;
+  if (cudaMalloc(&p, sizeof(mrcqr_stats_t)) != cudaSuccess) return nullptr;
+  g_slots[key] = p;
+  return p;
+}
+
+mrcqr_stats_t* find_slot(cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_slots.find(std::make_pair(dev, (void*)st));
+  return it == g_slots.end() ? nullptr : it->second;
+}
+
+bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + bbytes && pb < pa + abytes;
+}
+
+int validate(int64_t m, int64_t n, const double* A, int64_t lda, const double* Q, int64_t ldq, const double* R,
+             int64_t ldr, int s_factor) {
+  if (!A || !Q || !R) return MRCQR_ERR_INVALID;
+  if (n < 1 || n > kMaxN || m < 1 || m >= (int64_t(1) << 31)) return MRCQR_ERR_INVALID;
+  if (s_factor < 1 || s_factor > 16) return MRCQR_ERR_INVALID;
+  const int64_t s = (int64_t)s_factor * n;
+  if (s > m || s > 8192) return MRCQR_ERR_INVALID;
+  if (lda < m || ldq < m || ldr < n) return MRCQR_ERR_INVALID;
+  const size_t abytes = sizeof(double) * (size_t)((n - 1) * lda + m);
+  const size_t qbytes = sizeof(double) * (size_t)((n - 1) * ldq + m);
+  const size_t rbytes = sizeof(double) * (size_t)((n - 1) * ldr + n);
+  if (overlaps(A, abytes, Q, qbytes) || overlaps(A, abytes, R, rbytes) || overlaps(Q, qbytes, R, rbytes))
+    return MRCQR_ERR_INVALID;
+  return MRCQR_OK;
+}
+
+// Precision ladder starting at p (Sec. II-C): FP16/BF16 -> FP32 -> FP64.
+int make_ladder(int p, bool escalate, int* lv) {
+  int k = 0;
+  lv[k++] = p;
+  if (escalate) {
+    if (p == P_FP16 || p == P_BF16) lv[k++] = P_FP32;
+    if (p != P_FP64) lv[k++] = P_FP64;
+  }
+  return k;
+}
+
+// Stage 2 + 3 for level `lvl` (R_s already in the workspace).
+void enqueue_stage2(const Plan& p, void* ws, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
+                    int64_t ldr, int check, Ctl* ctl, int lvl, cudaStream_t st) {
+  double* RsT = at<double>(ws, p.off_rst);
+  double* rinv = at<double>(ws, p.off_rinv);
+  double* Gpart = at<double>(ws, p.off_gpart);
+  double* Rc = at<double>(ws, p.off_rc);
+  double* XT = at<double>(ws, p.off_xt);
+  double* Rs = at<double>(ws, p.off_rs);
+  launch(SG_TRSM, lvl, st, [&] { launch_trsm(p.m, p.n, A, lda, RsT, rinv, Q, ldq, ctl, lvl, st); });
+  launch(SG_SYRK, lvl, st, [&] { launch_syrk(p.m, p.n, Q, ldq, p.splits, Gpart, ctl, lvl, st); });
+  double* E = at<double>(ws, p.off_e);
+  launch(SG_GREDUCE, lvl, st, [&] { launch_reduce_partials(p.n, p.splits, Gpart, Rc, ctl, lvl, st); });
+  launch(SG_CHOL, lvl, st, [&] { launch_chol(p.n, Rc, ctl, lvl, st); });
+  launch(SG_TRINV, lvl, st, [&] { launch_trinv(p.n, Rc, XT, ctl, lvl, st); });
+  launch(SG_RMUL, lvl, st, [&] { launch_rmul(p.n, Rc, Rs, R, ldr, ctl, lvl, st); });
+  launch(SG_FINALIZE, lvl, st, [&] { launch_finalize(p.m, p.n, Q, ldq, XT, ctl, lvl, st); });
+  if (check) {
+    launch(SG_CHECK, lvl, st, [&] { launch_syrk(p.m, p.n, Q, ldq, p.splits, Gpart, ctl, lvl, st); });
+    launch(SG_EREDUCE, lvl, st, [&] { launch_reduce_partials(p.n, p.splits, Gpart, E, ctl, lvl, st); });
+  }
+  launch(SG_JUDGE, lvl, st, [&] { launch_judge(p.n, E, check, ctl, lvl, st); });
+}
+
+int finish(cudaStream_t st) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "mrcqr: CUDA error %s\n", cudaGetErrorString(e));
+    return MRCQR_ERR_CUDA;
+  }
+  (void)st;
+  return MRCQR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mrcqr_version(void) { return kVersion; }
+
+const char* mrcqr_status_string(int status) {
+  switch (status) {
+    case MRCQR_OK: return "ok";
+    case MRCQR_ERR_INVALID: return "invalid argument";
+    case MRCQR_ERR_BREAKDOWN: return "Cholesky breakdown (Gram matrix not positive definite)";
+    case MRCQR_ERR_NONFINITE: return "non-finite input";
+    case MRCQR_ERR_ORTHO: return "orthogonality check failed at the highest precision";
+    case MRCQR_ERR_ALLOC: return "workspace allocation failed";
+    case MRCQR_ERR_CUDA: return "CUDA error";
+    case MRCQR_ERR_TIMEOUT: return "bounded device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
+                    int64_t ldr, int sketch_prec, uint64_t seed, const mrcqr_opts_t* opts, mrcqr_stream_t stream) {
+  const int s_factor = (opts && opts->s_factor > 0) ? opts->s_factor : 2;
+  const int check = opts ? (opts->check != 0) : 1;
+  const bool escalate = opts ? (opts->escalate != 0) : true;
+  const double tol = (opts && opts->ortho_tol > 0) ? opts->ortho_tol : kDefaultTol;
+  int rc = validate(m, n, A, lda, Q, ldq, R, ldr, s_factor);
+  if (rc != MRCQR_OK) return rc;
+  if (sketch_prec < P_FP16 || sketch_prec > P_FP64) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int s = s_factor * (int)n;
+  const Plan p = make_plan(m, (int)n, s);
+  int lv[kMaxLevels] = {P_FP64, P_FP64, P_FP64, P_FP64};
+  const int nlevels = make_ladder(sketch_prec, escalate, lv);
+  mrcqr_stats_t* slot = status_slot(st);
+  if (!slot) return MRCQR_ERR_ALLOC;
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, p.total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCQR_ERR_ALLOC;
+  }
+  Ctl* ctl = at<Ctl>(ws, p.off_ctl);
+  uint32_t* idx = at<uint32_t>(ws, p.off_idx);
+  double* tab = at<double>(ws, p.off_tab);
+  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, nlevels, lv[0], lv[1], lv[2], lv[3], tol); });
+  launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, s, seed, idx, ctl, st); });
+  launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, st); });
+  for (int L = 0; L < nlevels; ++L) {
+    double* ypart = at<double>(ws, p.off_ypart);
+    double* y = at<double>(ws, p.off_y);
+    launch(SG_SKETCH, L, st, [&] {
+      launch_sketch(lv[L], A, lda, m, (int)n, s, idx, tab, seed, p.chunks, ypart, ctl, L, st);
+    });
+    launch(SG_SKREDUCE, L, st, [&] { launch_sketch_reduce(m, (int)n, s, p.chunks, ypart, idx, y, ctl, L, st); });
+    launch(SG_SQR, L, st, [&] {
+      launch_sketch_qr(lv[L], (int)n, s, y, at<void>(ws, p.off_sqr), at<double>(ws, p.off_rs),
+                       at<double>(ws, p.off_rst), at<double>(ws, p.off_rinv), ctl, L, st);
+    });
+    enqueue_stage2(p, ws, A, lda, Q, ldq, R, ldr, check, ctl, L, st);
+  }
+  launch(SG_STATS, 0, st, [&] { k_write_stats<<<1, 1, 0, st>>>(ctl, slot); });
+  if (opts && opts->stats_device)
+    launch(SG_STATS, 0, st, [&] { k_write_stats<<<1, 1, 0, st>>>(ctl, (mrcqr_stats_t*)opts->stats_device); });
+  cudaFreeAsync(ws, st);
+  return finish(st);
+}
+
+int mrcqr_factor(int64_t m, int64_t n, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
+                 int sketch_prec, uint64_t seed, mrcqr_stream_t stream) {
+  return mrcqr_factor_ex(m, n, A, lda, Q, ldq, R, n, sketch_prec, seed, nullptr, stream);
+}
+
+int mrcqr_get_last_status(mrcqr_stream_t stream, mrcqr_stats_t* out) {
+  if (!out) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  mrcqr_stats_t* slot = find_slot(st);
+  if (!slot) return MRCQR_ERR_INVALID;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MRCQR_ERR_CUDA;
+  if (cudaMemcpy(out, slot, sizeof(mrcqr_stats_t), cudaMemcpyDeviceToHost) != cudaSuccess) return MRCQR_ERR_CUDA;
+  return MRCQR_OK;
+}
+
+int mrcqr_factor_batched(int count, const int64_t* m, const int64_t* n, const double* const* A, const int64_t* lda,
+                         double* const* Q, const int64_t* ldq, double* const* R, const int* sketch_prec,
+                         const uint64_t* seeds, int32_t* status, mrcqr_stream_t stream) {
+  if (count < 1 || !m || !n || !A || !lda || !Q || !ldq || !R || !sketch_prec || !seeds || !status)
+    return MRCQR_ERR_INVALID;
+  for (int i = 0; i < count; ++i) {
+    const int rc = validate(m[i], n[i], A[i], lda[i], Q[i], ldq[i], R[i], n[i], 2);
+    if (rc != MRCQR_OK) return rc;
+    if (sketch_prec[i] < P_FP16 || sketch_prec[i] > P_FP64) return MRCQR_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < count; ++i) {
+    mrcqr_opts_t o{};
+    o.s_factor = 2;
+    o.check = 1;
+    o.escalate = 1;
+    o.ortho_tol = kDefaultTol;
+    o.stats_device = nullptr;
+    mrcqr_stats_t* slot = status_slot(st);
+    if (!slot) return MRCQR_ERR_ALLOC;
+    const int rc = mrcqr_factor_ex(m[i], n[i], A[i], lda[i], Q[i], ldq[i], R[i], n[i], sketch_prec[i], seeds[i], &o,
+                                   stream);
+    if (rc != MRCQR_OK) return rc;
+    cudaMemcpyAsync(status + i, &slot->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+  }
+  return finish(st);
+}
+
+int mrcqr_signs(int64_t m, uint64_t seed, double* d, mrcqr_stream_t stream) {
+  if (!d || m < 1 || m >= (int64_t(1) << 31)) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  launch(SG_PREP, 0, st, [&] { launch_signs(m, seed, d, st); });
+  return finish(st);
+}
+
+int mrcqr_sample_rows(int64_t m, int64_t s, uint64_t seed, uint32_t* idx, mrcqr_stream_t stream) {
+  if (!idx || m < 1 || m >= (int64_t(1) << 31) || s < 1 || s > m || s > 8192) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, (int)s, seed, idx, nullptr, st); });
+  return finish(st);
+}
+
+int mrcqr_sketch(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, int sketch_prec, uint64_t seed,
+                 double* Y, mrcqr_stream_t stream) {
+  if (!A || !Y || n < 1 || n > kMaxN || m < 1 || m >= (int64_t(1) << 31) || lda < m || s < 1 || s > m ||
+      s > 8192)
+    return MRCQR_ERR_INVALID;
+  if (sketch_prec < P_FP16 || sketch_prec > P_FP64) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(m, (int)n, (int)s);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, p.total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCQR_ERR_ALLOC;
+  }
+  Ctl* ctl = at<Ctl>(ws, p.off_ctl);
+  uint32_t* idx = at<uint32_t>(ws, p.off_idx);
+  double* tab = at<double>(ws, p.off_tab);
+  double* ypart = at<double>(ws, p.off_ypart);
+  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, sketch_prec, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, (int)s, seed, idx, ctl, st); });
+  launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, st); });
+  launch(SG_SKETCH, 0, st, [&] {
+    launch_sketch(sketch_prec, A, lda, m, (int)n, (int)s, idx, tab, seed, p.chunks, ypart, ctl, 0, st);
+  });
+  launch(SG_SKREDUCE, 0, st, [&] { launch_sketch_reduce(m, (int)n, (int)s, p.chunks, ypart, idx, Y, ctl, 0, st); });
+  cudaFreeAsync(ws, st);
+  return finish(st);
+}
+
+int mrcqr_sketch_qr(int64_t n, int64_t s, const double* Y, int prec, double* Rs, mrcqr_stream_t stream) {
+  if (!Y || !Rs || n < 1 || n > kMaxN || s < n || s > 8192) return MRCQR_ERR_INVALID;
+  if (prec < P_FP16 || prec > P_FP64) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int npad = (int)((n + 31) / 32 * 32);
+  const size_t o_ctl = 0, o_w = align_up(sizeof(Ctl)), o_rst = o_w + align_up(sqr_workspace_bytes((int)n, (int)s)),
+               o_rinv = o_rst + align_up(sizeof(double) * n * npad), total = o_rinv + align_up(sizeof(double) * npad);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCQR_ERR_ALLOC;
+  }
+  Ctl* ctl = at<Ctl>(ws, o_ctl);
+  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, prec, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  launch(SG_SQR, 0, st, [&] {
+    launch_sketch_qr(prec, (int)n, (int)s, Y, at<void>(ws, o_w), Rs, at<double>(ws, o_rst), at<double>(ws, o_rinv),
+                     ctl, 0, st);
+  });
+  cudaFreeAsync(ws, st);
+  return finish(st);
+}
+
+int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, const double* Rs, double* Q,
+                         int64_t ldq, double* R, int64_t ldr, mrcqr_stream_t stream) {
+  int rc = validate(m, n, A, lda, Q, ldq, R, ldr, 1);
+  if (rc != MRCQR_OK) return rc;
+  if (!Rs) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(m, (int)n, (int)n);
+  mrcqr_stats_t* slot = status_slot(st);
+  if (!slot) return MRCQR_ERR_ALLOC;
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, p.total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCQR_ERR_ALLOC;
+  }
+  Ctl* ctl = at<Ctl>(ws, p.off_ctl);
+  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  cudaMemcpyAsync(at<double>(ws, p.off_rs), Rs, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st);
+  launch(SG_PREP, 0, st, [&] { launch_rs_prepare((int)n, Rs, at<double>(ws, p.off_rst), at<double>(ws, p.off_rinv), st); });
+  enqueue_stage2(p, ws, A, lda, Q, ldq, R, ldr, 1, ctl, 0, st);
+  launch(SG_STATS, 0, st, [&] { k_write_stats<<<1, 1, 0, st>>>(ctl, slot); });
+  cudaFreeAsync(ws, st);
+  return finish(st);
+}
+
+uint64_t mrcqr_launch_count(void) { return g_launches.load(); }
+
+const char* mrcqr_stage_name(int stage) {
+  return (stage >= 0 && stage < SG_COUNT) ? kStageNames[stage] : "unknown";
+}
+
+int mrcqr_profile_begin(void) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  for (auto& r : g_prof.recs) {
+    g_prof.pool.push_back(r.a);
+    g_prof.pool.push_back(r.b);
+  }
+  g_prof.recs.clear();
+  g_prof.on = true;
+  return MRCQR_OK;
+}
+
+int mrcqr_profile_end(int max_records, int32_t* stage, int32_t* level, float* ms, int32_t* count) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.on = false;
+  int k = 0;
+  for (auto& r : g_prof.recs) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return MRCQR_ERR_CUDA;
+    if (k < max_records) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, r.a, r.b);
+      if (stage) stage[k] = r.stage;
+      if (level) level[k] = r.level;
+      if (ms) ms[k] = t;
+    }
+    ++k;
+    g_prof.pool.push_back(r.a);
+    g_prof.pool.push_back(r.b);
+  }
+  g_prof.recs.clear();
+  if (count) *count = k;
+  return MRCQR_OK;
+}
+
+int mrcqr_shutdown(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& kv : g_slots) cudaFree(kv.second);
+  g_slots.clear();
+  return MRCQR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+// Stage 1 of MRCQR (Algorithm 2 steps 1-4, Sec. II-A): random signs D, the
+// sample set S, and the sketch Y = sqrt(m/s) P F D A with F the orthonormal
+// DCT-II, computed in the sketch precision p.
+//
+// This file holds the SIMT kernels (every precision; the FP64 sketch always
+// runs here because FP64 has no tensor-core path on this GPU); the tensor-core
+// FP16/BF16/TF32 sketch lives in sketch_tc.cu.
+#include <type_traits>
+#include "kernels.h"
+
+namespace mrcqr {
+
+// ---------------------------------------------------------------------------
+// Sample set (Algorithm 2 step 1): s distinct rows of {0..m-1}, uniform
+// without replacement by Floyd's algorithm, sorted ascending.  The draw for
+// j in [m-s, m) is r_j = (Philox(key, (j,1,0,0)).x * (j+1)) >> 32, uniform on
+// {0..j}; Floyd keeps r_j unless it was already chosen, in which case it
+// keeps j (never chosen before, since all earlier values are < j).
+constexpr uint32_t kEmpty = 0xffffffffu;
+
+__global__ void __launch_bounds__(1024) k_sample(int64_t m, int s, uint2 key, uint32_t* __restrict__ idx,
+                                                  const Ctl* ctl) {
+  extern __shared__ uint32_t sm[];
+  int H = 1;
+  while (H < 2 * s) H <<= 1;
+  uint32_t* draws = sm;            // s
+  uint32_t* hash = sm + s;         // H
+  uint32_t* keys = hash + H;       // P (power of two >= s) for the sort
+  int P = 1;
+  while (P < s) P <<= 1;
+  for (int t = threadIdx.x; t < s; t += blockDim.x) {
+    const uint64_t j = (uint64_t)(m - s + t);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)j, 1u, 0u, 0u), key);
+    draws[t] = (uint32_t)(((uint64_t)r.x * (j + 1)) >> 32);
+  }
+  for (int h = threadIdx.x; h < H; h += blockDim.x) hash[h] = kEmpty;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) keys[p] = kEmpty;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int hb = __ffs(H) - 1;
+    for (int t = 0; t < s; ++t) {
+      const uint32_t j = (uint32_t)(m - s + t);
+      uint32_t v = draws[t];
+      // lookup v
+      uint32_t h = (v * 2654435761u) >> (32 - max(hb, 1));
+      h &= (H - 1);
+      bool found = false;
+      while (hash[h] != kEmpty) {
+        if (hash[h] == v) { found = true; break; }
+        h = (h + 1) & (H - 1);
+      }
+      if (found) {
+        v = j;
+        h = ((v * 2654435761u) >> (32 - max(hb, 1))) & (H - 1);
+        while (hash[h] != kEmpty) h = (h + 1) & (H - 1);
+      }
+      hash[h] = v;
+      keys[t] = v;
+    }
+  }
+  __syncthreads();
+  // bitonic sort of keys[0..P) ascending (padding kEmpty sorts last)
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int l = i ^ jj;
+        if (l > i) {
+          const uint32_t a = keys[i], b = keys[l];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) { keys[i] = b; keys[l] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < s; t += blockDim.x) idx[t] = keys[t];
+}
+
+void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ctl, cudaStream_t st) {
+  int H = 1;
+  while (H < 2 * s) H <<= 1;
+  int P = 1;
+  while (P < s) P <<= 1;
+  const size_t smem = sizeof(uint32_t) * (size_t)(s + H + P);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_sample<<<1, 1024, smem, st>>>(m, s, seed_key(seed), idx, ctl);
+}
+
+// ---------------------------------------------------------------------------
+// Quarter-wave table cos(pi q / (2m)), q = 0..m (FP64).
+__global__ void k_costab(int64_t m, double* __restrict__ tab) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q <= m) tab[q] = cospi((double)q / (2.0 * (double)m));
+}
+
+void launch_costab(int64_t m, double* tab, cudaStream_t st) {
+  const int64_t nq = m + 1;
+  k_costab<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(m, tab);
+}
+
+__global__ void k_signs(int64_t m, uint2 key, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = row_sign((uint64_t)i, key);
+}
+
+void launch_signs(int64_t m, uint64_t seed, double* out, cudaStream_t st) {
+  k_signs<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, seed_key(seed), out);
+}
+
+// ---------------------------------------------------------------------------
+// SIMT sketch: a CTA owns a 64 (sample rows) x 64 (columns) tile of Y over
+// one chunk of m and walks it in slabs of 32 rows.  Per slab: Rademacher
+// signs from Philox, the sign-flipped A tile scaled per column by 2^e so
+// that max |.| lies in [2^13, 2^14) (keeps FP16 clear of underflow), one
+// rounding to p (fl_p), the transform entries cos(pi k (2j+1) / (2m))
+// rounded to p, products accumulated in FP32 (FP64 for the FP64 sketch) and
+// the scale undone.  Partials of every chunk go to Ypart and are summed in a
+// fixed order by k_sketch_reduce (deterministic).
+constexpr int kSkST = 64, kSkNT = 64, kSkT = 32;
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_sketch_simt(const double* __restrict__ A, int64_t lda, int64_t m, int n,
+                                                      int s, const uint32_t* __restrict__ idx,
+                                                      const double* __restrict__ tab, uint2 key,
+                                                      int64_t rows_per_chunk, double* __restrict__ Ypart,
+                                                      const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level)) return;
+  using Acc = std::conditional_t<PREC == P_FP64, double, float>;
+  constexpr int ST = kSkST, NT = kSkNT, T = kSkT;
+  __shared__ double Xd[T][NT + 1];
+  // FP64 reads its operand straight from Xd; the others round into Xs
+  __shared__ __align__(16) Acc Xs[T][PREC == P_FP64 ? 1 : NT];
+  __shared__ __align__(16) Acc Ss[T][ST];
+  __shared__ Acc colscale[NT];
+  __shared__ double sg[T];
+  __shared__ uint32_t ks[ST];
+  __shared__ uint64_t r0[ST];
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int s0 = blockIdx.y * ST, n0 = blockIdx.z * NT;
+  const int64_t j_begin = (int64_t)blockIdx.x * rows_per_chunk;
+  const int64_t j_end = min(m, j_begin + rows_per_chunk);
+  const uint64_t four_m = 4ull * (uint64_t)m;
+  if (tid < ST) ks[tid] = (s0 + tid < s) ? idx[s0 + tid] : kEmpty;
+
+  Acc acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = Acc(0);
+
+  for (int64_t j0 = j_begin; j0 < j_end; j0 += T) {
+    __syncthreads();
+    if (tid < T) sg[tid] = (j0 + tid < j_end) ? row_sign((uint64_t)(j0 + tid), key) : 0.0;
+    if (tid >= 64 && tid < 64 + ST) {
+      const int i = tid - 64;
+      r0[i] = ks[i] == kEmpty ? 0 : ((uint64_t)ks[i] * (uint64_t)(2 * j0 + 1)) % four_m;
+    }
+    __syncthreads();
+    for (int e = tid; e < T * NT; e += 256) {
+      const int t = e % T, c = e / T;
+      const int64_t j = j0 + t;
+      const int col = n0 + c;
+      double v = 0.0;
+      if (j < j_end && col < n) v = A[j + (int64_t)col * lda] * sg[t];
+      Xd[t][c] = v;
+    }
+    for (int e = tid; e < T * ST; e += 256) {
+      const int i = e % ST, t = e / ST;
+      const uint32_t k = ks[i];
+      double v = 0.0;
+      if (k != kEmpty && j0 + t < j_end) {
+        const uint64_t r = (r0[i] + 2ull * (uint64_t)k * (uint64_t)t) % four_m;
+        v = cos_phase(tab, (int64_t)r, m);
+      }
+      if constexpr (PREC == P_FP64) Ss[t][i] = v;
+      else Ss[t][i] = round_to_p<PREC>(v);
+    }
+    __syncthreads();
+    if constexpr (PREC != P_FP64) {
+      if (tid < NT) {
+        double amax = 0.0;
+#pragma unroll 8
+        for (int t = 0; t < T; ++t) amax = fmax(amax, fabs(Xd[t][tid]));
+        const int e = scale_exponent(amax);
+        colscale[tid] = (Acc)exp2i(-e);
+        const double up = exp2i(e);
+#pragma unroll 8
+        for (int t = 0; t < T; ++t) Xs[t][tid] = round_to_p<PREC>(Xd[t][tid] * up);
+      }
+    }
+    __syncthreads();
+    Acc tmp[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tmp[r][c] = Acc(0);
+#pragma unroll 4
+    for (int t = 0; t < T; ++t) {
+      Acc a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = Ss[t][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if constexpr (PREC == P_FP64) b[c] = Xd[t][tx * 4 + c];
+        else b[c] = Xs[t][tx * 4 + c];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmp[r][c] = fma(a[r], b[c], tmp[r][c]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if constexpr (PREC == P_FP64) acc[r][c] += tmp[r][c];
+        else acc[r][c] = fma(tmp[r][c], colscale[tx * 4 + c], acc[r][c]);
+      }
+  }
+  double* out = Ypart + (size_t)blockIdx.x * (size_t)s * (size_t)n;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = s0 + ty * 4 + r, col = n0 + tx * 4 + c;
+      if (i < s && col < n) out[(size_t)col * s + i] = (double)acc[r][c];
+    }
+}
+
+int sketch_chunks(int64_t m, int n, int s) {
+  const int tiles = ((s + kSkST - 1) / kSkST) * ((n + kSkNT - 1) / kSkNT);
+  int chunks = (4 * 152 + tiles - 1) / tiles;
+  const int64_t max_chunks = (m + kSkT - 1) / kSkT;
+  if (chunks > max_chunks) chunks = (int)max_chunks;
+  if (chunks < 1) chunks = 1;
+  return chunks;
+}
+
+static int64_t rows_per_chunk(int64_t m, int chunks) {
+  int64_t r = (m + chunks - 1) / chunks;
+  return (r + kSkT - 1) / kSkT * kSkT;
+}
+
+void launch_sketch(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,
+                   const double* tab, uint64_t seed, int chunks, double* Ypart, const Ctl* ctl, int level,
+                   cudaStream_t st) {
+  const dim3 grid(chunks, (s + kSkST - 1) / kSkST, (n + kSkNT - 1) / kSkNT);
+  const int64_t rpc = rows_per_chunk(m, chunks);
+  const uint2 key = seed_key(seed);
+  switch (prec) {
+    case P_FP16: k_sketch_simt<P_FP16><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); break;
+    case P_BF16: k_sketch_simt<P_BF16><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); break;
+    case P_FP32: k_sketch_simt<P_FP32><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); break;
+    default: k_sketch_simt<P_FP64><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); break;
+  }
+}
+
+// Y = sqrt(2/s) c_k * sum over chunks (fixed order), with c_0 = 1/sqrt(2):
+// the sqrt(m/s) sketch scale times the sqrt(2/m) c_k of the orthonormal DCT.
+__global__ void k_sketch_reduce(int n, int s, int chunks, const double* __restrict__ Ypart,
+                                const uint32_t* __restrict__ idx, double* __restrict__ Y, Ctl* ctl, int level) {
+  if (level_inactive(ctl, level)) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)s * n;
+  if (e >= total) return;
+  const int i = (int)(e % s);
+  double acc = 0.0;
+  for (int c = 0; c < chunks; ++c) acc += Ypart[(size_t)c * total + e];
+  const double coef = sqrt(2.0 / (double)s) * (idx[i] == 0 ? 0.70710678118654752440 : 1.0);
+  const double y = acc * coef;
+  Y[e] = y;
+  if (!isfinite(y)) {
+    ctl->input_nonfinite = 1;
+    raise_level_status(ctl, ST_NONFINITE);
+  }
+}
+
+void launch_sketch_reduce(int64_t m, int n, int s, int chunks, const double* Ypart, const uint32_t* idx, double* Y,
+                          Ctl* ctl, int level, cudaStream_t st) {
+  (void)m;
+  const int64_t total = (int64_t)s * n;
+  k_sketch_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, chunks, Ypart, idx, Y, ctl, level);
+}
+
+}  // namespace mrcqr

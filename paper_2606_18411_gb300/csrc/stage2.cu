@@ -1,0 +1,374 @@
+// Stage 2 and 3 of MRCQR (Algorithm 2 steps 7-9, Algorithm 1, Sec. II-A), all
+// in FP64: W = A R_s^{-1} by substitution, G = W^T W, R_c = chol(G), the
+// orthogonal factor Q = W R_c^{-1}, R = R_c R_s, and the orthogonality check
+// E = Q^T Q that judges the result (Sec. II-C: a precision that was too low
+// shows as ||I - Q^T Q|| >> u and triggers a rerun at the next precision).
+//
+// FP64 on this GPU runs at ~1/64 of the FP32 rate and has no tensor-core
+// path, so these kernels are FP64-pipe bound for every n >= 4: each one is a
+// plain SIMT kernel that keeps the DFMA pipe fed (independent accumulators,
+// broadcast operand loads), and memory traffic is secondary.
+#include "kernels.h"
+
+namespace mrcqr {
+
+constexpr int kNC = 32;   // column chunk of the row-per-thread kernels
+constexpr int kPad = 32;  // row stride padding of the transposed triangles
+
+static inline int padded(int n) { return (n + kPad - 1) / kPad * kPad; }
+
+// ---------------------------------------------------------------------------
+// W = A R_s^{-1}: every row w of W solves w R_s = a by substitution
+// (Algorithm 2 step 7, the paper's dtrsm), w_j = (a_j - sum_{k<j} w_k R_kj) / R_jj.
+// One thread per row; columns in chunks of 32 held in registers; finished
+// columns are read back from W (the Q buffer).  R_s comes transposed
+// (row-major, row stride npad, zero padding) so a row segment is one
+// contiguous uniform load.
+__global__ void __launch_bounds__(128) k_trsm(int64_t m, int n, const double* __restrict__ A, int64_t lda,
+                                              const double* __restrict__ RT, const double* __restrict__ rinv,
+                                              double* __restrict__ W, int64_t ldw, const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  const int npad = (n + kPad - 1) / kPad * kPad;
+  for (int J0 = 0; J0 < n; J0 += kNC) {
+    double t[kNC];
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) t[c] = (J0 + c < n) ? A[r + (int64_t)(J0 + c) * lda] : 0.0;
+    for (int k = 0; k < J0; ++k) {
+      const double wk = W[r + (int64_t)k * ldw];
+      const double2* Rk = reinterpret_cast<const double2*>(RT + (int64_t)k * npad + J0);
+#pragma unroll
+      for (int c2 = 0; c2 < kNC / 2; ++c2) {
+        const double2 rv = __ldg(Rk + c2);
+        t[2 * c2] = fma(-wk, rv.x, t[2 * c2]);
+        t[2 * c2 + 1] = fma(-wk, rv.y, t[2 * c2 + 1]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) {
+      t[c] *= __ldg(rinv + J0 + c);
+      const double* Rc = RT + (int64_t)(J0 + c) * npad + J0;
+      if (J0 + c < n) {
+#pragma unroll
+        for (int c2 = c + 1; c2 < kNC; ++c2) t[c2] = fma(-t[c], __ldg(Rc + c2), t[c2]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kNC; ++c)
+      if (J0 + c < n) W[r + (int64_t)(J0 + c) * ldw] = t[c];
+  }
+}
+
+void launch_trsm(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv, double* W,
+                 int64_t ldw, const Ctl* ctl, int level, cudaStream_t st) {
+  k_trsm<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(m, n, A, lda, RT, rinv, W, ldw, ctl, level);
+}
+
+// ---------------------------------------------------------------------------
+// Partial Gram matrices X^T X (upper triangle) over row splits: the Gram
+// step of Algorithm 1 (the paper uses dgemm; computing only the upper
+// triangle is the same arithmetic per entry).  A CTA owns one TN x TN tile
+// (ti <= tj) and one row split; each warp owns a 16 x 16 block and skips it
+// when it lies strictly below the diagonal.  Lane (li, lj) computes rows
+// li*4..+4 and columns lj*2..+2 of its block.  Partials are summed in a
+// fixed order by the consumer (deterministic).
+template <int TN>
+__global__ void __launch_bounds__(32 * (TN / 16) * (TN / 16)) k_syrk(int64_t m, int n, const double* __restrict__ X, int64_t ldx,
+                                                          int64_t rows_per_split, int ntile,
+                                                          double* __restrict__ Gpart, const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  constexpr int KB = 32;
+  constexpr int NB = TN / 16;          // 16x16 blocks per tile side
+  constexpr int NT = 32 * NB * NB;     // threads
+  __shared__ __align__(16) double Xi[KB][TN];
+  __shared__ __align__(16) double Xj[KB][TN];
+  // tile index -> (ti, tj), ti <= tj, row-major over the upper triangle
+  int t = blockIdx.x, ti = 0;
+  while (t >= ntile - ti) { t -= ntile - ti; ++ti; }
+  const int tj = ti + t;
+  const int i0 = ti * TN, j0 = tj * TN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bi = warp / NB, bj = warp % NB;
+  const bool active = !(ti == tj && bi > bj);
+  const int li = lane & 3, lj = lane >> 2;
+  const int rbase = bi * 16 + li * 4, cbase = bj * 16 + lj * 2;
+  const int64_t k_begin = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t k_end = min(m, k_begin + rows_per_split);
+  double acc[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.0;
+  for (int64_t k0 = k_begin; k0 < k_end; k0 += KB) {
+    __syncthreads();
+    for (int e = tid; e < KB * TN; e += NT) {
+      const int kk = e % KB, c = e / KB;
+      const int64_t row = k0 + kk;
+      const bool okr = row < k_end;
+      Xi[kk][c] = (okr && i0 + c < n) ? X[row + (int64_t)(i0 + c) * ldx] : 0.0;
+      if (ti != tj) Xj[kk][c] = (okr && j0 + c < n) ? X[row + (int64_t)(j0 + c) * ldx] : 0.0;
+    }
+    __syncthreads();
+    if (active) {
+      const double(*Xb)[TN] = (ti == tj) ? Xi : Xj;
+#pragma unroll 8
+      for (int kk = 0; kk < KB; ++kk) {
+        const double2 b = *reinterpret_cast<const double2*>(&Xb[kk][cbase]);
+        double a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = Xi[kk][rbase + q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[q][0] = fma(a[q], b.x, acc[q][0]);
+          acc[q][1] = fma(a[q], b.y, acc[q][1]);
+        }
+      }
+    }
+  }
+  if (!active) return;
+  double* out = Gpart + (size_t)blockIdx.y * (size_t)n * (size_t)n;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int gi = i0 + rbase + q, gj = j0 + cbase + c;
+      if (gi < n && gj < n && gi <= gj) out[(int64_t)gj * n + gi] = acc[q][c];
+    }
+}
+
+static int syrk_tile(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : 64); }
+
+int syrk_splits(int64_t m, int n) {
+  const int TN = syrk_tile(n);
+  const int nt = (n + TN - 1) / TN;
+  const int tiles = nt * (nt + 1) / 2;
+  // enough CTAs to fill the GPU a few times over; each split >= 256 rows
+  int splits = (8 * 152 + tiles - 1) / tiles;
+  const int64_t maxs = (m + 255) / 256;
+  if (splits > maxs) splits = (int)maxs;
+  return splits < 1 ? 1 : splits;
+}
+
+void launch_syrk(int64_t m, int n, const double* X, int64_t ldx, int splits, double* Gpart, const Ctl* ctl, int level,
+                 cudaStream_t st) {
+  const int TN = syrk_tile(n);
+  const int nt = (n + TN - 1) / TN;
+  const int tiles = nt * (nt + 1) / 2;
+  int64_t rps = (m + splits - 1) / splits;
+  rps = (rps + 31) / 32 * 32;
+  const dim3 grid(tiles, splits);
+  if (TN == 16) k_syrk<16><<<grid, 32, 0, st>>>(m, n, X, ldx, rps, nt, Gpart, ctl, level);
+  else if (TN == 32) k_syrk<32><<<grid, 128, 0, st>>>(m, n, X, ldx, rps, nt, Gpart, ctl, level);
+  else k_syrk<64><<<grid, 512, 0, st>>>(m, n, X, ldx, rps, nt, Gpart, ctl, level);
+}
+
+// ---------------------------------------------------------------------------
+// Sum of the per-split Gram partials, upper triangle, in a fixed order (one
+// thread per entry; deterministic).  Lower triangle set to zero.
+__global__ void k_reduce_partials(int n, int splits, const double* __restrict__ part, double* __restrict__ out,
+                                  const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int64_t nn = (int64_t)n * n;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  double v = 0.0;
+  if (i <= j)
+    for (int sp = 0; sp < splits; ++sp) v += part[(size_t)sp * nn + e];
+  out[e] = v;
+}
+
+void launch_reduce_partials(int n, int splits, const double* part, double* out, const Ctl* ctl, int level,
+                            cudaStream_t st) {
+  const int64_t nn = (int64_t)n * n;
+  k_reduce_partials<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, splits, part, out, ctl, level);
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky of the Gram matrix (Algorithm 1 step 2): G = R_c^T R_c, R_c
+// upper with positive diagonal, in place on the reduced upper triangle with
+// right-looking elimination (one CTA).  A non-positive or non-finite pivot
+// raises BREAKDOWN for this level.
+__global__ void __launch_bounds__(1024) k_chol(int n, double* __restrict__ G, Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int tid = threadIdx.x;
+  const int64_t nn = (int64_t)n * n;
+  __shared__ double piv;
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      const double d = G[(int64_t)k * n + k];
+      piv = (d > 0.0 && isfinite(d)) ? sqrt(d) : -1.0;
+      if (piv > 0.0) G[(int64_t)k * n + k] = piv;
+    }
+    __syncthreads();
+    const double p = piv;
+    if (!(p > 0.0)) {
+      if (tid == 0) raise_level_status(ctl, ST_BREAKDOWN);
+      return;
+    }
+    const double ip = 1.0 / p;
+    for (int j = k + 1 + tid; j < n; j += blockDim.x) G[(int64_t)j * n + k] *= ip;   // row k
+    __syncthreads();
+    // trailing update G[i][j] -= R[k][i] R[k][j], k < i <= j: lanes over
+    // rows i (coalesced within a column), warps over columns j
+    const int tx = tid & 31, ty = tid >> 5;
+    for (int j = k + 1 + ty; j < n; j += 32) {
+      const double rkj = G[(int64_t)j * n + k];
+      for (int i = k + 1 + tx; i <= j; i += 32)
+        G[(int64_t)j * n + i] = fma(-G[(int64_t)i * n + k], rkj, G[(int64_t)j * n + i]);
+    }
+    __syncthreads();
+  }
+  for (int64_t e = tid; e < nn; e += blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i > j) G[e] = 0.0;
+  }
+}
+
+void launch_chol(int n, double* G, Ctl* ctl, int level, cudaStream_t st) {
+  k_chol<<<1, 1024, 0, st>>>(n, G, ctl, level);
+}
+
+// ---------------------------------------------------------------------------
+// X = R_c^{-1} (upper): column j by back substitution, one thread per column.
+// R_c is well conditioned after preconditioning, so forming its inverse and
+// applying it as a product (instead of a second substitution) keeps FP64
+// orthogonality; the paper's warning against explicit inverses concerns the
+// ill-conditioned R_s (Sec. II-A).  Output transposed: XT[k][j] = X[k][j]
+// stored row-major with row stride npad, zeros below the diagonal and in
+// the padding.
+__global__ void k_trinv(int n, const double* __restrict__ Rc, double* __restrict__ XT, const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int npad = (n + kPad - 1) / kPad * kPad;
+  if (j >= npad) return;
+  for (int i = j + 1; i < n; ++i) XT[(int64_t)i * npad + j] = 0.0;
+  if (j >= n) {
+    for (int i = 0; i < n; ++i) XT[(int64_t)i * npad + j] = 0.0;
+    return;
+  }
+  XT[(int64_t)j * npad + j] = 1.0 / Rc[(int64_t)j * n + j];
+  for (int i = j - 1; i >= 0; --i) {
+    double acc = 0.0;
+    for (int k = i + 1; k <= j; ++k) acc = fma(Rc[(int64_t)k * n + i], XT[(int64_t)k * npad + j], acc);
+    XT[(int64_t)i * npad + j] = -acc / Rc[(int64_t)i * n + i];
+  }
+}
+
+void launch_trinv(int n, const double* Rc, double* RcinvT, const Ctl* ctl, int level, cudaStream_t st) {
+  const int npad = padded(n);
+  k_trinv<<<(npad + 63) / 64, 64, 0, st>>>(n, Rc, RcinvT, ctl, level);
+}
+
+// R = R_c R_s (Algorithm 2 step 9), upper x upper; R col-major with ld ldr,
+// strict lower triangle set to zero.
+__global__ void k_rmul(int n, const double* __restrict__ Rc, const double* __restrict__ Rs, double* __restrict__ R,
+                       int64_t ldr, const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  double acc = 0.0;
+  for (int k = i; k <= j; ++k) acc = fma(Rc[(int64_t)k * n + i], Rs[(int64_t)j * n + k], acc);
+  R[(int64_t)j * ldr + i] = (i <= j) ? acc : 0.0;
+}
+
+void launch_rmul(int n, const double* Rc, const double* Rs, double* R, int64_t ldr, const Ctl* ctl, int level,
+                 cudaStream_t st) {
+  const int64_t nn = (int64_t)n * n;
+  k_rmul<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, Rc, Rs, R, ldr, ctl, level);
+}
+
+// ---------------------------------------------------------------------------
+// Q = W X in place (X = R_c^{-1} upper): q_j = sum_{k<=j} w_k X_kj.  One
+// thread per row; column chunks right to left so every chunk reads only
+// columns that are still W.
+__global__ void __launch_bounds__(128) k_finalize(int64_t m, int n, double* __restrict__ Q, int64_t ldq,
+                                                  const double* __restrict__ XT, const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  const int npad = (n + kPad - 1) / kPad * kPad;
+  const int last = (n - 1) / kNC * kNC;
+  for (int J0 = last; J0 >= 0; J0 -= kNC) {
+    double acc[kNC];
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) acc[c] = 0.0;
+    for (int k = 0; k < J0; ++k) {
+      const double wk = Q[r + (int64_t)k * ldq];
+      const double2* Xk = reinterpret_cast<const double2*>(XT + (int64_t)k * npad + J0);
+#pragma unroll
+      for (int c2 = 0; c2 < kNC / 2; ++c2) {
+        const double2 xv = __ldg(Xk + c2);
+        acc[2 * c2] = fma(wk, xv.x, acc[2 * c2]);
+        acc[2 * c2 + 1] = fma(wk, xv.y, acc[2 * c2 + 1]);
+      }
+    }
+#pragma unroll
+    for (int kc = 0; kc < kNC; ++kc) {
+      if (J0 + kc < n) {
+        const double wk = Q[r + (int64_t)(J0 + kc) * ldq];
+        const double* Xk = XT + (int64_t)(J0 + kc) * npad + J0;
+#pragma unroll
+        for (int c = kc; c < kNC; ++c) acc[c] = fma(wk, __ldg(Xk + c), acc[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kNC; ++c)
+      if (J0 + c < n) Q[r + (int64_t)(J0 + c) * ldq] = acc[c];
+  }
+}
+
+void launch_finalize(int64_t m, int n, double* Q, int64_t ldq, const double* XT, const Ctl* ctl, int level,
+                     cudaStream_t st) {
+  k_finalize<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(m, n, Q, ldq, XT, ctl, level);
+}
+
+// ---------------------------------------------------------------------------
+// Judge (Sec. II-C): e = ||I - Q^T Q||_F from the check partials (fixed
+// order); accept, or escalate to the next level, or give up.
+__global__ void __launch_bounds__(1024) k_judge(int n, const double* __restrict__ E, int check, Ctl* ctl,
+                                                int level) {
+  if (level_inactive(ctl, level)) return;
+  __shared__ double red[33];
+  const int64_t nn = (int64_t)n * n;
+  double part = 0.0;
+  const bool run_check = check && ctl->lvl_status == 0;
+  if (run_check) {
+    for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int i = (int)(e % n), j = (int)(e / n);
+      if (i > j) continue;
+      const double v = E[e] - (i == j ? 1.0 : 0.0);
+      part += (i == j ? 1.0 : 2.0) * v * v;
+    }
+  }
+  const double ss = block_sum(part, red);
+  if (threadIdx.x != 0) return;
+  const double e = run_check ? sqrt(ss) : 0.0;
+  const bool ok = ctl->lvl_status == 0 && e <= ctl->tol;   // NaN fails
+  if (ok) {
+    ctl->final_status = ST_OK;
+    ctl->prec_used = ctl->lvl_prec[level];
+    ctl->ortho_fro = e;
+    ctl->active = -1;
+  } else if (ctl->input_nonfinite) {
+    ctl->final_status = ST_NONFINITE;
+    ctl->prec_used = ctl->lvl_prec[level];
+    ctl->ortho_fro = e;
+    ctl->active = -1;
+  } else if (level + 1 < ctl->nlevels) {
+    ctl->retries += 1;
+    ctl->lvl_status = 0;
+    ctl->active = level + 1;
+  } else {
+    ctl->final_status = ctl->lvl_status ? ctl->lvl_status : ST_ORTHO;
+    ctl->prec_used = ctl->lvl_prec[level];
+    ctl->ortho_fro = e;
+    ctl->active = -1;
+  }
+}
+
+void launch_judge(int n, const double* E, int check, Ctl* ctl, int level, cudaStream_t st) {
+  k_judge<<<1, 1024, 0, st>>>(n, E, check, ctl, level);
+}
+
+}  // namespace mrcqr

@@ -94,3 +94,24 @@ def upper_with_positive_diag(n: int, kappa_scale: float = 1.0, seed: int = 0) ->
 def gaussian(m: int, n: int, seed: int = 0) -> np.ndarray:
     rng = np.random.Generator(np.random.Philox(seed))
     return np.asfortranarray(rng.standard_normal((m, n)))
+
+
+def make_matrix_device(m: int, n: int, kappa: float, kind: str = "geometric", seed: int = 0, device="cuda"):
+    """Same construction as ``make_matrix`` for large m, on ``device``: U is
+    orthonormalised from the seeded Gaussian by two rounds of Gram/Cholesky
+    (matrix products on the device, the n x n Cholesky on the host), which
+    for a Gaussian m x n (kappa ~ 1) gives orthonormality at the 1e-15 level.
+    Input generation only.  Returns a column-major torch float64 tensor."""
+    import torch
+    rng = np.random.Generator(np.random.Philox(seed))
+    sig = spectrum(kind, n, kappa, rng)
+    U = torch.from_numpy(rng.standard_normal((n, m))).to(device).t()      # column-major m x n
+    for _ in range(2):
+        G = (U.t() @ U).cpu().numpy()
+        Rinv = np.linalg.inv(np.linalg.cholesky(G).T)
+        U = U @ torch.from_numpy(Rinv).to(device)
+    V = torch.from_numpy(_orthonormal_columns(rng.standard_normal((n, n)))).to(device)
+    B = torch.from_numpy(sig).to(device)[:, None] * V.t()                 # Sigma V^T
+    out = torch.empty((n, m), dtype=torch.float64, device=device).t()
+    out.copy_(U @ B)
+    return out

@@ -1,0 +1,152 @@
+"""Python binding of the MRCQR C ABI: argument marshalling only.
+
+Matrices are torch CUDA float64 tensors in column-major layout, i.e. a
+tensor ``A`` of shape (m, n) with ``A.stride() == (1, lda)``; use
+``empty_colmajor`` / ``to_colmajor`` to make them.  Every computation runs in
+libmrcqr.so on the tensors' device, on torch's current stream unless a
+stream is passed."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import PREC, PREC_NAME, MrcqrError, Opts, Stats, check
+
+__all__ = ["factor", "factor_ex", "last_status", "factor_batched", "signs", "sample_rows", "sketch", "sketch_qr",
+           "cholqr_precond", "empty_colmajor", "to_colmajor", "version", "PREC", "PREC_NAME", "MrcqrError"]
+
+
+def _prec(p) -> int:
+    if isinstance(p, str):
+        return PREC[p.lower()]
+    return int(p)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def empty_colmajor(m: int, n: int, device=None, ld: int | None = None) -> torch.Tensor:
+    ld = m if ld is None else ld
+    return torch.empty((n, ld), dtype=torch.float64, device=device or "cuda").t()[:m]
+
+
+def to_colmajor(x, device=None, ld: int | None = None) -> torch.Tensor:
+    """Column-major float64 copy of an (m, n) array or tensor on the device."""
+    t = torch.as_tensor(x, dtype=torch.float64)
+    m, n = t.shape
+    out = empty_colmajor(m, n, device=device or "cuda", ld=ld)
+    out.copy_(t)
+    return out
+
+
+def _ld(t: torch.Tensor, name: str) -> int:
+    """Leading dimension of a column-major (m, n) CUDA float64 tensor."""
+    if t.dtype != torch.float64 or not t.is_cuda or t.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D CUDA float64 tensor")
+    if t.stride(0) != 1 and t.shape[0] > 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    return max(t.stride(1), t.shape[0]) if t.shape[1] == 1 else t.stride(1)
+
+
+def version() -> int:
+    return _lib.load().mrcqr_version()
+
+
+def factor_ex(A: torch.Tensor, Q: torch.Tensor, R: torch.Tensor, prec="fp64", seed: int = 0, s_factor: int = 2,
+              check_ortho: bool = True, escalate: bool = True, tol: float = 1e-13, stats_device=None,
+              stream=None) -> None:
+    """Enqueue MRCQR of A into Q (m x n) and R (n x n); asynchronous."""
+    m, n = A.shape
+    o = Opts(s_factor=s_factor, check=int(check_ortho), escalate=int(escalate), reserved0=0, ortho_tol=tol,
+             stats_device=stats_device.data_ptr() if stats_device is not None else None)
+    rc = _lib.load().mrcqr_factor_ex(m, n, A.data_ptr(), _ld(A, "A"), Q.data_ptr(), _ld(Q, "Q"), R.data_ptr(),
+                                     _ld(R, "R"), _prec(prec), seed, ctypes.byref(o), _stream(stream))
+    check(rc, "mrcqr_factor_ex")
+
+
+def factor(A: torch.Tensor, prec="fp64", seed: int = 0, stream=None, **kw):
+    """Q, R = MRCQR(A); returns column-major tensors (asynchronous)."""
+    m, n = A.shape
+    Q = empty_colmajor(m, n, device=A.device)
+    R = empty_colmajor(n, n, device=A.device)
+    if kw:
+        factor_ex(A, Q, R, prec=prec, seed=seed, stream=stream, **kw)
+    else:
+        check(_lib.load().mrcqr_factor(m, n, A.data_ptr(), _ld(A, "A"), Q.data_ptr(), _ld(Q, "Q"), R.data_ptr(),
+                                       _prec(prec), seed, _stream(stream)), "mrcqr_factor")
+    return Q, R
+
+
+def last_status(stream=None) -> dict:
+    st = Stats()
+    check(_lib.load().mrcqr_get_last_status(_stream(stream), ctypes.byref(st)), "mrcqr_get_last_status")
+    return st.as_dict()
+
+
+def factor_batched(As, Qs, Rs, precs, seeds, status: torch.Tensor, stream=None) -> None:
+    """Enqueue MRCQR of every A_i (lists of column-major tensors)."""
+    cnt = len(As)
+    arr = lambda ct, vals: (ct * cnt)(*vals)
+    m = arr(ctypes.c_int64, [a.shape[0] for a in As])
+    n = arr(ctypes.c_int64, [a.shape[1] for a in As])
+    lda = arr(ctypes.c_int64, [_ld(a, "A") for a in As])
+    ldq = arr(ctypes.c_int64, [_ld(q, "Q") for q in Qs])
+    pa = arr(ctypes.c_void_p, [a.data_ptr() for a in As])
+    pq = arr(ctypes.c_void_p, [q.data_ptr() for q in Qs])
+    pr = arr(ctypes.c_void_p, [r.data_ptr() for r in Rs])
+    pp = arr(ctypes.c_int, [_prec(p) for p in precs])
+    ps = arr(ctypes.c_uint64, [int(s) for s in seeds])
+    if status.dtype != torch.int32 or not status.is_cuda or status.numel() < cnt:
+        raise ValueError("status must be a CUDA int32 tensor with >= count entries")
+    rc = _lib.load().mrcqr_factor_batched(cnt, m, n, pa, lda, pq, ldq, pr, pp, ps, status.data_ptr(),
+                                          _stream(stream))
+    check(rc, "mrcqr_factor_batched")
+
+
+def signs(m: int, seed: int, device="cuda", stream=None) -> torch.Tensor:
+    d = torch.empty(m, dtype=torch.float64, device=device)
+    check(_lib.load().mrcqr_signs(m, seed, d.data_ptr(), _stream(stream)), "mrcqr_signs")
+    return d
+
+
+def sample_rows(m: int, s: int, seed: int, device="cuda", stream=None) -> torch.Tensor:
+    idx = torch.empty(s, dtype=torch.int32, device=device)
+    check(_lib.load().mrcqr_sample_rows(m, s, seed, idx.data_ptr(), _stream(stream)), "mrcqr_sample_rows")
+    return idx
+
+
+def sketch(A: torch.Tensor, s: int, prec="fp64", seed: int = 0, stream=None) -> torch.Tensor:
+    m, n = A.shape
+    Y = empty_colmajor(s, n, device=A.device)
+    check(_lib.load().mrcqr_sketch(m, n, A.data_ptr(), _ld(A, "A"), s, _prec(prec), seed, Y.data_ptr(),
+                                   _stream(stream)), "mrcqr_sketch")
+    return Y
+
+
+def sketch_qr(Y: torch.Tensor, prec="fp64", stream=None) -> torch.Tensor:
+    s, n = Y.shape
+    if _ld(Y, "Y") != s:
+        raise ValueError("Y must be packed (ld == s)")
+    Rs = empty_colmajor(n, n, device=Y.device)
+    check(_lib.load().mrcqr_sketch_qr(n, s, Y.data_ptr(), _prec(prec), Rs.data_ptr(), _stream(stream)),
+          "mrcqr_sketch_qr")
+    return Rs
+
+
+def cholqr_precond(A: torch.Tensor, Rs: torch.Tensor, stream=None):
+    m, n = A.shape
+    if _ld(Rs, "Rs") != n:
+        raise ValueError("Rs must be packed (ld == n)")
+    Q = empty_colmajor(m, n, device=A.device)
+    R = empty_colmajor(n, n, device=A.device)
+    check(_lib.load().mrcqr_cholqr_precond(m, n, A.data_ptr(), _ld(A, "A"), Rs.data_ptr(), Q.data_ptr(),
+                                           _ld(Q, "Q"), R.data_ptr(), _ld(R, "R"), _stream(stream)),
+          "mrcqr_cholqr_precond")
+    return Q, R

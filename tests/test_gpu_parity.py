@@ -1,0 +1,223 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact: signs and sample indices.  Floating point: the spec limits
+-- sketch within 5e-3 (FP16/BF16), 1e-5 (FP32) relative Frobenius of the FP64
+oracle sketch (1e-13 for the FP64 sketch: same arithmetic, different
+summation order); ||I - Q^T Q||_2 <= 1e-13 and ||A - QR||_F / ||A||_F <= 1e-13
+at the precision the paper's bounds allow (Sec. II-B)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_18411_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SKETCH_TOL = {"fp16": 5e-3, "bf16": 5e-3, "fp32": 1e-5, "fp64": 1e-13}
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_18411_gb300 import build
+    build.build()
+    from paper_2606_18411_gb300 import mrcqr
+    return mrcqr
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# --- Algorithm 2 step 1 ------------------------------------------------------
+
+@pytest.mark.parametrize("m,seed", [(1, 0), (4097, 0), (1 << 20, 7), ((1 << 22) + 3, 2 ** 40 + 5)])
+def test_signs_bit_exact(M, m, seed):
+    np.testing.assert_array_equal(_np(M.signs(m, seed)), O.rademacher(m, seed))
+
+
+@pytest.mark.parametrize("m,s,seed", [(1, 1, 0), (64, 64, 3), (4096, 64, 0), (4096 + 17, 66, 9),
+                                      (1 << 20, 256, 1), (1 << 22, 1024, 12345), (300000, 8192, 2 ** 33 + 1)])
+def test_sample_rows_bit_exact(M, m, s, seed):
+    got = _np(M.sample_rows(m, s, seed)).astype(np.int64)
+    np.testing.assert_array_equal(got, O.sample_rows(m, s, seed))
+
+
+# --- Algorithm 2 steps 2-4 -------------------------------------------------------
+
+@pytest.mark.parametrize("m", [8, 64, 256])
+def test_sketch_brute_force_tiny(M, m):
+    # s = m: every row of S sampled; elementwise against the dense S A
+    n = 5
+    A = inputs.gaussian(m, n, seed=m)
+    Y = _np(M.sketch(M.to_colmajor(A), m, "fp64", seed=3))
+    ref = O.sketch(A, O.sample_rows(m, m, 3), O.rademacher(m, 3))
+    np.testing.assert_allclose(Y, ref, rtol=0, atol=1e-14 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32", "fp64"])
+@pytest.mark.parametrize("m,n", [(4096, 32), (4096 + 17, 33), (20000, 100), (1000, 7)])
+def test_sketch_against_oracle(M, prec, m, n):
+    s = 2 * n
+    A = inputs.make_matrix(m, n, 1e8, seed=m + n)
+    Y = _np(M.sketch(M.to_colmajor(A), s, prec, seed=11))
+    d, idx = O.rademacher(m, 11), O.sample_rows(m, s, 11)
+    ref = O.sketch(A, idx, d)
+    err = _rel(Y, ref)
+    assert err <= SKETCH_TOL[prec], err
+    if prec != "fp64":
+        # the fl_p error model of the oracle agrees within the same order
+        emu = O.sketch_emulated(A, idx, d, prec)
+        assert _rel(Y, emu) <= 2 * SKETCH_TOL[prec]
+
+
+def test_sketch_scale_exponent_keeps_fp16_in_range(M):
+    # columns of very different magnitude (1e-12 .. 1e6): per-column 2^e scaling
+    m, n = 8192, 8
+    A = inputs.gaussian(m, n, seed=5) * np.logspace(-12, 6, n)[None, :]
+    Y = _np(M.sketch(M.to_colmajor(A), 16, "fp16", seed=1))
+    ref = O.sketch(A, O.sample_rows(m, 16, 1), O.rademacher(m, 1))
+    colerr = np.linalg.norm(Y - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert colerr.max() < 5e-3
+
+
+# --- Algorithm 2 steps 5-6 -------------------------------------------------------
+
+@pytest.mark.parametrize("prec,n", [("fp64", 32), ("fp64", 100), ("fp32", 32), ("fp32", 129)])
+def test_sketch_qr_against_householder(M, prec, n):
+    s = 2 * n
+    Y = inputs.gaussian(s, n, seed=n) * np.logspace(0, -6, n)[None, :]
+    Rs = _np(M.sketch_qr(M.to_colmajor(Y), prec))
+    ref = O.householder_qr(Y)
+    assert np.all(np.diag(Rs) > 0)
+    np.testing.assert_array_equal(np.tril(Rs, -1), 0)
+    # column-scaled Gaussian: Householder errors are columnwise ~ u_p
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    colerr = np.linalg.norm(Rs - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert colerr.max() < tol
+
+
+# --- Algorithm 1 / Algorithm 2 steps 7-9 -----------------------------------------
+
+def test_stage2_with_identity_is_cholqr(M):
+    A = inputs.make_matrix(20000, 24, 100.0, seed=3)
+    Q, R = M.cholqr_precond(M.to_colmajor(A), M.to_colmajor(np.eye(24)))
+    Qr, Rr = O.cholqr(A)
+    np.testing.assert_allclose(_np(R), Rr, rtol=0, atol=1e-12 * np.abs(Rr).max())
+    np.testing.assert_allclose(_np(Q), Qr, rtol=0, atol=1e-12)
+
+
+def test_stage2_orthonormal_input(M):
+    U = inputs.orthonormal_matrix(50000, 40, seed=2)
+    Q, R = M.cholqr_precond(M.to_colmajor(U), M.to_colmajor(np.eye(40)))
+    np.testing.assert_allclose(_np(Q), U, atol=1e-14)
+    np.testing.assert_allclose(_np(R), np.eye(40), atol=1e-14)
+
+
+def test_stage2_given_preconditioner_matches_oracle(M):
+    A = inputs.make_matrix(30000, 48, 1e12, seed=4)
+    ref = O.mrcqr(A, seed=1, prec="fp64")
+    Q, R = M.cholqr_precond(M.to_colmajor(A), M.to_colmajor(ref.Rs))
+    assert M.last_status()["status"] == "OK"
+    Qh, Rh = _np(Q), _np(R)
+    assert O.orthogonality_error(Qh)[0] <= 1e-13
+    assert O.residual_error(A, Qh, Rh)[0] <= 1e-13
+    # same R_s, same arithmetic up to summation order: W and R_c agree to ~u kappa(W)
+    assert _rel(Rh, ref.R) < 1e-10
+
+
+# --- Algorithm 2 end to end ------------------------------------------------------
+
+def _check_factor(M, A, prec, seed=0, expect_prec=None, **kw):
+    Ad = M.to_colmajor(A)
+    Q, R = M.factor(Ad, prec=prec, seed=seed, **kw)
+    st = M.last_status()
+    Qh, Rh = _np(Q), _np(R)
+    o2, of, _ = O.orthogonality_error(Qh)
+    rf, r2 = O.residual_error(A, Qh, Rh)
+    return st, o2, rf, Qh, Rh
+
+
+def test_config1_fp32_sketch(M):
+    # m=4096, n=32, geometric sigma 1..1e-8, FP32 sketch, s=2n, seed 0
+    A = inputs.make_matrix(4096, 32, 1e8, seed=1001)
+    st, o2, rf, Qh, Rh = _check_factor(M, A, "fp32", seed=0)
+    assert st["status"] == "OK" and st["retries"] == 0 and st["prec_used"] == "fp32"
+    assert o2 <= 1e-13 and rf <= 1e-13
+    assert np.all(np.diag(Rh) > 0)
+    np.testing.assert_array_equal(np.tril(Rh, -1), 0)
+    ref = O.mrcqr(A, seed=0, prec="fp32")
+    # two backward-stable QRs of the same A with diag(R) > 0: forward error O(kappa u)
+    assert _rel(Rh, ref.R) < 1e4 * 1e8 * O.U_FP64
+    assert st["ortho_fro"] <= 1e-13
+
+
+@pytest.mark.parametrize("kappa", [1e0, 1e2, 1e4, 1e8, 1e12, 1e16])
+@pytest.mark.parametrize("m,n", [(4096, 16), (10007, 50), (16384, 128)])
+def test_rule_precision_end_to_end(M, kappa, m, n):
+    prec = O.precision_rule(kappa)
+    A = inputs.make_matrix(m, n, kappa, seed=int(np.log10(kappa)) + 7 * n)
+    st, o2, rf, _, _ = _check_factor(M, A, prec, seed=3)
+    assert st["status"] == "OK", st
+    assert o2 <= 1e-13 and rf <= 1e-13, (o2, rf)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+def test_escalation_on_underestimated_precision(M, prec):
+    # Sec. II-C: a too-low precision is detected and re-run higher
+    A = inputs.make_matrix(8192, 32, 1e13, seed=21)
+    st, o2, rf, _, _ = _check_factor(M, A, prec, seed=2)
+    assert st["status"] == "OK" and st["retries"] >= 1 and st["prec_used"] == "fp64"
+    assert o2 <= 1e-13 and rf <= 1e-13
+
+
+def test_no_escalation_reports_failure(M):
+    A = inputs.make_matrix(8192, 32, 1e12, seed=22)
+    Ad = M.to_colmajor(A)
+    Q = M.empty_colmajor(8192, 32)
+    R = M.empty_colmajor(32, 32)
+    M.factor_ex(Ad, Q, R, prec="fp16", seed=0, escalate=False)
+    st = M.last_status()
+    assert st["status"] in ("ORTHO", "BREAKDOWN") and st["retries"] == 0
+
+
+def test_nonfinite_input(M):
+    A = inputs.make_matrix(4096, 16, 10.0, seed=23)
+    A[100, 3] = np.nan
+    _, _ = M.factor(M.to_colmajor(A), prec="fp32")
+    assert M.last_status()["status"] == "NONFINITE"
+
+
+def test_rank_deficient_input_fails(M):
+    A = inputs.make_matrix(4096, 16, 10.0, seed=24)
+    A[:, 5] = A[:, 9]
+    _, _ = M.factor(M.to_colmajor(A), prec="fp64")
+    assert M.last_status()["status"] in ("BREAKDOWN", "ORTHO")
+
+
+def test_deterministic(M):
+    A = M.to_colmajor(inputs.make_matrix(50000, 64, 1e8, seed=25))
+    Q1, R1 = M.factor(A, prec="fp32", seed=4)
+    Q2, R2 = M.factor(A, prec="fp32", seed=4)
+    assert (Q1 == Q2).all().item() and (R1 == R2).all().item()
+
+
+def test_leading_dimensions(M):
+    m, n = 5000, 20
+    A = inputs.make_matrix(m, n, 1e6, seed=26)
+    Ad = M.to_colmajor(A, ld=m + 13)
+    Q = M.empty_colmajor(m, n, ld=m + 5)
+    import torch
+    Rbig = torch.zeros((n, n + 3), dtype=torch.float64, device="cuda").t()[:n]
+    M.factor_ex(Ad, Q, Rbig, prec="fp32", seed=1)
+    assert M.last_status()["status"] == "OK"
+    Qh, Rh = _np(Q), _np(Rbig)
+    assert O.orthogonality_error(Qh)[0] <= 1e-13 and O.residual_error(A, Qh, Rh)[0] <= 1e-13
