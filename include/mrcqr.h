@@ -146,6 +146,25 @@ int mrcqr_sketch_qr(int64_t n, int64_t s, const double* Y, int prec, double* Rs,
 int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, const double* Rs, double* Q,
                          int64_t ldq, double* R, int64_t ldr, mrcqr_stream_t stream);
 
+/* Allocation-free variant of mrcqr_sketch_qr.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * when they need R_s -- code running under another framework's memory
+ * manager that forbids raw cudaMalloc, or a latency-critical loop where a
+ * device allocation (and the synchronization it can imply) is not allowed.
+ * Same arguments, layout and result as mrcqr_sketch_qr, but the scratch
+ * (working copy of Y, padded R_s^T, 1/diag, control block; about 641 KiB) is
+ * one static device array inside the library, held on every GPU that loads
+ * the library until the process exits.  Limits: 1 <= n <= 128 and
+ * n <= s <= 512; larger sizes return MRCQR_ERR_INVALID (with a message on
+ * stderr) before anything is enqueued.  The call allocates nothing
+ * (no cudaMalloc/cudaMallocAsync/cudaFree).  All calls share the array and it
+ * keeps the last call's contents (each call clears what must start at zero),
+ * so calls whose kernels overlap on the GPU race: order them on one stream
+ * or with events.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * outside any stream capture. */
+int mrcqr_sketch_qr_noalloc(int64_t n, int64_t s, const double* Y, int prec, double* Rs, mrcqr_stream_t stream);
+
 /* ---- instrumentation (per-kernel timing) ------ */
 
 /* Number of kernels this library has launched in this process. */

@@ -57,6 +57,7 @@ SIGNATURES = {
     "mrcqr_sketch": ([_i64, _i64, _vp, _i64, _i64, _i32, _u64, _vp, _vp], _i32),
     "mrcqr_sketch_qr": ([_i64, _i64, _vp, _i32, _vp, _vp], _i32),
     "mrcqr_cholqr_precond": ([_i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp], _i32),
+    "mrcqr_sketch_qr_noalloc": ([_i64, _i64, _vp, _i32, _vp, _vp], _i32),
     "mrcqr_launch_count": ([], ctypes.c_uint64),
     "mrcqr_stage_name": ([_i32], ctypes.c_char_p),
     "mrcqr_profile_begin": ([], _i32),
