@@ -64,7 +64,8 @@ typedef struct mrcqr_opts {
   int32_t check;      /* 1 (default): measure ||I - Q^T Q||_F on device and judge the result */
   int32_t escalate;   /* 1 (default): on failure re-run at the next precision (Sec. II-C),
                          FP16/BF16 -> FP32 -> FP64 */
-  int32_t reserved0;
+  int32_t sketch_variant; /* 0 (default): tensor-core sketch for FP16/BF16/FP32 when A is 16-byte aligned
+                             and lda is even, SIMT otherwise; 1: SIMT; 2: tensor cores when possible */
   double ortho_tol;   /* acceptance threshold on ||I - Q^T Q||_F (default 1e-13) */
   void* stats_device; /* optional DEVICE pointer to an mrcqr_stats_t written at the end */
 } mrcqr_opts_t;
@@ -129,11 +130,21 @@ int mrcqr_signs(int64_t m, uint64_t seed, double* d, mrcqr_stream_t stream);
  * ascending (DEVICE uint32[s]); 1 <= s <= min(m, 8192). */
 int mrcqr_sample_rows(int64_t m, int64_t s, uint64_t seed, uint32_t* idx, mrcqr_stream_t stream);
 
+/* fl_p of Algorithm 2 step 2 exactly as the tensor-core sketch applies it:
+ * one round-to-nearest-even from FP64 to FP16, BF16 or FP32 (subnormal
+ * targets included), y[i] = fl_p(x[i]) widened back to FP64 (DEVICE arrays
+ * of count doubles).  FP64 copies. */
+int mrcqr_round(int prec, int64_t count, const double* x, double* y, mrcqr_stream_t stream);
+
 /* Algorithm 2 steps 1-4: Y = sqrt(m/s) P F D A in precision sketch_prec
  * (FP16/BF16/FP32/FP64), returned widened to FP64 (DEVICE double s x n,
  * ld = s). */
 int mrcqr_sketch(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, int sketch_prec, uint64_t seed,
                  double* Y, mrcqr_stream_t stream);
+
+/* As mrcqr_sketch with an explicit kernel variant (see mrcqr_opts_t.sketch_variant). */
+int mrcqr_sketch_ex(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, int sketch_prec, uint64_t seed,
+                    int variant, double* Y, mrcqr_stream_t stream);
 
 /* Algorithm 2 steps 5-6: R_s of Y (DEVICE double s x n, ld = s) by
  * Householder QR in FP32 (prec FP16/BF16/FP32) or FP64, diag(R_s) > 0,
@@ -166,6 +177,10 @@ int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, con
 int mrcqr_sketch_qr_noalloc(int64_t n, int64_t s, const double* Y, int prec, double* Rs, mrcqr_stream_t stream);
 
 /* ---- instrumentation (per-kernel timing) ------ */
+
+/* Sketch kernel variant used by the most recent sketch launch of this
+ * process: 1 SIMT, 2 tensor cores (0 before any). */
+int mrcqr_last_sketch_variant(void);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t mrcqr_launch_count(void);

@@ -25,7 +25,7 @@ size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 struct Plan {
   int64_t m = 0;
   int n = 0, s = 0, npad = 0, chunks = 0, splits = 0;
-  size_t off_ctl = 0, off_idx = 0, off_tab = 0, off_ypart = 0, off_y = 0, off_sqr = 0, off_rs = 0, off_rst = 0,
+  size_t off_ctl = 0, off_idx = 0, off_tab = 0, off_tabf = 0, off_ypart = 0, off_y = 0, off_sqr = 0, off_rs = 0, off_rst = 0,
          off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, total = 0;
 };
 
@@ -46,6 +46,7 @@ Plan make_plan(int64_t m, int n, int s) {
   p.off_ctl = take(sizeof(Ctl));
   p.off_idx = take(sizeof(uint32_t) * (size_t)s);
   p.off_tab = take(sizeof(double) * (size_t)(m + 1));
+  p.off_tabf = take(sizeof(float) * (size_t)(m + 1));
   p.off_ypart = take(sizeof(double) * (size_t)p.chunks * s * n);
   p.off_y = take(sizeof(double) * (size_t)s * n);
   p.off_sqr = take(sqr_workspace_bytes(n, s));
@@ -203,6 +204,8 @@ int make_ladder(int p, bool escalate, int* lv) {
 }
 
 // Stage 2 + 3 for level `lvl` (R_s already in the workspace).
+int g_sketch_variant_last = 0;
+
 void enqueue_stage2(const Plan& p, void* ws, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
                     int64_t ldr, int check, Ctl* ctl, int lvl, cudaStream_t st) {
   double* RsT = at<double>(ws, p.off_rst);
@@ -262,6 +265,7 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
   const int check = opts ? (opts->check != 0) : 1;
   const bool escalate = opts ? (opts->escalate != 0) : true;
   const double tol = (opts && opts->ortho_tol > 0) ? opts->ortho_tol : kDefaultTol;
+  const int variant = opts ? opts->sketch_variant : 0;
   int rc = validate(m, n, A, lda, Q, ldq, R, ldr, s_factor);
   if (rc != MRCQR_OK) return rc;
   if (sketch_prec < P_FP16 || sketch_prec > P_FP64) return MRCQR_ERR_INVALID;
@@ -282,12 +286,13 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
   double* tab = at<double>(ws, p.off_tab);
   launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, nlevels, lv[0], lv[1], lv[2], lv[3], tol); });
   launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, s, seed, idx, ctl, st); });
-  launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, st); });
+  launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, at<float>(ws, p.off_tabf), st); });
   for (int L = 0; L < nlevels; ++L) {
     double* ypart = at<double>(ws, p.off_ypart);
     double* y = at<double>(ws, p.off_y);
     launch(SG_SKETCH, L, st, [&] {
-      launch_sketch(lv[L], A, lda, m, (int)n, s, idx, tab, seed, p.chunks, ypart, ctl, L, st);
+      g_sketch_variant_last = launch_sketch(lv[L], variant, A, lda, m, (int)n, s, idx, tab, at<float>(ws, p.off_tabf),
+                                            seed, p.chunks, ypart, ctl, L, st);
     });
     launch(SG_SKREDUCE, L, st, [&] { launch_sketch_reduce(m, (int)n, s, p.chunks, ypart, idx, y, ctl, L, st); });
     launch(SG_SQR, L, st, [&] {
@@ -353,6 +358,14 @@ int mrcqr_signs(int64_t m, uint64_t seed, double* d, mrcqr_stream_t stream) {
   return finish(st);
 }
 
+int mrcqr_round(int prec, int64_t count, const double* x, double* y, mrcqr_stream_t stream) {
+  if (!x || !y || count < 0 || prec < P_FP16 || prec > P_FP64) return MRCQR_ERR_INVALID;
+  if (count == 0) return MRCQR_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  launch(SG_PREP, 0, st, [&] { launch_round(prec, count, x, y, st); });
+  return finish(st);
+}
+
 int mrcqr_sample_rows(int64_t m, int64_t s, uint64_t seed, uint32_t* idx, mrcqr_stream_t stream) {
   if (!idx || m < 1 || m >= (int64_t(1) << 31) || s < 1 || s > m || s > 8192) return MRCQR_ERR_INVALID;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -362,6 +375,11 @@ int mrcqr_sample_rows(int64_t m, int64_t s, uint64_t seed, uint32_t* idx, mrcqr_
 
 int mrcqr_sketch(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, int sketch_prec, uint64_t seed,
                  double* Y, mrcqr_stream_t stream) {
+  return mrcqr_sketch_ex(m, n, A, lda, s, sketch_prec, seed, 0, Y, stream);
+}
+
+int mrcqr_sketch_ex(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, int sketch_prec, uint64_t seed,
+                    int variant, double* Y, mrcqr_stream_t stream) {
   if (!A || !Y || n < 1 || n > kMaxN || m < 1 || m >= (int64_t(1) << 31) || lda < m || s < 1 || s > m ||
       s > 8192)
     return MRCQR_ERR_INVALID;
@@ -379,9 +397,10 @@ int mrcqr_sketch(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, 
   double* ypart = at<double>(ws, p.off_ypart);
   launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, sketch_prec, P_FP64, P_FP64, P_FP64, kDefaultTol); });
   launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, (int)s, seed, idx, ctl, st); });
-  launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, st); });
+  launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, at<float>(ws, p.off_tabf), st); });
   launch(SG_SKETCH, 0, st, [&] {
-    launch_sketch(sketch_prec, A, lda, m, (int)n, (int)s, idx, tab, seed, p.chunks, ypart, ctl, 0, st);
+    g_sketch_variant_last = launch_sketch(sketch_prec, variant, A, lda, m, (int)n, (int)s, idx, tab,
+                                          at<float>(ws, p.off_tabf), seed, p.chunks, ypart, ctl, 0, st);
   });
   launch(SG_SKREDUCE, 0, st, [&] { launch_sketch_reduce(m, (int)n, (int)s, p.chunks, ypart, idx, Y, ctl, 0, st); });
   cudaFreeAsync(ws, st);
@@ -435,6 +454,8 @@ int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, con
 }
 
 uint64_t mrcqr_launch_count(void) { return g_launches.load(); }
+
+int mrcqr_last_sketch_variant(void) { return g_sketch_variant_last; }
 
 const char* mrcqr_stage_name(int stage) {
   return (stage >= 0 && stage < SG_COUNT) ? kStageNames[stage] : "unknown";

@@ -123,6 +123,146 @@ __device__ __forceinline__ double cos_phase(const double* __restrict__ tab, int6
   return __ldg(tab + r);
 }
 
+// cos(pi r / (2m)) as FP64 bits (hi, lo) from the same table, the sign
+// applied by XOR (no FP64 instruction).
+__device__ __forceinline__ void cos_phase_bits(const double* __restrict__ tab, int64_t r, int64_t m, uint32_t& hi,
+                                               uint32_t& lo) {
+  uint32_t neg = 0u;
+  if (r >= 2 * m) r = 4 * m - r;
+  if (r > m) {
+    r = 2 * m - r;
+    neg = 0x80000000u;
+  }
+  const uint2 w = __ldg(reinterpret_cast<const uint2*>(tab) + r);
+  lo = w.x;
+  hi = w.y ^ neg;
+}
+
+// Same phase from the FP32 copy of the table.
+__device__ __forceinline__ float cos_phase_f(const float* __restrict__ tabf, int64_t r, int64_t m) {
+  if (r >= 2 * m) r = 4 * m - r;
+  if (r > m) return -__ldg(tabf + (2 * m - r));
+  return __ldg(tabf + r);
+}
+
+// ---------------------------------------------------------------------------
+// fl_p on the FP64 bit pattern with 32-bit integer operations only.  On this
+// GPU every FP64 instruction (even a multiply by +-1, a compare or a
+// conversion) issues to the 1/64-rate FP64 pipe, so the per-element work of
+// the reduced-precision sketch avoids it: the Rademacher sign is an XOR of
+// bit 63 (as the paper's DiagMult does), the 2^e scaling adds e to the
+// exponent field, and rounding to FP16 / BF16 / FP32 is round-to-nearest-
+// even computed from the 52-bit mantissa (one rounding, subnormal targets
+// included).  x = (hi, lo) are the high and low words of the double.
+
+// RNE of the 53-bit significand M (implicit bit set) shifted right by sh
+// (1 <= sh <= 63): the subnormal-target path.
+__device__ __forceinline__ uint32_t rne_shift(uint64_t M, int sh) {
+  if (sh >= 64) return 0u;
+  uint64_t q = M >> sh;
+  const uint64_t rem = M & ((1ull << sh) - 1ull);
+  const uint64_t half = 1ull << (sh - 1);
+  q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+  return (uint32_t)q;
+}
+
+// Target formats: mantissa bits MB, exponent bias BIAS, minimum normal
+// unbiased exponent EMIN, maximum EMAX; returns the target bit pattern
+// (FP16/BF16 in the low 16 bits, FP32 in 32 bits).
+template <int MB, int BIAS, int EMIN, int EMAX, int SIGNSHIFT>
+__device__ __forceinline__ uint32_t f64bits_to(uint32_t hi, uint32_t lo) {
+  const uint32_t sign = (hi >> 31) << SIGNSHIFT;
+  const int E = (int)((hi >> 20) & 0x7FFu);
+  const uint32_t inf = (uint32_t)(EMAX + BIAS + 1) << MB;
+  if (E == 0x7FF) return sign | inf | (((hi & 0xFFFFFu) | lo) ? (1u << (MB - 1)) : 0u);
+  if (E == 0) return sign;   // FP64 zero or subnormal: below every target's range
+  const int u = E - 1023;
+  if (u > EMAX) return sign | inf;
+  if (u >= EMIN) {
+    // top MB mantissa bits: mantissa bits [51 .. 52-MB]
+    uint32_t mant, rbit, sticky;
+    if constexpr (MB <= 19) {
+      mant = (hi >> (20 - MB)) & ((1u << MB) - 1u);
+      rbit = (hi >> (19 - MB)) & 1u;
+      sticky = (hi & ((1u << (19 - MB)) - 1u)) | lo;
+    } else {   // FP32: 20 bits from hi, MB-20 from lo
+      mant = ((hi & 0xFFFFFu) << (MB - 20)) | (lo >> (52 - MB));
+      rbit = (lo >> (51 - MB)) & 1u;
+      sticky = lo & ((1u << (51 - MB)) - 1u);
+    }
+    uint32_t q = ((uint32_t)(u + BIAS) << MB) | mant;
+    q += rbit & ((sticky != 0u) | (q & 1u));   // carries into the exponent correctly
+    return sign | q;
+  }
+  // subnormal target: units of 2^(EMIN - MB)
+  const uint64_t M = (((uint64_t)(hi & 0xFFFFFu) << 32) | lo) | (1ull << 52);
+  return sign | rne_shift(M, 52 - (u - (EMIN - MB)));
+}
+
+__device__ __forceinline__ uint32_t f64bits_to_f16(uint32_t hi, uint32_t lo) {
+  return f64bits_to<10, 15, -14, 15, 15>(hi, lo);
+}
+__device__ __forceinline__ uint32_t f64bits_to_bf16(uint32_t hi, uint32_t lo) {
+  return f64bits_to<7, 127, -126, 127, 15>(hi, lo);
+}
+__device__ __forceinline__ uint32_t f64bits_to_f32(uint32_t hi, uint32_t lo) {
+  return f64bits_to<23, 127, -126, 127, 31>(hi, lo);
+}
+
+// x * 2^e on the bit pattern for finite normal x and a result that is still
+// normal or underflows to a value below every target format (flushed to a
+// signed zero, which the conversions above map to zero).  FP64 subnormal
+// inputs take the slow FP64 path.
+__device__ __forceinline__ void scale_bits(uint32_t& hi, uint32_t& lo, int e) {
+  const int E = (int)((hi >> 20) & 0x7FFu);
+  if (E == 0x7FF) return;
+  if (E == 0) {
+    if (((hi & 0xFFFFFu) | lo) == 0u) return;
+    double v = __hiloint2double((int)hi, (int)lo) * exp2i(e);
+    hi = (uint32_t)__double2hiint(v);
+    lo = (uint32_t)__double2loint(v);
+    return;
+  }
+  const int E2 = E + e;
+  if (E2 <= 0) {
+    hi &= 0x80000000u;
+    lo = 0u;
+    return;
+  }
+  hi = (hi & 0x800FFFFFu) | ((uint32_t)E2 << 20);
+}
+
+// x 2^e as FP32 bits, for x in the FP32 normal range after scaling, by
+// rounding to odd (truncate, OR the sticky bit into the last place).  A
+// later round-to-nearest-even to a format with at least two fewer bits
+// (FP16, BF16) then equals one direct rounding of x 2^e.  Returns false when
+// the scaled value leaves the FP32 normal range or x is not finite; the
+// caller then takes the exact slow path.
+__device__ __forceinline__ bool scaled_f32_rto(uint32_t hi, uint32_t lo, int e, uint32_t& out) {
+  const int E = (int)((hi >> 20) & 0x7FFu);
+  if (E == 0) {
+    out = hi & 0x80000000u;
+    return ((hi & 0xFFFFFu) | lo) == 0u;   // signed zero is fine, FP64 subnormal is not
+  }
+  const int u = E + e - 1023;
+  if (E == 0x7FF || u < -126 || u > 127) return false;
+  const uint32_t sticky = (lo & 0x1FFFFFFFu) != 0u ? 1u : 0u;
+  out = (hi & 0x80000000u) | ((uint32_t)(u + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29) | sticky;
+  return true;
+}
+
+// Exponent e with max|x| 2^e in [2^13, 2^14), from the high word of max|x|
+// (the exponent field orders like the value); zero or non-finite -> 0.
+__device__ __forceinline__ int scale_exponent_bits(uint32_t hi_abs_max, uint32_t lo_of_max) {
+  const int E = (int)(hi_abs_max >> 20);
+  if (E == 0x7FF) return 0;
+  if (E == 0) {
+    if ((hi_abs_max | lo_of_max) == 0u) return 0;
+    return scale_exponent(__hiloint2double((int)hi_abs_max, (int)lo_of_max));
+  }
+  return 1036 - E;   // frexp exponent ex = E - 1022, e = 14 - ex
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -8,13 +8,21 @@ namespace mrcqr {
 
 // --- sketch (sketch.cu) ------------------------------------------------------
 void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ctl, cudaStream_t st);
-void launch_costab(int64_t m, double* tab, cudaStream_t st);
+void launch_costab(int64_t m, double* tab, float* tabf, cudaStream_t st);
 int sketch_chunks(int64_t m, int n, int s);
-void launch_sketch(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,
-                   const double* tab, uint64_t seed, int chunks, double* Ypart, const Ctl* ctl, int level,
-                   cudaStream_t st);
+// variant: 0 = auto (tensor cores when eligible), 1 = SIMT, 2 = tensor cores (falls back to SIMT when
+// the TMA preconditions fail).  Returns the variant launched (1 or 2).
+int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m, int n, int s,
+                  const uint32_t* idx, const double* tab, const float* tabf, uint64_t seed, int chunks,
+                  double* Ypart, Ctl* ctl, int level, cudaStream_t st);
+// tensor-core sketch (sketch_tc.cu): FP16/BF16/FP32, A 16-byte aligned, lda even
+bool sketch_tc_eligible(int prec, const double* A, int64_t lda);
+bool launch_sketch_tc(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,
+                      const double* tab, const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl,
+                      int level, cudaStream_t st);
 void launch_sketch_reduce(int64_t m, int n, int s, int chunks, const double* Ypart, const uint32_t* idx,
                           double* Y, Ctl* ctl, int level, cudaStream_t st);
+void launch_round(int prec, int64_t count, const double* x, double* y, cudaStream_t st);
 // Signs of rows [0, m) as +-1 doubles (test entry point).
 void launch_signs(int64_t m, uint64_t seed, double* out, cudaStream_t st);
 

@@ -3,8 +3,8 @@
 // DCT-II, computed in the sketch precision p.
 //
 // This file holds the SIMT kernels (every precision; the FP64 sketch always
-// runs here because FP64 has no tensor-core path on this GPU); the tensor-core
-// FP16/BF16/TF32 sketch lives in sketch_tc.cu.
+// runs here because FP64 has no tensor-core path on this GPU) and the sketch
+// dispatch; the tensor-core FP16/BF16/FP32 sketch lives in sketch_tc.cu.
 #include <type_traits>
 #include "kernels.h"
 
@@ -87,15 +87,38 @@ void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ct
 }
 
 // ---------------------------------------------------------------------------
-// Quarter-wave table cos(pi q / (2m)), q = 0..m (FP64).
-__global__ void k_costab(int64_t m, double* __restrict__ tab) {
+// Quarter-wave table cos(pi q / (2m)), q = 0..m, in FP64 and rounded to FP32.
+__global__ void k_costab(int64_t m, double* __restrict__ tab, float* __restrict__ tabf) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q <= m) tab[q] = cospi((double)q / (2.0 * (double)m));
+  if (q <= m) {
+    const double c = cospi((double)q / (2.0 * (double)m));
+    tab[q] = c;
+    tabf[q] = (float)c;
+  }
 }
 
-void launch_costab(int64_t m, double* tab, cudaStream_t st) {
+void launch_costab(int64_t m, double* tab, float* tabf, cudaStream_t st) {
   const int64_t nq = m + 1;
-  k_costab<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(m, tab);
+  k_costab<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(m, tab, tabf);
+}
+
+// fl_p exactly as the tensor-core sketch computes it (integer RNE on the
+// FP64 bits), widened back to FP64.
+__global__ void k_round(int prec, int64_t count, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double v = x[i];
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  double r;
+  if (prec == P_FP16) r = (double)__half2float(__ushort_as_half((unsigned short)f64bits_to_f16(hi, lo)));
+  else if (prec == P_BF16) r = (double)__bfloat162float(__ushort_as_bfloat16((unsigned short)f64bits_to_bf16(hi, lo)));
+  else if (prec == P_FP32) r = (double)__uint_as_float(f64bits_to_f32(hi, lo));
+  else r = v;
+  y[i] = r;
+}
+
+void launch_round(int prec, int64_t count, const double* x, double* y, cudaStream_t st) {
+  k_round<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(prec, count, x, y);
 }
 
 __global__ void k_signs(int64_t m, uint2 key, double* __restrict__ out) {
@@ -240,12 +263,15 @@ int sketch_chunks(int64_t m, int n, int s) {
 
 static int64_t rows_per_chunk(int64_t m, int chunks) {
   int64_t r = (m + chunks - 1) / chunks;
-  return (r + kSkT - 1) / kSkT * kSkT;
+  return (r + 63) / 64 * 64;
 }
 
-void launch_sketch(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,
-                   const double* tab, uint64_t seed, int chunks, double* Ypart, const Ctl* ctl, int level,
-                   cudaStream_t st) {
+int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m, int n, int s,
+                  const uint32_t* idx, const double* tab, const float* tabf, uint64_t seed, int chunks,
+                  double* Ypart, Ctl* ctl, int level, cudaStream_t st) {
+  if (variant != 1 && sketch_tc_eligible(prec, A, lda) &&
+      launch_sketch_tc(prec, A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st))
+    return 2;
   const dim3 grid(chunks, (s + kSkST - 1) / kSkST, (n + kSkNT - 1) / kSkNT);
   const int64_t rpc = rows_per_chunk(m, chunks);
   const uint2 key = seed_key(seed);
@@ -255,6 +281,7 @@ void launch_sketch(int prec, const double* A, int64_t lda, int64_t m, int n, int
     case P_FP32: k_sketch_simt<P_FP32><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); break;
     default: k_sketch_simt<P_FP64><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); break;
   }
+  return 1;
 }
 
 // Y = sqrt(2/s) c_k * sum over chunks (fixed order), with c_0 = 1/sqrt(2):

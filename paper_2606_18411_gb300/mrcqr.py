@@ -61,10 +61,11 @@ def version() -> int:
 
 def factor_ex(A: torch.Tensor, Q: torch.Tensor, R: torch.Tensor, prec="fp64", seed: int = 0, s_factor: int = 2,
               check_ortho: bool = True, escalate: bool = True, tol: float = 1e-13, stats_device=None,
-              stream=None) -> None:
+              sketch_variant: int = 0, stream=None) -> None:
     """Enqueue MRCQR of A into Q (m x n) and R (n x n); asynchronous."""
     m, n = A.shape
-    o = Opts(s_factor=s_factor, check=int(check_ortho), escalate=int(escalate), reserved0=0, ortho_tol=tol,
+    o = Opts(s_factor=s_factor, check=int(check_ortho), escalate=int(escalate), sketch_variant=sketch_variant,
+             ortho_tol=tol,
              stats_device=stats_device.data_ptr() if stats_device is not None else None)
     rc = _lib.load().mrcqr_factor_ex(m, n, A.data_ptr(), _ld(A, "A"), Q.data_ptr(), _ld(Q, "Q"), R.data_ptr(),
                                      _ld(R, "R"), _prec(prec), seed, ctypes.byref(o), _stream(stream))
@@ -110,6 +111,14 @@ def factor_batched(As, Qs, Rs, precs, seeds, status: torch.Tensor, stream=None) 
     check(rc, "mrcqr_factor_batched")
 
 
+def round_to(prec, x: torch.Tensor, stream=None) -> torch.Tensor:
+    """fl_p(x) as the tensor-core sketch computes it, widened to float64."""
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    check(_lib.load().mrcqr_round(_prec(prec), x.numel(), x.data_ptr(), y.data_ptr(), _stream(stream)), "mrcqr_round")
+    return y
+
+
 def signs(m: int, seed: int, device="cuda", stream=None) -> torch.Tensor:
     d = torch.empty(m, dtype=torch.float64, device=device)
     check(_lib.load().mrcqr_signs(m, seed, d.data_ptr(), _stream(stream)), "mrcqr_signs")
@@ -122,12 +131,17 @@ def sample_rows(m: int, s: int, seed: int, device="cuda", stream=None) -> torch.
     return idx
 
 
-def sketch(A: torch.Tensor, s: int, prec="fp64", seed: int = 0, stream=None) -> torch.Tensor:
+def sketch(A: torch.Tensor, s: int, prec="fp64", seed: int = 0, variant: int = 0, stream=None) -> torch.Tensor:
+    """Y = sqrt(m/s) P F D A in precision prec (variant 0 auto, 1 SIMT, 2 tensor cores)."""
     m, n = A.shape
     Y = empty_colmajor(s, n, device=A.device)
-    check(_lib.load().mrcqr_sketch(m, n, A.data_ptr(), _ld(A, "A"), s, _prec(prec), seed, Y.data_ptr(),
-                                   _stream(stream)), "mrcqr_sketch")
+    check(_lib.load().mrcqr_sketch_ex(m, n, A.data_ptr(), _ld(A, "A"), s, _prec(prec), seed, variant, Y.data_ptr(),
+                                      _stream(stream)), "mrcqr_sketch_ex")
     return Y
+
+
+def last_sketch_variant() -> int:
+    return _lib.load().mrcqr_last_sketch_variant()
 
 
 def sketch_qr(Y: torch.Tensor, prec="fp64", stream=None) -> torch.Tensor:
