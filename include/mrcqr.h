@@ -109,17 +109,52 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
 int mrcqr_get_last_status(mrcqr_stream_t stream, mrcqr_stats_t* out);
 
 /* Many independent factorizations (the repeated QRs of block Krylov and
- * randomized-SVD power steps, Sec. II-C) in grouped launches.
+ * randomized-SVD power steps, Sec. II-C) in grouped launches over the whole
+ * batch (a one-shot plan, see mrcqr_batched_plan_create).
  *   count          : number of problems (>= 1).
  *   m, n, lda, ldq : HOST arrays[count] (used for planning).
  *   A, Q, R        : HOST arrays[count] of DEVICE pointers; R_i is n_i x n_i, ld n_i.
  *   sketch_prec    : HOST array[count] of mrcqr_prec_t (AUTO not accepted here).
  *   seeds          : HOST array[count].
  *   status         : DEVICE int32[count] receiving each problem's mrcqr_status_t.
- * Per-problem rules are those of mrcqr_factor; problems are independent. */
+ * Per-problem rules are those of mrcqr_factor with m >= 2n; problems are
+ * independent.  The workspace comes from the stream-ordered allocator. */
 int mrcqr_factor_batched(int count, const int64_t* m, const int64_t* n, const double* const* A, const int64_t* lda,
                          double* const* Q, const int64_t* ldq, double* const* R, const int* sketch_prec,
                          const uint64_t* seeds, int32_t* status, mrcqr_stream_t stream);
+
+/* Reusable batched plans.  A plan owns the batch workspace (allocated once)
+ * and the per-phase work lists; executing it enqueues one grouped launch per
+ * phase and kernel variant (about 20 per escalation level for the whole
+ * batch) or, with use_graph, replays them as one CUDA graph (captured at the
+ * first execute on a private stream, then launched on the caller's stream).
+ * The buffers named at creation are the ones every execute reads and writes.
+ * autotune = 1 times the grouped SYRK and sketch kernels on this batch for
+ * a few split sizes at creation (synchronous; results cached per batch shape
+ * and, when the environment variable MRCQR_TUNE_CACHE names a file, stored
+ * there). */
+typedef struct mrcqr_batched_plan_s* mrcqr_batched_plan_t;
+
+typedef struct mrcqr_batched_opts {
+  int32_t use_graph;      /* 1: capture the launch sequence into a CUDA graph */
+  int32_t autotune;       /* 1: tune rows_per_split / rows_per_chunk at creation */
+  int32_t check;          /* 1 (default): device orthogonality judge */
+  int32_t escalate;       /* 1 (default): re-run failed problems at the next precision */
+  double ortho_tol;       /* default 1e-13 */
+  int64_t rows_per_split; /* SYRK rows per partial (0: tuned or default 4096) */
+  int64_t rows_per_chunk; /* sketch rows per partial (0: tuned or default 8192) */
+} mrcqr_batched_opts_t;
+
+int mrcqr_batched_plan_create(int count, const int64_t* m, const int64_t* n, const double* const* A,
+                              const int64_t* lda, double* const* Q, const int64_t* ldq, double* const* R,
+                              const int* sketch_prec, const uint64_t* seeds, int32_t* status,
+                              const mrcqr_batched_opts_t* opts, mrcqr_batched_plan_t* plan);
+int mrcqr_batched_plan_execute(mrcqr_batched_plan_t plan, mrcqr_stream_t stream);
+/* Tuned sizes, launches per execute and workspace bytes of a plan (host outputs, any may be NULL). */
+int mrcqr_batched_plan_info(mrcqr_batched_plan_t plan, int64_t* rows_per_split, int64_t* rows_per_chunk,
+                            int32_t* kernels_per_execute, int64_t* workspace_bytes);
+/* Frees the plan; the caller must first make sure no execute is in flight. */
+int mrcqr_batched_plan_destroy(mrcqr_batched_plan_t plan);
 
 /* ---- step-level entry points (each is one step of Algorithm 2) ---------- */
 

@@ -26,6 +26,12 @@ class Opts(ctypes.Structure):
                 ("sketch_variant", ctypes.c_int32), ("ortho_tol", ctypes.c_double), ("stats_device", ctypes.c_void_p)]
 
 
+class BatchedOpts(ctypes.Structure):
+    _fields_ = [("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32), ("check", ctypes.c_int32),
+                ("escalate", ctypes.c_int32), ("ortho_tol", ctypes.c_double), ("rows_per_split", ctypes.c_int64),
+                ("rows_per_chunk", ctypes.c_int64)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("prec_used", ctypes.c_int32), ("retries", ctypes.c_int32),
                 ("prec_first", ctypes.c_int32), ("selector_choice", ctypes.c_int32),
@@ -52,6 +58,14 @@ SIGNATURES = {
     "mrcqr_factor_batched": ([_i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_vp),
                               ctypes.POINTER(_i64), ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_vp),
                               ctypes.POINTER(_i32), ctypes.POINTER(_u64), _vp, _vp], _i32),
+    "mrcqr_batched_plan_create": ([_i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_vp),
+                                   ctypes.POINTER(_i64), ctypes.POINTER(_vp), ctypes.POINTER(_i64),
+                                   ctypes.POINTER(_vp), ctypes.POINTER(_i32), ctypes.POINTER(_u64), _vp,
+                                   ctypes.POINTER(BatchedOpts), ctypes.POINTER(_vp)], _i32),
+    "mrcqr_batched_plan_execute": ([_vp, _vp], _i32),
+    "mrcqr_batched_plan_info": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.POINTER(_i64)], _i32),
+    "mrcqr_batched_plan_destroy": ([_vp], _i32),
     "mrcqr_signs": ([_i64, _u64, _vp, _vp], _i32),
     "mrcqr_sample_rows": ([_i64, _i64, _u64, _vp, _vp], _i32),
     "mrcqr_round": ([_i32, _i64, _vp, _vp, _vp], _i32),

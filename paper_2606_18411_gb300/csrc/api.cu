@@ -323,34 +323,6 @@ int mrcqr_get_last_status(mrcqr_stream_t stream, mrcqr_stats_t* out) {
   return MRCQR_OK;
 }
 
-int mrcqr_factor_batched(int count, const int64_t* m, const int64_t* n, const double* const* A, const int64_t* lda,
-                         double* const* Q, const int64_t* ldq, double* const* R, const int* sketch_prec,
-                         const uint64_t* seeds, int32_t* status, mrcqr_stream_t stream) {
-  if (count < 1 || !m || !n || !A || !lda || !Q || !ldq || !R || !sketch_prec || !seeds || !status)
-    return MRCQR_ERR_INVALID;
-  for (int i = 0; i < count; ++i) {
-    const int rc = validate(m[i], n[i], A[i], lda[i], Q[i], ldq[i], R[i], n[i], 2);
-    if (rc != MRCQR_OK) return rc;
-    if (sketch_prec[i] < P_FP16 || sketch_prec[i] > P_FP64) return MRCQR_ERR_INVALID;
-  }
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  for (int i = 0; i < count; ++i) {
-    mrcqr_opts_t o{};
-    o.s_factor = 2;
-    o.check = 1;
-    o.escalate = 1;
-    o.ortho_tol = kDefaultTol;
-    o.stats_device = nullptr;
-    mrcqr_stats_t* slot = status_slot(st);
-    if (!slot) return MRCQR_ERR_ALLOC;
-    const int rc = mrcqr_factor_ex(m[i], n[i], A[i], lda[i], Q[i], ldq[i], R[i], n[i], sketch_prec[i], seeds[i], &o,
-                                   stream);
-    if (rc != MRCQR_OK) return rc;
-    cudaMemcpyAsync(status + i, &slot->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-  }
-  return finish(st);
-}
-
 int mrcqr_signs(int64_t m, uint64_t seed, double* d, mrcqr_stream_t stream) {
   if (!d || m < 1 || m >= (int64_t(1) << 31)) return MRCQR_ERR_INVALID;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -6,6 +6,62 @@
 
 namespace mrcqr {
 
+// One problem of a grouped (batched) launch: caller buffers, shape, tuned
+// split sizes and its slice of the batch workspace.
+struct Prob {
+  const double* A;
+  double* Q;
+  double* R;
+  int64_t lda, ldq, ldr;
+  int64_t m;
+  int n, s, npad, chunks, splits, ntile_syrk, check, nlevels;
+  int lvl_prec[kMaxLevels];
+  int64_t rows_per_chunk, rows_per_split;
+  uint2 key;
+  double tol;
+  Ctl* ctl;
+  uint32_t* idx;
+  double* tab;
+  float* tabf;
+  double* ypart;
+  double* y;
+  void* sqrw;
+  double* rs;
+  double* rst;
+  double* rinv;
+  double* gpart;
+  double* rc;
+  double* xt;
+  double* e;
+  int32_t* status;   // caller's status entry
+};
+
+// A grouped launch walks a list of work items {problem, a, b, c} with a
+// grid-stride loop; every item skips itself unless its problem's control
+// block names the launch's escalation level.
+struct Group {
+  const Prob* probs;
+  const int4* items;
+  int nitems;
+};
+
+void prepare_g_kernels(int max_s);   // kernel attributes; call outside stream capture
+void launch_g_init(const Group& g, cudaStream_t st);
+void launch_g_sample(const Group& g, int max_s, cudaStream_t st);
+void launch_g_costab(const Group& g, cudaStream_t st);
+void launch_g_sketch(const Group& g, int prec, int level, cudaStream_t st);
+void launch_g_sketch_reduce(const Group& g, int level, cudaStream_t st);
+void launch_g_sketch_qr(const Group& g, bool fp64, int level, cudaStream_t st);
+void launch_g_trsm(const Group& g, int level, cudaStream_t st);
+void launch_g_syrk(const Group& g, int tn, bool check, int level, cudaStream_t st);
+void launch_g_reduce(const Group& g, bool check, int level, cudaStream_t st);
+void launch_g_chol(const Group& g, int level, cudaStream_t st);
+void launch_g_trinv(const Group& g, int level, cudaStream_t st);
+void launch_g_rmul(const Group& g, int level, cudaStream_t st);
+void launch_g_finalize(const Group& g, int level, cudaStream_t st);
+void launch_g_judge(const Group& g, int level, cudaStream_t st);
+void launch_g_publish(const Group& g, cudaStream_t st);
+
 // --- sketch (sketch.cu) ------------------------------------------------------
 void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ctl, cudaStream_t st);
 void launch_costab(int64_t m, double* tab, float* tabf, cudaStream_t st);
@@ -36,6 +92,7 @@ void launch_rs_prepare(int n, const double* Rs, double* RsT, double* rinv, cudaS
 void launch_trsm(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv,
                  double* W, int64_t ldw, const Ctl* ctl, int level, cudaStream_t st);
 int syrk_splits(int64_t m, int n);
+int syrk_tile_for(int n);
 void launch_syrk(int64_t m, int n, const double* X, int64_t ldx, int splits, double* Gpart, const Ctl* ctl,
                  int level, cudaStream_t st);
 void launch_reduce_partials(int n, int splits, const double* part, double* out, const Ctl* ctl, int level,

@@ -18,8 +18,7 @@ namespace mrcqr {
 // keeps j (never chosen before, since all earlier values are < j).
 constexpr uint32_t kEmpty = 0xffffffffu;
 
-__global__ void __launch_bounds__(1024) k_sample(int64_t m, int s, uint2 key, uint32_t* __restrict__ idx,
-                                                  const Ctl* ctl) {
+__device__ __forceinline__ void sample_block(int64_t m, int s, uint2 key, uint32_t* __restrict__ idx) {
   extern __shared__ uint32_t sm[];
   int H = 1;
   while (H < 2 * s) H <<= 1;
@@ -74,6 +73,13 @@ __global__ void __launch_bounds__(1024) k_sample(int64_t m, int s, uint2 key, ui
     }
   }
   for (int t = threadIdx.x; t < s; t += blockDim.x) idx[t] = keys[t];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_sample(int64_t m, int s, uint2 key, uint32_t* __restrict__ idx,
+                                                  const Ctl* ctl) {
+  (void)ctl;
+  sample_block(m, s, key, idx);
 }
 
 void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ctl, cudaStream_t st) {
@@ -142,12 +148,10 @@ void launch_signs(int64_t m, uint64_t seed, double* out, cudaStream_t st) {
 constexpr int kSkST = 64, kSkNT = 64, kSkT = 32;
 
 template <int PREC>
-__global__ void __launch_bounds__(256) k_sketch_simt(const double* __restrict__ A, int64_t lda, int64_t m, int n,
-                                                      int s, const uint32_t* __restrict__ idx,
-                                                      const double* __restrict__ tab, uint2 key,
-                                                      int64_t rows_per_chunk, double* __restrict__ Ypart,
-                                                      const Ctl* ctl, int level) {
-  if (level_inactive(ctl, level)) return;
+__device__ __forceinline__ void sketch_simt_block(const double* __restrict__ A, int64_t lda, int64_t m, int n, int s,
+                                                  const uint32_t* __restrict__ idx, const double* __restrict__ tab,
+                                                  uint2 key, int64_t rows_per_chunk, double* __restrict__ Ypart,
+                                                  int bx, int by, int bz) {
   using Acc = std::conditional_t<PREC == P_FP64, double, float>;
   constexpr int ST = kSkST, NT = kSkNT, T = kSkT;
   __shared__ double Xd[T][NT + 1];
@@ -161,8 +165,8 @@ __global__ void __launch_bounds__(256) k_sketch_simt(const double* __restrict__ 
 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int s0 = blockIdx.y * ST, n0 = blockIdx.z * NT;
-  const int64_t j_begin = (int64_t)blockIdx.x * rows_per_chunk;
+  const int s0 = by * ST, n0 = bz * NT;
+  const int64_t j_begin = (int64_t)bx * rows_per_chunk;
   const int64_t j_end = min(m, j_begin + rows_per_chunk);
   const uint64_t four_m = 4ull * (uint64_t)m;
   if (tid < ST) ks[tid] = (s0 + tid < s) ? idx[s0 + tid] : kEmpty;
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(256) k_sketch_simt(const double* __restrict__ 
         else acc[r][c] = fma(tmp[r][c], colscale[tx * 4 + c], acc[r][c]);
       }
   }
-  double* out = Ypart + (size_t)blockIdx.x * (size_t)s * (size_t)n;
+  double* out = Ypart + (size_t)bx * (size_t)s * (size_t)n;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -250,6 +254,17 @@ __global__ void __launch_bounds__(256) k_sketch_simt(const double* __restrict__ 
       const int i = s0 + ty * 4 + r, col = n0 + tx * 4 + c;
       if (i < s && col < n) out[(size_t)col * s + i] = (double)acc[r][c];
     }
+  __syncthreads();
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_sketch_simt(const double* __restrict__ A, int64_t lda, int64_t m, int n,
+                                                      int s, const uint32_t* __restrict__ idx,
+                                                      const double* __restrict__ tab, uint2 key,
+                                                      int64_t rows_per_chunk, double* __restrict__ Ypart,
+                                                      const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level)) return;
+  sketch_simt_block<PREC>(A, lda, m, n, s, idx, tab, key, rows_per_chunk, Ypart, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 int sketch_chunks(int64_t m, int n, int s) {
@@ -286,12 +301,10 @@ int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m
 
 // Y = sqrt(2/s) c_k * sum over chunks (fixed order), with c_0 = 1/sqrt(2):
 // the sqrt(m/s) sketch scale times the sqrt(2/m) c_k of the orthonormal DCT.
-__global__ void k_sketch_reduce(int n, int s, int chunks, const double* __restrict__ Ypart,
-                                const uint32_t* __restrict__ idx, double* __restrict__ Y, Ctl* ctl, int level) {
-  if (level_inactive(ctl, level)) return;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sketch_reduce_entry(int n, int s, int chunks, const double* __restrict__ Ypart,
+                                                    const uint32_t* __restrict__ idx, double* __restrict__ Y,
+                                                    Ctl* ctl, int64_t e) {
   const int64_t total = (int64_t)s * n;
-  if (e >= total) return;
   const int i = (int)(e % s);
   double acc = 0.0;
   for (int c = 0; c < chunks; ++c) acc += Ypart[(size_t)c * total + e];
@@ -304,11 +317,123 @@ __global__ void k_sketch_reduce(int n, int s, int chunks, const double* __restri
   }
 }
 
+__global__ void k_sketch_reduce(int n, int s, int chunks, const double* __restrict__ Ypart,
+                                const uint32_t* __restrict__ idx, double* __restrict__ Y, Ctl* ctl, int level) {
+  if (level_inactive(ctl, level)) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (int64_t)s * n) sketch_reduce_entry(n, s, chunks, Ypart, idx, Y, ctl, e);
+}
+
 void launch_sketch_reduce(int64_t m, int n, int s, int chunks, const double* Ypart, const uint32_t* idx, double* Y,
                           Ctl* ctl, int level, cudaStream_t st) {
   (void)m;
   const int64_t total = (int64_t)s * n;
   k_sketch_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, chunks, Ypart, idx, Y, ctl, level);
+}
+
+// ---------------------------------------------------------------------------
+// Grouped kernels (batched factorizations).
+namespace {
+
+constexpr int kGridCapS = 152 * 8;
+inline unsigned gridS(int nitems) { return (unsigned)(nitems < kGridCapS ? (nitems > 0 ? nitems : 1) : kGridCapS); }
+
+__global__ void kg_init(Group g) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.nitems) return;
+  const Prob& P = g.probs[p];
+  Ctl* c = P.ctl;
+  c->active = 0;
+  c->lvl_status = 0;
+  c->final_status = ST_OK;
+  c->prec_used = P.lvl_prec[0];
+  c->retries = 0;
+  c->prec_first = P.lvl_prec[0];
+  c->nlevels = P.nlevels;
+  c->input_nonfinite = 0;
+  for (int i = 0; i < kMaxLevels; ++i) c->lvl_prec[i] = P.lvl_prec[i];
+  c->mlp_choice = -1;
+  c->pad0 = 0;
+  c->tol = P.tol;
+  c->ortho_fro = 0.0;
+  for (int i = 0; i < kNumFeatures; ++i) c->features[i] = 0.f;
+}
+
+__global__ void __launch_bounds__(1024) kg_sample(Group g) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const Prob& P = g.probs[g.items[it].x];
+    sample_block(P.m, P.s, P.key, P.idx);
+  }
+}
+
+__global__ void kg_costab(Group g) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    const int64_t q = (int64_t)w.y * 256 + threadIdx.x;
+    if (q <= P.m) {
+      const double c = cospi((double)q / (2.0 * (double)P.m));
+      P.tab[q] = c;
+      P.tabf[q] = (float)c;
+    }
+  }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) kg_sketch(Group g, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (P.ctl->active != level) continue;
+    sketch_simt_block<PREC>(P.A, P.lda, P.m, P.n, P.s, P.idx, P.tab, P.key, P.rows_per_chunk, P.ypart, w.y, w.z,
+                            w.w);
+  }
+}
+
+__global__ void kg_sketch_reduce(Group g, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (P.ctl->active != level) continue;
+    const int64_t e = (int64_t)w.y * 256 + threadIdx.x;
+    if (e < (int64_t)P.s * P.n) sketch_reduce_entry(P.n, P.s, P.chunks, P.ypart, P.idx, P.y, P.ctl, e);
+  }
+}
+
+}  // namespace
+
+void launch_g_init(const Group& g, cudaStream_t st) {
+  if (g.nitems) kg_init<<<(g.nitems + 127) / 128, 128, 0, st>>>(g);
+}
+static size_t g_sample_smem(int max_s) {
+  int H = 1;
+  while (H < 2 * max_s) H <<= 1;
+  int P = 1;
+  while (P < max_s) P <<= 1;
+  return sizeof(uint32_t) * (size_t)(max_s + H + P);
+}
+
+void prepare_g_kernels(int max_s) {
+  cudaFuncSetAttribute(kg_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_sample_smem(max_s));
+}
+
+void launch_g_sample(const Group& g, int max_s, cudaStream_t st) {
+  if (g.nitems) kg_sample<<<gridS(g.nitems), 1024, g_sample_smem(max_s), st>>>(g);
+}
+void launch_g_costab(const Group& g, cudaStream_t st) {
+  if (g.nitems) kg_costab<<<gridS(g.nitems), 256, 0, st>>>(g);
+}
+void launch_g_sketch(const Group& g, int prec, int level, cudaStream_t st) {
+  if (!g.nitems) return;
+  switch (prec) {
+    case P_FP16: kg_sketch<P_FP16><<<gridS(g.nitems), 256, 0, st>>>(g, level); break;
+    case P_BF16: kg_sketch<P_BF16><<<gridS(g.nitems), 256, 0, st>>>(g, level); break;
+    case P_FP32: kg_sketch<P_FP32><<<gridS(g.nitems), 256, 0, st>>>(g, level); break;
+    default: kg_sketch<P_FP64><<<gridS(g.nitems), 256, 0, st>>>(g, level); break;
+  }
+}
+void launch_g_sketch_reduce(const Group& g, int level, cudaStream_t st) {
+  if (g.nitems) kg_sketch_reduce<<<gridS(g.nitems), 256, 0, st>>>(g, level);
 }
 
 }  // namespace mrcqr

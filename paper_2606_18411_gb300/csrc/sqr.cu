@@ -19,12 +19,9 @@ constexpr int kPadCols = 32;
 __host__ __device__ inline int padded(int n) { return (n + kPadCols - 1) / kPadCols * kPadCols; }
 
 template <typename T>
-__global__ void __launch_bounds__(kSqrThreads) k_sketch_qr(int n, int s, const double* __restrict__ Y,
-                                                           T* __restrict__ W, double* __restrict__ Rs,
-                                                           double* __restrict__ RsT, double* __restrict__ rinv,
-                                                           Ctl* ctl, int level) {
-  if (level_inactive(ctl, level)) return;
-  if (ctl->lvl_status != 0) return;
+__device__ __forceinline__ void sketch_qr_block(int n, int s, const double* __restrict__ Y, T* __restrict__ W,
+                                                double* __restrict__ Rs, double* __restrict__ RsT,
+                                                double* __restrict__ rinv) {
   __shared__ T red[33];
   __shared__ T diag[512];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -92,6 +89,17 @@ __global__ void __launch_bounds__(kSqrThreads) k_sketch_qr(int n, int s, const d
     if (c < n) Rs[(int64_t)c * n + r] = v;
   }
   for (int r = tid; r < npad; r += blockDim.x) rinv[r] = r < n ? 1.0 / fabs((double)diag[r]) : 0.0;
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSqrThreads) k_sketch_qr(int n, int s, const double* __restrict__ Y,
+                                                           T* __restrict__ W, double* __restrict__ Rs,
+                                                           double* __restrict__ RsT, double* __restrict__ rinv,
+                                                           Ctl* ctl, int level) {
+  if (level_inactive(ctl, level)) return;
+  if (ctl->lvl_status != 0) return;
+  sketch_qr_block<T>(n, s, Y, W, Rs, RsT, rinv);
 }
 
 size_t sqr_workspace_bytes(int n, int s) { return (size_t)n * (size_t)s * sizeof(double); }
@@ -124,6 +132,27 @@ __global__ void k_rs_prepare(int n, const double* __restrict__ Rs, double* __res
 void launch_rs_prepare(int n, const double* Rs, double* RsT, double* rinv, cudaStream_t st) {
   const int64_t tot = (int64_t)n * padded(n);
   k_rs_prepare<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, Rs, RsT, rinv);
+}
+
+// Grouped sketch QR: one CTA per problem.
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(kSqrThreads) kg_sketch_qr(Group g, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const Prob& P = g.probs[g.items[it].x];
+    if (P.ctl->active != level || P.ctl->lvl_status != 0) continue;
+    sketch_qr_block<T>(P.n, P.s, P.y, static_cast<T*>(P.sqrw), P.rs, P.rst, P.rinv);
+  }
+}
+
+}  // namespace
+
+void launch_g_sketch_qr(const Group& g, bool fp64, int level, cudaStream_t st) {
+  if (!g.nitems) return;
+  const unsigned grid = (unsigned)(g.nitems < 152 * 2 ? g.nitems : 152 * 2);
+  if (fp64) kg_sketch_qr<double><<<grid, kSqrThreads, 0, st>>>(g, level);
+  else kg_sketch_qr<float><<<grid, kSqrThreads, 0, st>>>(g, level);
 }
 
 }  // namespace mrcqr

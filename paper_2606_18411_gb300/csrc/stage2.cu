@@ -24,12 +24,9 @@ static inline int padded(int n) { return (n + kPad - 1) / kPad * kPad; }
 // columns are read back from W (the Q buffer).  R_s comes transposed
 // (row-major, row stride npad, zero padding) so a row segment is one
 // contiguous uniform load.
-__global__ void __launch_bounds__(128) k_trsm(int64_t m, int n, const double* __restrict__ A, int64_t lda,
-                                              const double* __restrict__ RT, const double* __restrict__ rinv,
-                                              double* __restrict__ W, int64_t ldw, const Ctl* ctl, int level) {
-  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= m) return;
+__device__ __forceinline__ void trsm_row(int64_t r, int n, const double* __restrict__ A, int64_t lda,
+                                         const double* __restrict__ RT, const double* __restrict__ rinv,
+                                         double* __restrict__ W, int64_t ldw) {
   const int npad = (n + kPad - 1) / kPad * kPad;
   for (int J0 = 0; J0 < n; J0 += kNC) {
     double t[kNC];
@@ -60,6 +57,14 @@ __global__ void __launch_bounds__(128) k_trsm(int64_t m, int n, const double* __
   }
 }
 
+__global__ void __launch_bounds__(128) k_trsm(int64_t m, int n, const double* __restrict__ A, int64_t lda,
+                                              const double* __restrict__ RT, const double* __restrict__ rinv,
+                                              double* __restrict__ W, int64_t ldw, const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < m) trsm_row(r, n, A, lda, RT, rinv, W, ldw);
+}
+
 void launch_trsm(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv, double* W,
                  int64_t ldw, const Ctl* ctl, int level, cudaStream_t st) {
   k_trsm<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(m, n, A, lda, RT, rinv, W, ldw, ctl, level);
@@ -74,17 +79,16 @@ void launch_trsm(int64_t m, int n, const double* A, int64_t lda, const double* R
 // li*4..+4 and columns lj*2..+2 of its block.  Partials are summed in a
 // fixed order by the consumer (deterministic).
 template <int TN>
-__global__ void __launch_bounds__(32 * (TN / 16) * (TN / 16)) k_syrk(int64_t m, int n, const double* __restrict__ X, int64_t ldx,
-                                                          int64_t rows_per_split, int ntile,
-                                                          double* __restrict__ Gpart, const Ctl* ctl, int level) {
-  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+__device__ __forceinline__ void syrk_block(int64_t m, int n, const double* __restrict__ X, int64_t ldx,
+                                           int64_t rows_per_split, int ntile, double* __restrict__ Gpart,
+                                           int tile, int split) {
   constexpr int KB = 32;
   constexpr int NB = TN / 16;          // 16x16 blocks per tile side
   constexpr int NT = 32 * NB * NB;     // threads
   __shared__ __align__(16) double Xi[KB][TN];
   __shared__ __align__(16) double Xj[KB][TN];
   // tile index -> (ti, tj), ti <= tj, row-major over the upper triangle
-  int t = blockIdx.x, ti = 0;
+  int t = tile, ti = 0;
   while (t >= ntile - ti) { t -= ntile - ti; ++ti; }
   const int tj = ti + t;
   const int i0 = ti * TN, j0 = tj * TN;
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(32 * (TN / 16) * (TN / 16)) k_syrk(int64_t m, 
   const bool active = !(ti == tj && bi > bj);
   const int li = lane & 3, lj = lane >> 2;
   const int rbase = bi * 16 + li * 4, cbase = bj * 16 + lj * 2;
-  const int64_t k_begin = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t k_begin = (int64_t)split * rows_per_split;
   const int64_t k_end = min(m, k_begin + rows_per_split);
   double acc[4][2];
 #pragma unroll
@@ -124,8 +128,9 @@ __global__ void __launch_bounds__(32 * (TN / 16) * (TN / 16)) k_syrk(int64_t m, 
       }
     }
   }
+  __syncthreads();
   if (!active) return;
-  double* out = Gpart + (size_t)blockIdx.y * (size_t)n * (size_t)n;
+  double* out = Gpart + (size_t)split * (size_t)n * (size_t)n;
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -135,7 +140,17 @@ __global__ void __launch_bounds__(32 * (TN / 16) * (TN / 16)) k_syrk(int64_t m, 
     }
 }
 
+template <int TN>
+__global__ void __launch_bounds__(32 * (TN / 16) * (TN / 16)) k_syrk(int64_t m, int n, const double* __restrict__ X,
+                                                                      int64_t ldx, int64_t rows_per_split, int ntile,
+                                                                      double* __restrict__ Gpart, const Ctl* ctl,
+                                                                      int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  syrk_block<TN>(m, n, X, ldx, rows_per_split, ntile, Gpart, blockIdx.x, blockIdx.y);
+}
+
 static int syrk_tile(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : 64); }
+int syrk_tile_for(int n) { return syrk_tile(n); }
 
 int syrk_splits(int64_t m, int n) {
   const int TN = syrk_tile(n);
@@ -164,17 +179,21 @@ void launch_syrk(int64_t m, int n, const double* X, int64_t ldx, int splits, dou
 // ---------------------------------------------------------------------------
 // Sum of the per-split Gram partials, upper triangle, in a fixed order (one
 // thread per entry; deterministic).  Lower triangle set to zero.
-__global__ void k_reduce_partials(int n, int splits, const double* __restrict__ part, double* __restrict__ out,
-                                  const Ctl* ctl, int level) {
-  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+__device__ __forceinline__ void reduce_partial_entry(int n, int splits, const double* __restrict__ part,
+                                                     double* __restrict__ out, int64_t e) {
   const int64_t nn = (int64_t)n * n;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nn) return;
   const int i = (int)(e % n), j = (int)(e / n);
   double v = 0.0;
   if (i <= j)
     for (int sp = 0; sp < splits; ++sp) v += part[(size_t)sp * nn + e];
   out[e] = v;
+}
+
+__global__ void k_reduce_partials(int n, int splits, const double* __restrict__ part, double* __restrict__ out,
+                                  const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (int64_t)n * n) reduce_partial_entry(n, splits, part, out, e);
 }
 
 void launch_reduce_partials(int n, int splits, const double* part, double* out, const Ctl* ctl, int level,
@@ -188,8 +207,8 @@ void launch_reduce_partials(int n, int splits, const double* part, double* out, 
 // upper with positive diagonal, in place on the reduced upper triangle with
 // right-looking elimination (one CTA).  A non-positive or non-finite pivot
 // raises BREAKDOWN for this level.
-__global__ void __launch_bounds__(1024) k_chol(int n, double* __restrict__ G, Ctl* ctl, int level) {
-  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+// Returns false (for every thread) on breakdown.
+__device__ __forceinline__ bool chol_block(int n, double* __restrict__ G) {
   const int tid = threadIdx.x;
   const int64_t nn = (int64_t)n * n;
   __shared__ double piv;
@@ -202,8 +221,8 @@ __global__ void __launch_bounds__(1024) k_chol(int n, double* __restrict__ G, Ct
     __syncthreads();
     const double p = piv;
     if (!(p > 0.0)) {
-      if (tid == 0) raise_level_status(ctl, ST_BREAKDOWN);
-      return;
+      __syncthreads();
+      return false;
     }
     const double ip = 1.0 / p;
     for (int j = k + 1 + tid; j < n; j += blockDim.x) G[(int64_t)j * n + k] *= ip;   // row k
@@ -222,6 +241,13 @@ __global__ void __launch_bounds__(1024) k_chol(int n, double* __restrict__ G, Ct
     const int i = (int)(e % n), j = (int)(e / n);
     if (i > j) G[e] = 0.0;
   }
+  __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(1024) k_chol(int n, double* __restrict__ G, Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  if (!chol_block(n, G) && threadIdx.x == 0) raise_level_status(ctl, ST_BREAKDOWN);
 }
 
 void launch_chol(int n, double* G, Ctl* ctl, int level, cudaStream_t st) {
@@ -236,11 +262,8 @@ void launch_chol(int n, double* G, Ctl* ctl, int level, cudaStream_t st) {
 // ill-conditioned R_s (Sec. II-A).  Output transposed: XT[k][j] = X[k][j]
 // stored row-major with row stride npad, zeros below the diagonal and in
 // the padding.
-__global__ void k_trinv(int n, const double* __restrict__ Rc, double* __restrict__ XT, const Ctl* ctl, int level) {
-  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void trinv_column(int n, const double* __restrict__ Rc, double* __restrict__ XT, int j) {
   const int npad = (n + kPad - 1) / kPad * kPad;
-  if (j >= npad) return;
   for (int i = j + 1; i < n; ++i) XT[(int64_t)i * npad + j] = 0.0;
   if (j >= n) {
     for (int i = 0; i < n; ++i) XT[(int64_t)i * npad + j] = 0.0;
@@ -254,6 +277,13 @@ __global__ void k_trinv(int n, const double* __restrict__ Rc, double* __restrict
   }
 }
 
+__global__ void k_trinv(int n, const double* __restrict__ Rc, double* __restrict__ XT, const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int npad = (n + kPad - 1) / kPad * kPad;
+  if (j < npad) trinv_column(n, Rc, XT, j);
+}
+
 void launch_trinv(int n, const double* Rc, double* RcinvT, const Ctl* ctl, int level, cudaStream_t st) {
   const int npad = padded(n);
   k_trinv<<<(npad + 63) / 64, 64, 0, st>>>(n, Rc, RcinvT, ctl, level);
@@ -261,15 +291,19 @@ void launch_trinv(int n, const double* Rc, double* RcinvT, const Ctl* ctl, int l
 
 // R = R_c R_s (Algorithm 2 step 9), upper x upper; R col-major with ld ldr,
 // strict lower triangle set to zero.
-__global__ void k_rmul(int n, const double* __restrict__ Rc, const double* __restrict__ Rs, double* __restrict__ R,
-                       int64_t ldr, const Ctl* ctl, int level) {
-  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)n * n) return;
+__device__ __forceinline__ void rmul_entry(int n, const double* __restrict__ Rc, const double* __restrict__ Rs,
+                                           double* __restrict__ R, int64_t ldr, int64_t e) {
   const int i = (int)(e % n), j = (int)(e / n);
   double acc = 0.0;
   for (int k = i; k <= j; ++k) acc = fma(Rc[(int64_t)k * n + i], Rs[(int64_t)j * n + k], acc);
   R[(int64_t)j * ldr + i] = (i <= j) ? acc : 0.0;
+}
+
+__global__ void k_rmul(int n, const double* __restrict__ Rc, const double* __restrict__ Rs, double* __restrict__ R,
+                       int64_t ldr, const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (int64_t)n * n) rmul_entry(n, Rc, Rs, R, ldr, e);
 }
 
 void launch_rmul(int n, const double* Rc, const double* Rs, double* R, int64_t ldr, const Ctl* ctl, int level,
@@ -282,11 +316,8 @@ void launch_rmul(int n, const double* Rc, const double* Rs, double* R, int64_t l
 // Q = W X in place (X = R_c^{-1} upper): q_j = sum_{k<=j} w_k X_kj.  One
 // thread per row; column chunks right to left so every chunk reads only
 // columns that are still W.
-__global__ void __launch_bounds__(128) k_finalize(int64_t m, int n, double* __restrict__ Q, int64_t ldq,
-                                                  const double* __restrict__ XT, const Ctl* ctl, int level) {
-  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= m) return;
+__device__ __forceinline__ void finalize_row(int64_t r, int n, double* __restrict__ Q, int64_t ldq,
+                                             const double* __restrict__ XT) {
   const int npad = (n + kPad - 1) / kPad * kPad;
   const int last = (n - 1) / kNC * kNC;
   for (int J0 = last; J0 >= 0; J0 -= kNC) {
@@ -318,6 +349,13 @@ __global__ void __launch_bounds__(128) k_finalize(int64_t m, int n, double* __re
   }
 }
 
+__global__ void __launch_bounds__(128) k_finalize(int64_t m, int n, double* __restrict__ Q, int64_t ldq,
+                                                  const double* __restrict__ XT, const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < m) finalize_row(r, n, Q, ldq, XT);
+}
+
 void launch_finalize(int64_t m, int n, double* Q, int64_t ldq, const double* XT, const Ctl* ctl, int level,
                      cudaStream_t st) {
   k_finalize<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(m, n, Q, ldq, XT, ctl, level);
@@ -326,9 +364,9 @@ void launch_finalize(int64_t m, int n, double* Q, int64_t ldq, const double* XT,
 // ---------------------------------------------------------------------------
 // Judge (Sec. II-C): e = ||I - Q^T Q||_F from the check partials (fixed
 // order); accept, or escalate to the next level, or give up.
-__global__ void __launch_bounds__(1024) k_judge(int n, const double* __restrict__ E, int check, Ctl* ctl,
-                                                int level) {
-  if (level_inactive(ctl, level)) return;
+// One CTA: ||I - E||_F from the reduced check matrix, then accept / escalate /
+// give up (thread 0 writes the control block).
+__device__ __forceinline__ void judge_block(int n, const double* __restrict__ E, int check, Ctl* ctl, int level) {
   __shared__ double red[33];
   const int64_t nn = (int64_t)n * n;
   double part = 0.0;
@@ -342,33 +380,173 @@ __global__ void __launch_bounds__(1024) k_judge(int n, const double* __restrict_
     }
   }
   const double ss = block_sum(part, red);
-  if (threadIdx.x != 0) return;
-  const double e = run_check ? sqrt(ss) : 0.0;
-  const bool ok = ctl->lvl_status == 0 && e <= ctl->tol;   // NaN fails
-  if (ok) {
-    ctl->final_status = ST_OK;
-    ctl->prec_used = ctl->lvl_prec[level];
-    ctl->ortho_fro = e;
-    ctl->active = -1;
-  } else if (ctl->input_nonfinite) {
-    ctl->final_status = ST_NONFINITE;
-    ctl->prec_used = ctl->lvl_prec[level];
-    ctl->ortho_fro = e;
-    ctl->active = -1;
-  } else if (level + 1 < ctl->nlevels) {
-    ctl->retries += 1;
-    ctl->lvl_status = 0;
-    ctl->active = level + 1;
-  } else {
-    ctl->final_status = ctl->lvl_status ? ctl->lvl_status : ST_ORTHO;
-    ctl->prec_used = ctl->lvl_prec[level];
-    ctl->ortho_fro = e;
-    ctl->active = -1;
+  if (threadIdx.x == 0) {
+    const double e = run_check ? sqrt(ss) : 0.0;
+    const bool ok = ctl->lvl_status == 0 && e <= ctl->tol;   // NaN fails
+    if (ok) {
+      ctl->final_status = ST_OK;
+      ctl->prec_used = ctl->lvl_prec[level];
+      ctl->ortho_fro = e;
+      ctl->active = -1;
+    } else if (ctl->input_nonfinite) {
+      ctl->final_status = ST_NONFINITE;
+      ctl->prec_used = ctl->lvl_prec[level];
+      ctl->ortho_fro = e;
+      ctl->active = -1;
+    } else if (level + 1 < ctl->nlevels) {
+      ctl->retries += 1;
+      ctl->lvl_status = 0;
+      ctl->active = level + 1;
+    } else {
+      ctl->final_status = ctl->lvl_status ? ctl->lvl_status : ST_ORTHO;
+      ctl->prec_used = ctl->lvl_prec[level];
+      ctl->ortho_fro = e;
+      ctl->active = -1;
+    }
   }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_judge(int n, const double* __restrict__ E, int check, Ctl* ctl,
+                                                int level) {
+  if (level_inactive(ctl, level)) return;
+  judge_block(n, E, check, ctl, level);
 }
 
 void launch_judge(int n, const double* E, int check, Ctl* ctl, int level, cudaStream_t st) {
   k_judge<<<1, 1024, 0, st>>>(n, E, check, ctl, level);
+}
+
+// ---------------------------------------------------------------------------
+// Grouped kernels (batched factorizations): the same bodies over a work list.
+namespace {
+
+constexpr int kGridCap = 152 * 8;
+
+inline unsigned grid_for(int nitems) { return (unsigned)(nitems < kGridCap ? (nitems > 0 ? nitems : 1) : kGridCap); }
+
+__device__ __forceinline__ bool item_live(const Prob& P, int level) {
+  return P.ctl->active == level && P.ctl->lvl_status == 0;
+}
+
+__global__ void __launch_bounds__(128) kg_trsm(Group g, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (!item_live(P, level)) continue;
+    const int64_t r = (int64_t)w.y * 128 + threadIdx.x;
+    if (r < P.m) trsm_row(r, P.n, P.A, P.lda, P.rst, P.rinv, P.Q, P.ldq);
+  }
+}
+
+template <int TN>
+__global__ void __launch_bounds__(32 * (TN / 16) * (TN / 16)) kg_syrk(Group g, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (!item_live(P, level)) continue;
+    syrk_block<TN>(P.m, P.n, P.Q, P.ldq, P.rows_per_split, P.ntile_syrk, P.gpart, w.y, w.z);
+  }
+}
+
+__global__ void kg_reduce(Group g, int check, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (!item_live(P, level)) continue;
+    const int64_t e = (int64_t)w.y * 256 + threadIdx.x;
+    if (e < (int64_t)P.n * P.n) reduce_partial_entry(P.n, P.splits, P.gpart, check ? P.e : P.rc, e);
+  }
+}
+
+__global__ void __launch_bounds__(1024) kg_chol(Group g, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (!item_live(P, level)) continue;
+    if (!chol_block(P.n, P.rc) && threadIdx.x == 0) raise_level_status(P.ctl, ST_BREAKDOWN);
+    __syncthreads();
+  }
+}
+
+__global__ void kg_trinv(Group g, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (!item_live(P, level)) continue;
+    const int j = w.y * 64 + threadIdx.x;
+    if (j < P.npad) trinv_column(P.n, P.rc, P.xt, j);
+  }
+}
+
+__global__ void kg_rmul(Group g, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (!item_live(P, level)) continue;
+    const int64_t e = (int64_t)w.y * 256 + threadIdx.x;
+    if (e < (int64_t)P.n * P.n) rmul_entry(P.n, P.rc, P.rs, P.R, P.ldr, e);
+  }
+}
+
+__global__ void __launch_bounds__(128) kg_finalize(Group g, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (!item_live(P, level)) continue;
+    const int64_t r = (int64_t)w.y * 128 + threadIdx.x;
+    if (r < P.m) finalize_row(r, P.n, P.Q, P.ldq, P.xt);
+  }
+}
+
+__global__ void __launch_bounds__(1024) kg_judge(Group g, int level) {
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (P.ctl->active != level) continue;
+    judge_block(P.n, P.e, P.check, P.ctl, level);
+  }
+}
+
+__global__ void kg_publish(Group g) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.nitems) return;
+  const Prob& P = g.probs[p];
+  if (P.status) *P.status = P.ctl->final_status;
+}
+
+}  // namespace
+
+void launch_g_trsm(const Group& g, int level, cudaStream_t st) {
+  if (g.nitems) kg_trsm<<<grid_for(g.nitems), 128, 0, st>>>(g, level);
+}
+void launch_g_syrk(const Group& g, int tn, bool check, int level, cudaStream_t st) {
+  (void)check;
+  if (!g.nitems) return;
+  if (tn == 16) kg_syrk<16><<<grid_for(g.nitems), 32, 0, st>>>(g, level);
+  else if (tn == 32) kg_syrk<32><<<grid_for(g.nitems), 128, 0, st>>>(g, level);
+  else kg_syrk<64><<<grid_for(g.nitems), 512, 0, st>>>(g, level);
+}
+void launch_g_reduce(const Group& g, bool check, int level, cudaStream_t st) {
+  if (g.nitems) kg_reduce<<<grid_for(g.nitems), 256, 0, st>>>(g, check ? 1 : 0, level);
+}
+void launch_g_chol(const Group& g, int level, cudaStream_t st) {
+  if (g.nitems) kg_chol<<<grid_for(g.nitems), 1024, 0, st>>>(g, level);
+}
+void launch_g_trinv(const Group& g, int level, cudaStream_t st) {
+  if (g.nitems) kg_trinv<<<grid_for(g.nitems), 64, 0, st>>>(g, level);
+}
+void launch_g_rmul(const Group& g, int level, cudaStream_t st) {
+  if (g.nitems) kg_rmul<<<grid_for(g.nitems), 256, 0, st>>>(g, level);
+}
+void launch_g_finalize(const Group& g, int level, cudaStream_t st) {
+  if (g.nitems) kg_finalize<<<grid_for(g.nitems), 128, 0, st>>>(g, level);
+}
+void launch_g_judge(const Group& g, int level, cudaStream_t st) {
+  if (g.nitems) kg_judge<<<grid_for(g.nitems), 1024, 0, st>>>(g, level);
+}
+void launch_g_publish(const Group& g, cudaStream_t st) {
+  if (g.nitems) kg_publish<<<(g.nitems + 127) / 128, 128, 0, st>>>(g);
 }
 
 }  // namespace mrcqr

@@ -119,6 +119,54 @@ def round_to(prec, x: torch.Tensor, stream=None) -> torch.Tensor:
     return y
 
 
+class BatchedPlan:
+    """Reusable batched MRCQR over fixed buffers (mrcqr_batched_plan_*)."""
+
+    def __init__(self, As, Qs, Rs, precs, seeds, status: torch.Tensor, use_graph: bool = False,
+                 autotune: bool = False, check_ortho: bool = True, escalate: bool = True, tol: float = 1e-13,
+                 rows_per_split: int = 0, rows_per_chunk: int = 0):
+        cnt = len(As)
+        arr = lambda ct, vals: (ct * cnt)(*vals)
+        self._keep = dict(
+            m=arr(ctypes.c_int64, [a.shape[0] for a in As]), n=arr(ctypes.c_int64, [a.shape[1] for a in As]),
+            lda=arr(ctypes.c_int64, [_ld(a, "A") for a in As]), ldq=arr(ctypes.c_int64, [_ld(q, "Q") for q in Qs]),
+            pa=arr(ctypes.c_void_p, [a.data_ptr() for a in As]), pq=arr(ctypes.c_void_p, [q.data_ptr() for q in Qs]),
+            pr=arr(ctypes.c_void_p, [r.data_ptr() for r in Rs]), pp=arr(ctypes.c_int, [_prec(p) for p in precs]),
+            ps=arr(ctypes.c_uint64, [int(s) for s in seeds]))
+        if status.dtype != torch.int32 or not status.is_cuda or status.numel() < cnt:
+            raise ValueError("status must be a CUDA int32 tensor with >= count entries")
+        o = _lib.BatchedOpts(use_graph=int(use_graph), autotune=int(autotune), check=int(check_ortho),
+                             escalate=int(escalate), ortho_tol=tol, rows_per_split=rows_per_split,
+                             rows_per_chunk=rows_per_chunk)
+        self._plan = ctypes.c_void_p()
+        k = self._keep
+        check(_lib.load().mrcqr_batched_plan_create(cnt, k["m"], k["n"], k["pa"], k["lda"], k["pq"], k["ldq"],
+                                                     k["pr"], k["pp"], k["ps"], status.data_ptr(), ctypes.byref(o),
+                                                     ctypes.byref(self._plan)), "mrcqr_batched_plan_create")
+
+    def execute(self, stream=None) -> None:
+        check(_lib.load().mrcqr_batched_plan_execute(self._plan, _stream(stream)), "mrcqr_batched_plan_execute")
+
+    def info(self) -> dict:
+        a, b, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        k = ctypes.c_int32()
+        check(_lib.load().mrcqr_batched_plan_info(self._plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k),
+                                                   ctypes.byref(w)), "mrcqr_batched_plan_info")
+        return {"rows_per_split": a.value, "rows_per_chunk": b.value, "kernels_per_execute": k.value,
+                "workspace_bytes": w.value}
+
+    def close(self) -> None:
+        if self._plan:
+            _lib.load().mrcqr_batched_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def signs(m: int, seed: int, device="cuda", stream=None) -> torch.Tensor:
     d = torch.empty(m, dtype=torch.float64, device=device)
     check(_lib.load().mrcqr_signs(m, seed, d.data_ptr(), _stream(stream)), "mrcqr_signs")

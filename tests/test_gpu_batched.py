@@ -1,0 +1,118 @@
+"""Batched MRCQR (grouped launches over many problems of uneven m and n)
+against the CPU oracle's checks and the single-matrix entry point."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_18411_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_18411_gb300 import build
+    build.build()
+    from paper_2606_18411_gb300 import mrcqr as M
+    return torch, M
+
+
+def _batch(shapes, seed0=500):
+    mats, kappas = [], []
+    for i, (m, n, kappa) in enumerate(shapes):
+        mats.append(inputs.make_matrix(m, n, kappa, seed=seed0 + i))
+        kappas.append(kappa)
+    return mats, kappas
+
+
+SHAPES = [(16384, 16, 1e0), (20001, 32, 1e3), (16384, 64, 1e6), (30000, 128, 1e9), (5000, 50, 1e11),
+          (16384, 16, 1e12), (40000, 100, 1e2), (12288, 128, 1e4), (9999, 7, 1e7), (16384, 33, 1e10)]
+
+
+def _run_oneshot(torch, M, mats, precs, seeds):
+    As = [M.to_colmajor(a) for a in mats]
+    Qs = [M.empty_colmajor(*a.shape) for a in mats]
+    Rs = [M.empty_colmajor(a.shape[1], a.shape[1]) for a in mats]
+    status = torch.full((len(mats),), -1, dtype=torch.int32, device="cuda")
+    M.factor_batched(As, Qs, Rs, precs, seeds, status)
+    torch.cuda.synchronize()
+    return As, Qs, Rs, status
+
+
+def test_batched_rule_precision_against_oracle(env):
+    torch, M = env
+    mats, kappas = _batch(SHAPES)
+    precs = [O.precision_rule(k) for k in kappas]
+    _, Qs, Rs, status = _run_oneshot(torch, M, mats, precs, list(range(len(mats))))
+    assert status.cpu().tolist() == [0] * len(mats)
+    for A, Q, R, k in zip(mats, Qs, Rs, kappas):
+        Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
+        assert O.orthogonality_error(Qh)[0] <= 1e-13, k
+        assert O.residual_error(A, Qh, Rh)[0] <= 1e-13, k
+        assert np.all(np.diag(Rh) > 0)
+
+
+def test_batched_matches_single_factorizations(env):
+    torch, M = env
+    mats, kappas = _batch(SHAPES[:6], seed0=900)
+    precs = [O.precision_rule(k) for k in kappas]
+    _, Qs, Rs, status = _run_oneshot(torch, M, mats, precs, [7] * len(mats))
+    for A, Qb, Rb, p in zip(mats, Qs, Rs, precs):
+        Q1, R1 = M.factor(M.to_colmajor(A), prec=p, seed=7)
+        # same sign vector and sample set; only summation orders differ
+        assert np.linalg.norm(Rb.cpu().numpy() - R1.cpu().numpy()) <= 1e-9 * np.linalg.norm(R1.cpu().numpy())
+
+
+def test_batched_escalates_per_problem(env):
+    torch, M = env
+    mats, kappas = _batch([(16384, 32, 1e2), (16384, 32, 1e13), (20000, 64, 1e3)], seed0=1300)
+    # the middle problem is given a precision far too low and must escalate alone
+    _, Qs, Rs, status = _run_oneshot(torch, M, mats, ["fp16", "fp16", "bf16"], [1, 2, 3])
+    assert status.cpu().tolist() == [0, 0, 0]
+    for A, Q, R in zip(mats, Qs, Rs):
+        assert O.orthogonality_error(Q.cpu().numpy())[0] <= 1e-13
+        assert O.residual_error(A, Q.cpu().numpy(), R.cpu().numpy())[0] <= 1e-13
+
+
+def test_batched_plan_graph_replay_and_autotune(env):
+    torch, M = env
+    mats, kappas = _batch(SHAPES[:5], seed0=1700)
+    precs = [O.precision_rule(k) for k in kappas]
+    As = [M.to_colmajor(a) for a in mats]
+    Qs = [M.empty_colmajor(*a.shape) for a in mats]
+    Rs = [M.empty_colmajor(a.shape[1], a.shape[1]) for a in mats]
+    status = torch.full((len(mats),), -1, dtype=torch.int32, device="cuda")
+    plan = M.BatchedPlan(As, Qs, Rs, precs, [3] * len(mats), status, use_graph=True, autotune=True)
+    info = plan.info()
+    assert info["rows_per_split"] in (1024, 2048, 4096, 8192)
+    assert info["rows_per_chunk"] in (2048, 4096, 8192, 16384)
+    for rep in range(2):
+        if rep == 1:
+            # new data in the same buffers: the captured graph reads them
+            mats = [inputs.make_matrix(a.shape[0], a.shape[1], k, seed=2500 + i)
+                    for i, (a, k) in enumerate(zip(mats, kappas))]
+            for Ad, a in zip(As, mats):
+                Ad.copy_(torch.from_numpy(a))
+        status.fill_(-1)
+        plan.execute()
+        torch.cuda.synchronize()
+        assert status.cpu().tolist() == [0] * len(mats)
+        for A, Q, R in zip(mats, Qs, Rs):
+            assert O.orthogonality_error(Q.cpu().numpy())[0] <= 1e-13
+            assert O.residual_error(A, Q.cpu().numpy(), R.cpu().numpy())[0] <= 1e-13
+    plan.close()
+
+
+def test_batched_rejects_invalid(env):
+    torch, M = env
+    A = M.to_colmajor(inputs.gaussian(100, 60, seed=1))   # m < 2n
+    Q = M.empty_colmajor(100, 60)
+    R = M.empty_colmajor(60, 60)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(M.MrcqrError):
+        M.factor_batched([A], [Q], [R], ["fp64"], [0], status)
