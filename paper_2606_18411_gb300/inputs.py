@@ -115,3 +115,24 @@ def make_matrix_device(m: int, n: int, kappa: float, kind: str = "geometric", se
     out = torch.empty((n, m), dtype=torch.float64, device=device).t()
     out.copy_(U @ B)
     return out
+
+
+def make_matrix_torch(m: int, n: int, kappa: float, kind: str = "geometric", seed: int = 0, device="cuda"):
+    """Like ``make_matrix_device`` but with the Gaussian drawn by torch's
+    seeded generator on the device (fast input generation for large batches).
+    Returns a column-major torch float64 tensor."""
+    import torch
+    rng = np.random.Generator(np.random.Philox(seed))
+    sig = spectrum(kind, n, kappa, rng)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    U = torch.randn((n, m), dtype=torch.float64, device=device, generator=g).t()
+    for _ in range(2):
+        G = (U.t() @ U).cpu().numpy()
+        Rinv = np.linalg.inv(np.linalg.cholesky(G).T)
+        U = U @ torch.from_numpy(Rinv).to(device)
+    V = torch.from_numpy(_orthonormal_columns(rng.standard_normal((n, n)))).to(device)
+    B = torch.from_numpy(sig).to(device)[:, None] * V.t()
+    out = torch.empty((n, m), dtype=torch.float64, device=device).t()
+    out.copy_(U @ B)
+    return out
