@@ -94,7 +94,8 @@ const char* mrcqr_status_string(int status);
  *   R           : output n x n upper triangular (ld = n), positive diagonal,
  *                 strict lower triangle set to zero.
  *   sketch_prec : mrcqr_prec_t; with the default options a failed check
- *                 re-runs at the next precision.
+ *                 re-runs at the next precision.  MRCQR_PREC_AUTO needs
+ *                 selector weights (mrcqr_selector_load).
  *   seed        : Philox key of the random signs D and the sample set S.
  * Same as mrcqr_factor_ex(..., ldr = n, opts = NULL, stream). */
 int mrcqr_factor(int64_t m, int64_t n, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
@@ -210,6 +211,42 @@ int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, con
  * (cudaGetSymbolAddress, with that device current); make that first call
  * outside any stream capture. */
 int mrcqr_sketch_qr_noalloc(int64_t n, int64_t s, const double* Y, int prec, double* Rs, mrcqr_stream_t stream);
+
+/* ---- learned sketch-precision selector ------------------------------------
+ * The paper lets the caller pick p from a coarse regime of kappa_2(A) and
+ * names machine-learned condition estimators as one way to get it (Sec.
+ * II-C).  With sketch_prec = MRCQR_PREC_AUTO an FP16 sketch is taken, 16
+ * features of its R_s are computed on the device, and an MLP 16-64-64-3
+ * (BF16 weights, FP32 accumulation) picks where the ladder FP16 -> FP32 ->
+ * FP64 starts by minimising the expected cost (a too-low start costs every
+ * run up to the right precision); the orthogonality judge still escalates.
+ * Parameters (FP32, nparams = mrcqr_selector_num_params()): W1[64][16],
+ * b1[64], W2[64][64], b2[64], W3[3][64], b3[3] (row-major); the features are
+ * standardised with mu, sd before the first layer; costs[3] are the relative
+ * costs of one run at FP16, FP32, FP64. */
+int mrcqr_selector_num_params(void);
+/* Installs selector weights for the current device (HOST arrays). */
+int mrcqr_selector_set(const float* params, const float* mu, const float* sd, const float* costs);
+/* Loads a weight file: "MRCQRSEL", uint32 version 1, uint32 nparams, float mu[16], sd[16], costs[3],
+ * float params[nparams] (little endian). */
+int mrcqr_selector_load(const char* path);
+/* The 16 selector features of an upper-triangular Rs (DEVICE n x n, ld n) of a problem with m rows,
+ * written to feat (DEVICE float[16]). */
+int mrcqr_selector_features(int64_t m, int64_t n, const double* Rs, float* feat, mrcqr_stream_t stream);
+/* Batched MLP inference: logits (DEVICE float[batch][3]) and, if choice is non-NULL, the expected-cost
+ * choice (DEVICE int32[batch]) for raw features X (DEVICE float[batch][16]); w_bf16 DEVICE BF16
+ * parameters, mu/sd/costs DEVICE. */
+int mrcqr_mlp_forward(int batch, const float* X, const uint16_t* w_bf16, const float* mu, const float* sd,
+                      const float* costs, float* logits, int32_t* choice, mrcqr_stream_t stream);
+/* One training step on a minibatch (all DEVICE): class-weighted mean cross-entropy of labels y (0 fp16,
+ * 1 fp32, 2 fp64) with weights class_w[3], gradient on the BF16 weights w_bf16 (FP32 accumulation,
+ * deterministic fixed-order reduction); with apply = 1 an AdamW update (decoupled weight decay wd,
+ * bias-corrected at step >= 1) of the FP32 master weights and moments, and w_bf16 refreshed.
+ * grad_out (float[nparams]) and loss_out (float[1]) may be NULL. */
+int mrcqr_mlp_train_step(int batch, const float* X, const int32_t* y, const float* class_w, const float* mu,
+                         const float* sd, float* master, float* mom, float* var, uint16_t* w_bf16, float lr,
+                         float beta1, float beta2, float eps, float wd, int step, int apply, float* grad_out,
+                         float* loss_out, mrcqr_stream_t stream);
 
 /* ---- instrumentation (per-kernel timing) ------ */
 

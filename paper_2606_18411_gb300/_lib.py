@@ -75,6 +75,13 @@ SIGNATURES = {
     "mrcqr_last_sketch_variant": ([], _i32),
     "mrcqr_cholqr_precond": ([_i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp], _i32),
     "mrcqr_sketch_qr_noalloc": ([_i64, _i64, _vp, _i32, _vp, _vp], _i32),
+    "mrcqr_selector_num_params": ([], _i32),
+    "mrcqr_selector_set": ([_vp, _vp, _vp, _vp], _i32),
+    "mrcqr_selector_load": ([ctypes.c_char_p], _i32),
+    "mrcqr_selector_features": ([_i64, _i64, _vp, _vp, _vp], _i32),
+    "mrcqr_mlp_forward": ([_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "mrcqr_mlp_train_step": ([_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_float, ctypes.c_float, _i32, _i32, _vp, _vp, _vp], _i32),
     "mrcqr_launch_count": ([], ctypes.c_uint64),
     "mrcqr_stage_name": ([_i32], ctypes.c_char_p),
     "mrcqr_profile_begin": ([], _i32),

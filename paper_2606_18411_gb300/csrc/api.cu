@@ -26,7 +26,7 @@ struct Plan {
   int64_t m = 0;
   int n = 0, s = 0, npad = 0, chunks = 0, splits = 0;
   size_t off_ctl = 0, off_idx = 0, off_tab = 0, off_tabf = 0, off_ypart = 0, off_y = 0, off_sqr = 0, off_rs = 0, off_rst = 0,
-         off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, total = 0;
+         off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, off_feat = 0, total = 0;
 };
 
 Plan make_plan(int64_t m, int n, int s) {
@@ -57,6 +57,7 @@ Plan make_plan(int64_t m, int n, int s) {
   p.off_rc = take(sizeof(double) * (size_t)n * n);
   p.off_xt = take(sizeof(double) * (size_t)n * p.npad);
   p.off_e = take(sizeof(double) * (size_t)n * n);
+  p.off_feat = take(sizeof(float) * kNumFeatures);
   p.total = o;
   return p;
 }
@@ -139,11 +140,12 @@ void launch(int stage, int level, cudaStream_t st, F&& f) {
 
 enum Stage {
   SG_INIT = 0, SG_SAMPLE, SG_COSTAB, SG_SKETCH, SG_SKREDUCE, SG_SQR, SG_TRSM, SG_SYRK, SG_CHOL, SG_TRINV, SG_RMUL,
-  SG_FINALIZE, SG_CHECK, SG_JUDGE, SG_STATS, SG_PREP, SG_GREDUCE, SG_EREDUCE, SG_COUNT
+  SG_FINALIZE, SG_CHECK, SG_JUDGE, SG_STATS, SG_PREP, SG_GREDUCE, SG_EREDUCE, SG_FEATURES, SG_SELECT, SG_MLP,
+  SG_COUNT
 };
 const char* kStageNames[SG_COUNT] = {"init", "sample", "costab", "sketch", "sketch_reduce", "sketch_qr", "trsm",
                                      "syrk", "chol", "trinv", "rmul", "finalize", "check", "judge", "stats",
-                                     "prepare", "gram_reduce", "check_reduce"};
+                                     "prepare", "gram_reduce", "check_reduce", "features", "select", "mlp"};
 
 // Per-(device, stream) status records for mrcqr_get_last_status.
 std::mutex g_mu;
@@ -268,12 +270,18 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
   const int variant = opts ? opts->sketch_variant : 0;
   int rc = validate(m, n, A, lda, Q, ldq, R, ldr, s_factor);
   if (rc != MRCQR_OK) return rc;
-  if (sketch_prec < P_FP16 || sketch_prec > P_FP64) return MRCQR_ERR_INVALID;
+  if (sketch_prec < P_FP16 || sketch_prec > P_AUTO) return MRCQR_ERR_INVALID;
+  const bool autosel = sketch_prec == P_AUTO;
+  if (autosel && !selector_ready()) {
+    fprintf(stderr, "mrcqr: MRCQR_PREC_AUTO needs selector weights (mrcqr_selector_load / mrcqr_selector_set)\n");
+    return MRCQR_ERR_INVALID;
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int s = s_factor * (int)n;
   const Plan p = make_plan(m, (int)n, s);
   int lv[kMaxLevels] = {P_FP64, P_FP64, P_FP64, P_FP64};
-  const int nlevels = make_ladder(sketch_prec, escalate, lv);
+  // AUTO: the ladder fp16 -> fp32 -> fp64 always; the selector picks where it starts
+  const int nlevels = make_ladder(autosel ? (int)P_FP16 : sketch_prec, autosel || escalate, lv);
   mrcqr_stats_t* slot = status_slot(st);
   if (!slot) return MRCQR_ERR_ALLOC;
   void* ws = nullptr;
@@ -299,6 +307,11 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
       launch_sketch_qr(lv[L], (int)n, s, y, at<void>(ws, p.off_sqr), at<double>(ws, p.off_rs),
                        at<double>(ws, p.off_rst), at<double>(ws, p.off_rinv), ctl, L, st);
     });
+    if (autosel && L == 0) {
+      float* feat = at<float>(ws, p.off_feat);
+      launch(SG_FEATURES, 0, st, [&] { launch_features(at<double>(ws, p.off_rs), (int)n, m, feat, ctl, 0, st); });
+      launch(SG_SELECT, 0, st, [&] { launch_mlp_select(feat, ctl, st); });
+    }
     enqueue_stage2(p, ws, A, lda, Q, ldq, R, ldr, check, ctl, L, st);
   }
   launch(SG_STATS, 0, st, [&] { k_write_stats<<<1, 1, 0, st>>>(ctl, slot); });
@@ -464,6 +477,72 @@ int mrcqr_profile_end(int max_records, int32_t* stage, int32_t* level, float* ms
   g_prof.recs.clear();
   if (count) *count = k;
   return MRCQR_OK;
+}
+
+int mrcqr_selector_num_params(void) { return selector_num_params(); }
+
+int mrcqr_selector_set(const float* params, const float* mu, const float* sd, const float* costs) {
+  if (!params || !mu || !sd || !costs) return MRCQR_ERR_INVALID;
+  return selector_set(params, mu, sd, costs);
+}
+
+int mrcqr_selector_load(const char* path) {
+  if (!path) return MRCQR_ERR_INVALID;
+  FILE* f = fopen(path, "rb");
+  if (!f) return MRCQR_ERR_INVALID;
+  char magic[8];
+  uint32_t ver = 0, np = 0;
+  std::vector<float> aux(35), params;
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "MRCQRSEL", 8) == 0 && fread(&ver, 4, 1, f) == 1 &&
+            ver == 1 && fread(&np, 4, 1, f) == 1 && (int)np == selector_num_params() &&
+            fread(aux.data(), sizeof(float), 35, f) == 35;
+  if (ok) {
+    params.resize(np);
+    ok = fread(params.data(), sizeof(float), np, f) == np;
+  }
+  fclose(f);
+  if (!ok) return MRCQR_ERR_INVALID;
+  return selector_set(params.data(), aux.data(), aux.data() + 16, aux.data() + 32);
+}
+
+int mrcqr_selector_features(int64_t m, int64_t n, const double* Rs, float* feat, mrcqr_stream_t stream) {
+  if (!Rs || !feat || n < 1 || n > kMaxN || m < 1) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  launch(SG_FEATURES, 0, st, [&] { launch_features(Rs, (int)n, m, feat, nullptr, 0, st); });
+  return finish(st);
+}
+
+int mrcqr_mlp_forward(int batch, const float* X, const uint16_t* w_bf16, const float* mu, const float* sd,
+                      const float* costs, float* logits, int32_t* choice, mrcqr_stream_t stream) {
+  if (batch < 0 || !X || !w_bf16 || !mu || !sd || !costs || !logits) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  launch(SG_MLP, 0, st, [&] { launch_mlp_forward(w_bf16, mu, sd, costs, batch, X, logits, choice, st); });
+  return finish(st);
+}
+
+int mrcqr_mlp_train_step(int batch, const float* X, const int32_t* y, const float* class_w, const float* mu,
+                         const float* sd, float* master, float* mom, float* var, uint16_t* w_bf16, float lr,
+                         float beta1, float beta2, float eps, float wd, int step, int apply, float* grad_out,
+                         float* loss_out, mrcqr_stream_t stream) {
+  if (batch < 1 || !X || !y || !class_w || !mu || !sd || !w_bf16) return MRCQR_ERR_INVALID;
+  if (apply && (!master || !mom || !var || step < 1)) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int nparts = batch < 128 ? batch : 128;
+  void* scratch = nullptr;
+  const size_t bytes = sizeof(float) * ((size_t)nparts * selector_num_params() + nparts);
+  if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCQR_ERR_ALLOC;
+  }
+  float* part = static_cast<float*>(scratch);
+  float* lpart = part + (size_t)nparts * selector_num_params();
+  launch(SG_MLP, 0, st, [&] { launch_mlp_grad(w_bf16, mu, sd, batch, X, y, class_w, part, lpart, nparts, st); });
+  launch(SG_MLP, 0, st, [&] {
+    launch_mlp_reduce_adamw(nparts, part, lpart, master, mom, var, w_bf16, lr, beta1, beta2, eps, wd, step, apply,
+                            grad_out, loss_out, st);
+  });
+  cudaFreeAsync(scratch, st);
+  return finish(st);
 }
 
 int mrcqr_shutdown(void) {

@@ -105,4 +105,19 @@ void launch_finalize(int64_t m, int n, double* Q, int64_t ldq, const double* XT,
                      cudaStream_t st);
 void launch_judge(int n, const double* E, int check, Ctl* ctl, int level, cudaStream_t st);
 
+// --- learned selector (selector.cu) --------------------------------------------
+int selector_num_params();
+bool selector_ready();
+int selector_set(const float* params, const float* mu, const float* sd, const float* costs);
+void launch_features(const double* Rs, int n, int64_t m, float* out, const Ctl* ctl, int level, cudaStream_t st);
+bool launch_mlp_select(const float* feat, Ctl* ctl, cudaStream_t st);
+void launch_mlp_forward(const unsigned short* w, const float* mu, const float* sd, const float* costs, int batch,
+                        const float* X, float* logits, int32_t* choice, cudaStream_t st);
+void launch_mlp_grad(const unsigned short* w, const float* mu, const float* sd, int batch, const float* X,
+                     const int32_t* y, const float* class_w, float* part, float* loss_part, int nparts,
+                     cudaStream_t st);
+void launch_mlp_reduce_adamw(int nparts, const float* part, const float* loss_part, float* master, float* mom,
+                             float* var, unsigned short* wbf16, float lr, float beta1, float beta2, float eps,
+                             float wd, int step, int apply, float* grad_out, float* loss_out, cudaStream_t st);
+
 }  // namespace mrcqr

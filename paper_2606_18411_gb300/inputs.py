@@ -117,9 +117,11 @@ def make_matrix_device(m: int, n: int, kappa: float, kind: str = "geometric", se
     return out
 
 
-def make_matrix_torch(m: int, n: int, kappa: float, kind: str = "geometric", seed: int = 0, device="cuda"):
+def make_matrix_torch(m: int, n: int, kappa: float, kind: str = "geometric", seed: int = 0, device="cuda",
+                      rounds: int = 1):
     """Like ``make_matrix_device`` but with the Gaussian drawn by torch's
-    seeded generator on the device (fast input generation for large batches).
+    seeded generator on the device (fast input generation for large batches);
+    one Gram/Cholesky round already orthonormalises a Gaussian to ~1e-15.
     Returns a column-major torch float64 tensor."""
     import torch
     rng = np.random.Generator(np.random.Philox(seed))
@@ -127,7 +129,7 @@ def make_matrix_torch(m: int, n: int, kappa: float, kind: str = "geometric", see
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     U = torch.randn((n, m), dtype=torch.float64, device=device, generator=g).t()
-    for _ in range(2):
+    for _ in range(rounds):
         G = (U.t() @ U).cpu().numpy()
         Rinv = np.linalg.inv(np.linalg.cholesky(G).T)
         U = U @ torch.from_numpy(Rinv).to(device)

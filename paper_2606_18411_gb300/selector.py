@@ -1,0 +1,249 @@
+"""Training and evaluation of the learned sketch-precision selector.
+
+Every step runs in libmrcqr's kernels (features, MLP forward/backward,
+AdamW); this module only generates data, drives the training loop and
+stores the weights.  Data: synthetic m x n FP64 matrices A = U diag(sigma)
+V^T (spectra geometric, step-cliff, clustered, log-uniform; kappa_2
+log-uniform in [1, 1e16]), each labelled by running MRCQR without
+escalation at FP16 and at FP32: label 0 if FP16 passes the 1e-13 judge,
+1 if only FP32 does, 2 otherwise (FP64).
+
+    python -m paper_2606_18411_gb300.selector train --count 20000 --heldout 2000 \\
+        --out paper_2606_18411_gb300/selector_weights.bin
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import struct
+import time
+
+import numpy as np
+import torch
+
+from . import _lib, inputs
+from . import mrcqr as M
+
+NF = 16
+SPECTRA = inputs.SPECTRA
+DEFAULT_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.bin")
+
+
+def num_params() -> int:
+    return _lib.load().mrcqr_selector_num_params()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def features_of(A: torch.Tensor, seed: int = 0, out: torch.Tensor | None = None) -> torch.Tensor:
+    """The 16 selector features of the FP16 sketch's R_s of A (device)."""
+    m, n = A.shape
+    Y = M.sketch(A, 2 * n, "fp16", seed=seed)
+    Rs = M.sketch_qr(Y, "fp16")
+    f = out if out is not None else torch.empty(NF, dtype=torch.float32, device=A.device)
+    _lib.check(_lib.load().mrcqr_selector_features(m, n, Rs.data_ptr(), f.data_ptr(), _stream()),
+               "mrcqr_selector_features")
+    return f
+
+
+def passes(A: torch.Tensor, prec: str, seed: int = 0) -> bool:
+    m, n = A.shape
+    Q = M.empty_colmajor(m, n, device=A.device)
+    R = M.empty_colmajor(n, n, device=A.device)
+    M.factor_ex(A, Q, R, prec=prec, seed=seed, escalate=False)
+    return M.last_status()["status"] == "OK"
+
+
+def make_dataset(count: int, m: int, seed0: int, n_range=(32, 256), verify_fp64_every: int = 20, device="cuda",
+                 log_every: int = 0):
+    """Features X (count x 16), labels y, and (n, kappa, spectrum) of each matrix."""
+    rng = np.random.default_rng(seed0)
+    X = torch.empty((count, NF), dtype=torch.float32, device=device)
+    y = np.zeros(count, dtype=np.int32)
+    meta = []
+    monotone_violations = 0
+    t0 = time.time()
+    for i in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        kind = SPECTRA[int(rng.integers(len(SPECTRA)))]
+        kappa = float(10.0 ** rng.uniform(0.0, 16.0))
+        A = inputs.make_matrix_torch(m, n, kappa, kind=kind, seed=seed0 * 1000003 + i, device=device)
+        features_of(A, seed=i, out=X[i])
+        p16 = passes(A, "fp16", seed=i)
+        p32 = True if p16 else passes(A, "fp32", seed=i)
+        y[i] = 0 if p16 else (1 if p32 else 2)
+        if verify_fp64_every and i % verify_fp64_every == 0:
+            p64 = passes(A, "fp64", seed=i)
+            if not p64 or (p16 and not passes(A, "fp32", seed=i)):
+                monotone_violations += 1
+        meta.append((n, kappa, kind))
+        if log_every and (i + 1) % log_every == 0:
+            print(f"  {i + 1}/{count} matrices, {time.time() - t0:.0f} s", flush=True)
+    torch.cuda.synchronize()
+    return X, torch.from_numpy(y).to(device), meta, monotone_violations
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-normal hidden layers, small output layer, zero biases."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((64, 16)) * math.sqrt(2.0 / 16)
+    W2 = rng.standard_normal((64, 64)) * math.sqrt(2.0 / 64)
+    W3 = rng.standard_normal((3, 64)) * 0.01
+    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3.ravel(), np.zeros(3)]).astype(
+        np.float32)
+
+
+class Trainer:
+    """FP32 master weights, Adam moments and BF16 copies on the device."""
+
+    def __init__(self, params: np.ndarray, mu, sd, device="cuda"):
+        self.master = torch.from_numpy(np.asarray(params, np.float32)).to(device)
+        self.mom = torch.zeros_like(self.master)
+        self.var = torch.zeros_like(self.master)
+        self.wbf16 = self.master.to(torch.bfloat16).view(torch.int16)
+        self.mu = torch.as_tensor(mu, dtype=torch.float32, device=device)
+        self.sd = torch.as_tensor(sd, dtype=torch.float32, device=device)
+        self.step = 0
+
+    def train_step(self, X, y, class_w, lr=3e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd=1e-4, apply=True,
+                   grad_out=None):
+        loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+        if apply:
+            self.step += 1
+        _lib.check(_lib.load().mrcqr_mlp_train_step(
+            X.shape[0], X.data_ptr(), y.data_ptr(), class_w.data_ptr(), self.mu.data_ptr(), self.sd.data_ptr(),
+            self.master.data_ptr(), self.mom.data_ptr(), self.var.data_ptr(), self.wbf16.data_ptr(), lr, beta1,
+            beta2, eps, wd, max(self.step, 1), int(apply), _ptr(grad_out), loss.data_ptr(), _stream()),
+            "mrcqr_mlp_train_step")
+        return loss
+
+    def forward(self, X, costs):
+        logits = torch.empty((X.shape[0], 3), dtype=torch.float32, device=X.device)
+        choice = torch.empty(X.shape[0], dtype=torch.int32, device=X.device)
+        c = torch.as_tensor(costs, dtype=torch.float32, device=X.device)
+        _lib.check(_lib.load().mrcqr_mlp_forward(X.shape[0], X.data_ptr(), self.wbf16.data_ptr(), self.mu.data_ptr(),
+                                                 self.sd.data_ptr(), c.data_ptr(), logits.data_ptr(),
+                                                 choice.data_ptr(), _stream()), "mrcqr_mlp_forward")
+        return logits, choice
+
+
+def train(X, y, epochs=40, batch=256, lr=3e-3, class_w=(1.0, 1.0, 2.0), seed=0, log=None):
+    """Minibatch training; returns (trainer, mu, sd, losses per epoch)."""
+    mu = X.mean(0).cpu().numpy()
+    sd = X.std(0).cpu().numpy()
+    sd[sd < 1e-6] = 1.0
+    tr = Trainer(init_params(seed), mu, sd, device=X.device)
+    cw = torch.tensor(class_w, dtype=torch.float32, device=X.device)
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    losses = []
+    n = X.shape[0]
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g).to(X.device)
+        tot = 0.0
+        for b in range(0, n, batch):
+            idx = perm[b:b + batch]
+            tot += float(tr.train_step(X[idx].contiguous(), y[idx].contiguous(), cw, lr=lr).item()) * len(idx)
+        losses.append(tot / n)
+        if log:
+            log(f"epoch {ep + 1}: loss {losses[-1]:.4f}")
+    return tr, mu, sd, losses
+
+
+def save_weights(path, params, mu, sd, costs):
+    with open(path, "wb") as f:
+        f.write(b"MRCQRSEL")
+        f.write(struct.pack("<II", 1, len(params)))
+        f.write(np.asarray(mu, "<f4").tobytes())
+        f.write(np.asarray(sd, "<f4").tobytes())
+        f.write(np.asarray(costs, "<f4").tobytes())
+        f.write(np.asarray(params, "<f4").tobytes())
+
+
+def load_into_library(path: str = DEFAULT_WEIGHTS) -> None:
+    _lib.check(_lib.load().mrcqr_selector_load(path.encode()), "mrcqr_selector_load")
+
+
+def measure_costs(m=1 << 16, n=144, reps=5, device="cuda"):
+    """Relative time of one MRCQR run per sketch precision (FP16 = 1)."""
+    A = inputs.make_matrix_torch(m, n, 10.0, seed=1, device=device)
+    Q = M.empty_colmajor(m, n, device=device)
+    R = M.empty_colmajor(n, n, device=device)
+    t = []
+    for p in ("fp16", "fp32", "fp64"):
+        M.factor_ex(A, Q, R, prec=p, escalate=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            M.factor_ex(A, Q, R, prec=p, escalate=False)
+        e1.record()
+        torch.cuda.synchronize()
+        t.append(e0.elapsed_time(e1) / reps)
+    return [x / t[0] for x in t], t
+
+
+def ladder_cost(start: int, label: int, costs) -> float:
+    return costs[start] if start >= label else float(sum(costs[start:label + 1]))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    t = sub.add_parser("train")
+    t.add_argument("--count", type=int, default=20000)
+    t.add_argument("--heldout", type=int, default=2000)
+    t.add_argument("--m", type=int, default=1 << 16)
+    t.add_argument("--epochs", type=int, default=40)
+    t.add_argument("--out", default=DEFAULT_WEIGHTS)
+    t.add_argument("--report", default=None)
+    args = ap.parse_args()
+    from . import build
+    build.build()
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    costs, times = measure_costs(m=args.m)
+    print(f"relative run costs fp16/fp32/fp64: {costs} ({times} ms)", flush=True)
+    Xtr, ytr, _, v1 = make_dataset(args.count, args.m, seed0=1, log_every=2000)
+    Xte, yte, meta_te, v2 = make_dataset(args.heldout, args.m, seed0=2, log_every=1000)
+    t_data = time.time() - t0
+    tr, mu, sd, losses = train(Xtr, ytr, epochs=args.epochs, log=lambda s: print(s, flush=True))
+    params = tr.master.cpu().numpy()
+    save_weights(args.out, params, mu, sd, costs)
+    _, choice = tr.forward(Xte, costs)
+    ch = choice.cpu().numpy()
+    yt = yte.cpu().numpy()
+    conf = np.zeros((3, 3), dtype=int)
+    for a, b in zip(yt, ch):
+        conf[a, b] += 1
+    auto = sum(ladder_cost(int(c), int(l), costs) for c, l in zip(ch, yt))
+    a32 = sum(ladder_cost(1, int(l), costs) for l in yt)
+    a64 = sum(ladder_cost(2, int(l), costs) for l in yt)
+    ideal = sum(ladder_cost(int(l), int(l), costs) for l in yt)
+    rep = {"train_count": args.count, "heldout_count": args.heldout, "m": args.m,
+           "label_counts_train": np.bincount(ytr.cpu().numpy(), minlength=3).tolist(),
+           "label_counts_heldout": np.bincount(yt, minlength=3).tolist(),
+           "monotonicity_violations": int(v1 + v2), "relative_costs": costs, "run_ms": times,
+           "final_train_loss": losses[-1], "heldout_accuracy": float(np.mean(ch == yt)),
+           "confusion_true_by_chosen": conf.tolist(),
+           "heldout_relative_cost": {"selector": auto / ideal, "always_fp32": a32 / ideal,
+                                     "always_fp64": a64 / ideal, "ideal": 1.0},
+           "under_predictions": int(np.sum(ch < yt)), "data_seconds": t_data,
+           "total_seconds": time.time() - t0}
+    print(json.dumps(rep), flush=True)
+    if args.report:
+        with open(args.report, "w") as f:
+            json.dump(rep, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

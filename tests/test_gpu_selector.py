@@ -1,0 +1,120 @@
+"""Selector kernels (features, BF16 MLP forward/backward, AdamW, AUTO path)
+against the FP64 selector oracle on the same (BF16-rounded) weights."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import selector_oracle as SO
+from paper_2606_18411_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_18411_gb300 import build
+    build.build()
+    from paper_2606_18411_gb300 import mrcqr as M
+    from paper_2606_18411_gb300 import selector as S
+    return torch, M, S
+
+
+@pytest.mark.parametrize("m,n,kappa,kind", [(8192, 32, 1e2, "geometric"), (16384, 100, 1e10, "cliff"),
+                                            (20000, 256, 1e14, "loguniform"), (4096, 17, 1e6, "clustered")])
+def test_features_match_oracle(env, m, n, kappa, kind):
+    torch, M, S = env
+    A = M.to_colmajor(inputs.make_matrix(m, n, kappa, kind=kind, seed=n))
+    Y = M.sketch(A, 2 * n, "fp16", seed=1)
+    Rs = M.sketch_qr(Y, "fp16")
+    f = torch.empty(16, dtype=torch.float32, device="cuda")
+    from paper_2606_18411_gb300 import _lib
+    assert _lib.load().mrcqr_selector_features(m, n, Rs.data_ptr(), f.data_ptr(),
+                                               torch.cuda.current_stream().cuda_stream) == 0
+    ref = SO.features(Rs.cpu().numpy(), m)
+    np.testing.assert_allclose(f.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
+
+
+def _rand_setup(torch, S, B=300, seed=0):
+    rng = np.random.default_rng(seed)
+    theta = (rng.standard_normal(SO.NUM_PARAMS) * 0.3).astype(np.float32)
+    X = (rng.standard_normal((B, 16)) * 3 + 1).astype(np.float32)
+    y = rng.integers(0, 3, B).astype(np.int32)
+    mu = X.mean(0)
+    sd = X.std(0)
+    return theta, X, y, mu, sd
+
+
+def test_forward_and_gradient_match_oracle(env):
+    torch, M, S = env
+    theta, X, y, mu, sd = _rand_setup(torch, S)
+    tr = S.Trainer(theta, mu, sd)
+    theta_b = SO.round_bf16(theta)                       # the weights the kernels use
+    Xn = (X.astype(np.float64) - mu) / sd
+    Xd = torch.from_numpy(X).cuda()
+    logits, choice = tr.forward(Xd, [1.0, 1.02, 1.9])
+    z_ref, _ = SO.forward(theta_b, Xn)
+    np.testing.assert_allclose(logits.cpu().numpy(), z_ref, rtol=1e-4, atol=1e-4)
+    np.testing.assert_array_equal(choice.cpu().numpy(), SO.choose(theta_b, Xn, [1.0, 1.02, 1.9]))
+    cw = np.array([1.0, 1.5, 2.5], np.float32)
+    g = torch.zeros(SO.NUM_PARAMS, dtype=torch.float32, device="cuda")
+    loss = tr.train_step(Xd, torch.from_numpy(y).cuda(), torch.from_numpy(cw).cuda(), apply=False, grad_out=g)
+    l_ref, g_ref = SO.loss_and_grad(theta_b, Xn, y, cw.astype(np.float64))
+    assert abs(float(loss.item()) - l_ref) <= 1e-5 * l_ref
+    gh = g.cpu().numpy()
+    for part, ref in zip(SO.unpack(gh.astype(np.float64)), SO.unpack(g_ref)):
+        assert np.linalg.norm(part - ref) <= 1e-4 * np.linalg.norm(ref) + 1e-9
+
+
+def test_adamw_step_matches_oracle(env):
+    torch, M, S = env
+    theta, X, y, mu, sd = _rand_setup(torch, S, seed=1)
+    tr = S.Trainer(theta, mu, sd)
+    cw = torch.ones(3, dtype=torch.float32, device="cuda")
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    g = torch.zeros(SO.NUM_PARAMS, dtype=torch.float32, device="cuda")
+    tr.train_step(Xd, yd, cw, lr=1e-2, apply=False, grad_out=g)
+    tr.train_step(Xd, yd, cw, lr=1e-2, apply=True)
+    ref, _, _ = SO.adamw_step(theta.astype(np.float64), g.cpu().numpy().astype(np.float64),
+                              np.zeros(SO.NUM_PARAMS), np.zeros(SO.NUM_PARAMS), 1, lr=1e-2)
+    np.testing.assert_allclose(tr.master.cpu().numpy(), ref, rtol=1e-5, atol=1e-6)
+    np.testing.assert_array_equal(tr.wbf16.view(torch.bfloat16).float().cpu().numpy(),
+                                  SO.round_bf16(tr.master.cpu().numpy()))
+
+
+def test_training_on_gpu_reduces_loss(env):
+    torch, M, S = env
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((2000, 16)).astype(np.float32)
+    y = ((X[:, 0] > 0.3).astype(int) + (X[:, 3] > 0.3).astype(int)).astype(np.int32)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    tr, mu, sd, losses = S.train(Xd, yd, epochs=25, batch=200, lr=1e-2)
+    assert losses[-1] < 0.35 * losses[0]
+    logits, _ = tr.forward(Xd, [1.0, 1.0, 1.0])
+    assert np.mean(np.argmax(logits.cpu().numpy(), axis=1) == y) > 0.9
+
+
+@pytest.mark.parametrize("forced", [0, 1, 2])
+def test_auto_path_follows_selector_choice(env, forced):
+    torch, M, S = env
+    from paper_2606_18411_gb300 import _lib
+    # weights whose output bias forces the class `forced`
+    theta = np.zeros(SO.NUM_PARAMS, np.float32)
+    theta[-3:] = -40.0
+    theta[-3 + forced] = 40.0
+    mu, sd, costs = np.zeros(16, np.float32), np.ones(16, np.float32), np.array([1, 1.02, 1.9], np.float32)
+    lib = _lib.load()
+    assert lib.mrcqr_selector_set(theta.ctypes.data, mu.ctypes.data, sd.ctypes.data, costs.ctypes.data) == 0
+    A = inputs.make_matrix(8192, 48, 1e6, seed=44)
+    Q, R = M.factor(M.to_colmajor(A), prec="auto", seed=2)
+    st = M.last_status()
+    assert st["status"] == "OK" and st["selector_choice"] == forced
+    assert st["prec_first"] == ["fp16", "fp32", "fp64"][forced]
+    # kappa = 1e6: fp16 fails and escalates to fp32; fp32 / fp64 pass at once
+    assert st["prec_used"] == ("fp32" if forced == 0 else ["fp16", "fp32", "fp64"][forced])
+    assert O.orthogonality_error(Q.cpu().numpy())[0] <= 1e-13
+    assert O.residual_error(A, Q.cpu().numpy(), R.cpu().numpy())[0] <= 1e-13
