@@ -68,6 +68,11 @@ typedef struct mrcqr_opts {
                              and lda is even, SIMT otherwise; 1: SIMT; 2: tensor cores when possible */
   double ortho_tol;   /* acceptance threshold on ||I - Q^T Q||_F (default 1e-13) */
   void* stats_device; /* optional DEVICE pointer to an mrcqr_stats_t written at the end */
+  int32_t fp64_products; /* 0 (default): the Gram matrix W^T W, the product Q = W R_c^{-1} and
+                            the check Q^T Q as emulated FP64 on the FP16 tensor cores (exact 8-bit
+                            digit slicing, integer recombination, one final rounding; see
+                            mrcqr_gram and mrcqr_finalize_q); 1: FP64 FMA kernels throughout */
+  int32_t reserved1;
 } mrcqr_opts_t;
 
 typedef struct mrcqr_stats {
@@ -192,6 +197,32 @@ int mrcqr_sketch_qr(int64_t n, int64_t s, const double* Y, int prec, double* Rs,
  * Status (breakdown) through mrcqr_get_last_status. */
 int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, const double* Rs, double* Q,
                          int64_t ldq, double* R, int64_t ldr, mrcqr_stream_t stream);
+
+/* Algorithm 1 step 1 (and the check of Sec. II-C): G = W^T W.  W: DEVICE
+ * double m x n, column-major, ld ldw >= m; G: DEVICE double n x n, packed
+ * column-major, receives the upper triangle (diagonal included), strictly
+ * lower triangle set to zero.  fp64_products = 0: emulated FP64 on the FP16
+ * tensor cores -- every column sliced against the exponent of its maximum
+ * over all m rows, exact integer level sums, each entry rounded once (error
+ * per term at most 2^-57 times the two column maxima; deterministic for any
+ * launch configuration; a non-finite column gives NaN entries); 1: FP64 FMA
+ * with fixed-order partial sums.  1 <= n <= 512, 1 <= m < 2^31.  Allocates its
+ * workspace with cudaMallocAsync on `stream`. */
+int mrcqr_gram(int64_t m, int64_t n, const double* W, int64_t ldw, double* G, int fp64_products,
+               mrcqr_stream_t stream);
+
+/* Algorithm 1 step 3 (and Algorithm 2 step 9): Q <- W X in place, with
+ * X = R_c^{-1} upper triangular.  Q: DEVICE double m x n, column-major,
+ * ld ldq >= m, holds W on entry; X: DEVICE double n x n, column-major,
+ * ld ldx >= n, only the upper triangle (diagonal included) is read.
+ * fp64_products = 0: emulated FP64 on the FP16 tensor cores (each entry the
+ * once-rounded value of a 63-bit fixed-point evaluation of the exact sum,
+ * error per term at most 2^-57 times the row maximum of W times the column
+ * maximum of X; non-finite operands give NaN rows); 1: FP64 FMA.
+ * 1 <= n <= 512, 1 <= m < 2^31; Q and X must not overlap.  Allocates its workspace with cudaMallocAsync on `stream`.
+ * Returns MRCQR_ERR_INVALID / MRCQR_ERR_ALLOC before enqueueing anything. */
+int mrcqr_finalize_q(int64_t m, int64_t n, double* Q, int64_t ldq, const double* X, int64_t ldx, int fp64_products,
+                     mrcqr_stream_t stream);
 
 /* Allocation-free variant of mrcqr_sketch_qr.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory

@@ -261,6 +261,35 @@ def trsm_right_upper(A: np.ndarray, R: np.ndarray) -> np.ndarray:
     return W
 
 
+def two_product(a: np.ndarray, b: np.ndarray):
+    """Error-free product a * b = p + e (Dekker 1971, with Veltkamp's split
+    into 26-bit halves); exact unless a product under- or overflows."""
+    def split(x):
+        c = 134217729.0 * x          # 2^27 + 1
+        hi = c - (c - x)
+        return hi, x - hi
+    p = a * b
+    ah, al = split(a)
+    bh, bl = split(b)
+    e = ((ah * bh - p) + ah * bl + al * bh) + al * bl
+    return p, e
+
+
+def product_rounded(W: np.ndarray, X: np.ndarray, rows=None) -> np.ndarray:
+    """W X with every entry the exact sum sum_k W_ik X_kj rounded once to FP64
+    (the reference for the Q = W R_c^{-1} product of Algorithm 1 step 3 when
+    it is evaluated exactly or in emulated FP64): each product split into
+    p + e by ``two_product``, the 2K terms summed by math.fsum, which returns
+    the correctly rounded sum.  ``rows`` restricts the result to those rows."""
+    rows = np.arange(W.shape[0]) if rows is None else np.asarray(rows)
+    out = np.empty((len(rows), X.shape[1]))
+    for t, i in enumerate(rows):
+        p, e = two_product(W[i][:, None], X)          # K x n
+        for j in range(X.shape[1]):
+            out[t, j] = math.fsum(np.concatenate([p[:, j], e[:, j]]).tolist())
+    return out
+
+
 class CholeskyBreakdown(ArithmeticError):
     pass
 

@@ -23,7 +23,8 @@ class MrcqrError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("s_factor", ctypes.c_int32), ("check", ctypes.c_int32), ("escalate", ctypes.c_int32),
-                ("sketch_variant", ctypes.c_int32), ("ortho_tol", ctypes.c_double), ("stats_device", ctypes.c_void_p)]
+                ("sketch_variant", ctypes.c_int32), ("ortho_tol", ctypes.c_double), ("stats_device", ctypes.c_void_p),
+                ("fp64_products", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class BatchedOpts(ctypes.Structure):
@@ -74,6 +75,8 @@ SIGNATURES = {
     "mrcqr_sketch_qr": ([_i64, _i64, _vp, _i32, _vp, _vp], _i32),
     "mrcqr_last_sketch_variant": ([], _i32),
     "mrcqr_cholqr_precond": ([_i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp], _i32),
+    "mrcqr_finalize_q": ([_i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp], _i32),
+    "mrcqr_gram": ([_i64, _i64, _vp, _i64, _vp, _i32, _vp], _i32),
     "mrcqr_sketch_qr_noalloc": ([_i64, _i64, _vp, _i32, _vp, _vp], _i32),
     "mrcqr_selector_num_params": ([], _i32),
     "mrcqr_selector_set": ([_vp, _vp, _vp, _vp], _i32),

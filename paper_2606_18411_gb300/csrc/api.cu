@@ -26,7 +26,9 @@ struct Plan {
   int64_t m = 0;
   int n = 0, s = 0, npad = 0, chunks = 0, splits = 0;
   size_t off_ctl = 0, off_idx = 0, off_tab = 0, off_tabf = 0, off_ypart = 0, off_y = 0, off_sqr = 0, off_rs = 0, off_rst = 0,
-         off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, off_feat = 0, total = 0;
+         off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, off_feat = 0, off_oze = 0, off_ozx = 0,
+         off_colhi = 0, off_ozpart = 0, total = 0;
+  SyrkOzPlan oz{};
 };
 
 Plan make_plan(int64_t m, int n, int s) {
@@ -58,6 +60,11 @@ Plan make_plan(int64_t m, int n, int s) {
   p.off_xt = take(sizeof(double) * (size_t)n * p.npad);
   p.off_e = take(sizeof(double) * (size_t)n * n);
   p.off_feat = take(sizeof(float) * kNumFeatures);
+  p.off_oze = take(sizeof(uint32_t) * (size_t)((n + 63) / 64 * 64));
+  p.off_ozx = take(oz_xs_bytes(n));
+  p.oz = syrk_oz_plan(m, n);
+  p.off_colhi = take(syrk_oz_colhi_bytes(n));
+  p.off_ozpart = take(syrk_oz_part_bytes(p.oz));
   p.total = o;
   return p;
 }
@@ -209,22 +216,37 @@ int make_ladder(int p, bool escalate, int* lv) {
 int g_sketch_variant_last = 0;
 
 void enqueue_stage2(const Plan& p, void* ws, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
-                    int64_t ldr, int check, Ctl* ctl, int lvl, cudaStream_t st) {
+                    int64_t ldr, int check, Ctl* ctl, int lvl, cudaStream_t st, int fp64_products = 0) {
   double* RsT = at<double>(ws, p.off_rst);
   double* rinv = at<double>(ws, p.off_rinv);
   double* Gpart = at<double>(ws, p.off_gpart);
   double* Rc = at<double>(ws, p.off_rc);
   double* XT = at<double>(ws, p.off_xt);
   double* Rs = at<double>(ws, p.off_rs);
+  uint32_t* colhi = at<uint32_t>(ws, p.off_colhi);
+  long long* ozpart = at<long long>(ws, p.off_ozpart);
+  const bool emu = fp64_products == 0;
   launch(SG_TRSM, lvl, st, [&] { launch_trsm(p.m, p.n, A, lda, RsT, rinv, Q, ldq, ctl, lvl, st); });
-  launch(SG_SYRK, lvl, st, [&] { launch_syrk(p.m, p.n, Q, ldq, p.splits, Gpart, ctl, lvl, st); });
   double* E = at<double>(ws, p.off_e);
-  launch(SG_GREDUCE, lvl, st, [&] { launch_reduce_partials(p.n, p.splits, Gpart, Rc, ctl, lvl, st); });
+  if (emu) {
+    launch(SG_SYRK, lvl, st, [&] { launch_syrk_oz(p.m, p.n, Q, ldq, p.oz, colhi, ozpart, Rc, ctl, lvl, st); });
+  } else {
+    launch(SG_SYRK, lvl, st, [&] { launch_syrk(p.m, p.n, Q, ldq, p.splits, Gpart, ctl, lvl, st); });
+    launch(SG_GREDUCE, lvl, st, [&] { launch_reduce_partials(p.n, p.splits, Gpart, Rc, ctl, lvl, st); });
+  }
   launch(SG_CHOL, lvl, st, [&] { launch_chol(p.n, Rc, ctl, lvl, st); });
   launch(SG_TRINV, lvl, st, [&] { launch_trinv(p.n, Rc, XT, ctl, lvl, st); });
   launch(SG_RMUL, lvl, st, [&] { launch_rmul(p.n, Rc, Rs, R, ldr, ctl, lvl, st); });
-  launch(SG_FINALIZE, lvl, st, [&] { launch_finalize(p.m, p.n, Q, ldq, XT, ctl, lvl, st); });
-  if (check) {
+  if (!emu)
+    launch(SG_FINALIZE, lvl, st, [&] { launch_finalize(p.m, p.n, Q, ldq, XT, ctl, lvl, st); });
+  else
+    launch(SG_FINALIZE, lvl, st, [&] {
+      launch_finalize_oz(p.m, p.n, Q, ldq, XT, at<uint32_t>(ws, p.off_oze), at<unsigned char>(ws, p.off_ozx), ctl,
+                         lvl, st);
+    });
+  if (check && emu) {
+    launch(SG_CHECK, lvl, st, [&] { launch_syrk_oz(p.m, p.n, Q, ldq, p.oz, colhi, ozpart, E, ctl, lvl, st); });
+  } else if (check) {
     launch(SG_CHECK, lvl, st, [&] { launch_syrk(p.m, p.n, Q, ldq, p.splits, Gpart, ctl, lvl, st); });
     launch(SG_EREDUCE, lvl, st, [&] { launch_reduce_partials(p.n, p.splits, Gpart, E, ctl, lvl, st); });
   }
@@ -268,6 +290,7 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
   const bool escalate = opts ? (opts->escalate != 0) : true;
   const double tol = (opts && opts->ortho_tol > 0) ? opts->ortho_tol : kDefaultTol;
   const int variant = opts ? opts->sketch_variant : 0;
+  const int fp64p = opts ? opts->fp64_products : 0;
   int rc = validate(m, n, A, lda, Q, ldq, R, ldr, s_factor);
   if (rc != MRCQR_OK) return rc;
   if (sketch_prec < P_FP16 || sketch_prec > P_AUTO) return MRCQR_ERR_INVALID;
@@ -312,7 +335,7 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
       launch(SG_FEATURES, 0, st, [&] { launch_features(at<double>(ws, p.off_rs), (int)n, m, feat, ctl, 0, st); });
       launch(SG_SELECT, 0, st, [&] { launch_mlp_select(feat, ctl, st); });
     }
-    enqueue_stage2(p, ws, A, lda, Q, ldq, R, ldr, check, ctl, L, st);
+    enqueue_stage2(p, ws, A, lda, Q, ldq, R, ldr, check, ctl, L, st, fp64p);
   }
   launch(SG_STATS, 0, st, [&] { k_write_stats<<<1, 1, 0, st>>>(ctl, slot); });
   if (opts && opts->stats_device)
@@ -434,6 +457,66 @@ int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, con
   launch(SG_PREP, 0, st, [&] { launch_rs_prepare((int)n, Rs, at<double>(ws, p.off_rst), at<double>(ws, p.off_rinv), st); });
   enqueue_stage2(p, ws, A, lda, Q, ldq, R, ldr, 1, ctl, 0, st);
   launch(SG_STATS, 0, st, [&] { k_write_stats<<<1, 1, 0, st>>>(ctl, slot); });
+  cudaFreeAsync(ws, st);
+  return finish(st);
+}
+
+int mrcqr_gram(int64_t m, int64_t n, const double* W, int64_t ldw, double* G, int fp64_products,
+               mrcqr_stream_t stream) {
+  if (!W || !G || n < 1 || n > kMaxN || m < 1 || m >= (int64_t(1) << 31) || ldw < m ||
+      (fp64_products != 0 && fp64_products != 1))
+    return MRCQR_ERR_INVALID;
+  const size_t wbytes = sizeof(double) * (size_t)((n - 1) * ldw + m);
+  if (overlaps(W, wbytes, G, sizeof(double) * (size_t)(n * n))) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(m, (int)n, (int)n);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, p.total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCQR_ERR_ALLOC;
+  }
+  Ctl* ctl = at<Ctl>(ws, p.off_ctl);
+  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  if (fp64_products == 0) {
+    launch(SG_SYRK, 0, st, [&] {
+      launch_syrk_oz(m, (int)n, W, ldw, p.oz, at<uint32_t>(ws, p.off_colhi), at<long long>(ws, p.off_ozpart), G, ctl,
+                     0, st);
+    });
+  } else {
+    double* Gpart = at<double>(ws, p.off_gpart);
+    launch(SG_SYRK, 0, st, [&] { launch_syrk(m, (int)n, W, ldw, p.splits, Gpart, ctl, 0, st); });
+    launch(SG_GREDUCE, 0, st, [&] { launch_reduce_partials((int)n, p.splits, Gpart, G, ctl, 0, st); });
+  }
+  cudaFreeAsync(ws, st);
+  return finish(st);
+}
+
+int mrcqr_finalize_q(int64_t m, int64_t n, double* Q, int64_t ldq, const double* X, int64_t ldx, int fp64_products,
+                     mrcqr_stream_t stream) {
+  if (!Q || !X || n < 1 || n > kMaxN || m < 1 || m >= (int64_t(1) << 31) || ldq < m || ldx < n ||
+      (fp64_products != 0 && fp64_products != 1))
+    return MRCQR_ERR_INVALID;
+  const size_t qbytes = sizeof(double) * (size_t)((n - 1) * ldq + m);
+  const size_t xbytes = sizeof(double) * (size_t)((n - 1) * ldx + n);
+  if (overlaps(Q, qbytes, X, xbytes)) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(m, (int)n, (int)n);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, p.total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCQR_ERR_ALLOC;
+  }
+  Ctl* ctl = at<Ctl>(ws, p.off_ctl);
+  double* XT = at<double>(ws, p.off_xt);
+  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  launch(SG_PREP, 0, st, [&] { launch_upper_to_xt((int)n, X, ldx, XT, st); });
+  if (fp64_products == 1)
+    launch(SG_FINALIZE, 0, st, [&] { launch_finalize(m, (int)n, Q, ldq, XT, ctl, 0, st); });
+  else
+    launch(SG_FINALIZE, 0, st, [&] {
+      launch_finalize_oz(m, (int)n, Q, ldq, XT, at<uint32_t>(ws, p.off_oze), at<unsigned char>(ws, p.off_ozx), ctl,
+                         0, st);
+    });
   cudaFreeAsync(ws, st);
   return finish(st);
 }

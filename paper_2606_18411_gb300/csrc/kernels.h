@@ -99,11 +99,28 @@ void launch_reduce_partials(int n, int splits, const double* part, double* out, 
                             cudaStream_t st);
 void launch_chol(int n, double* G, Ctl* ctl, int level, cudaStream_t st);
 void launch_trinv(int n, const double* Rc, double* RcinvT, const Ctl* ctl, int level, cudaStream_t st);
+void launch_upper_to_xt(int n, const double* X, int64_t ldx, double* XT, cudaStream_t st);
 void launch_rmul(int n, const double* Rc, const double* Rs, double* R, int64_t ldr, const Ctl* ctl, int level,
                  cudaStream_t st);
 void launch_finalize(int64_t m, int n, double* Q, int64_t ldq, const double* XT, const Ctl* ctl, int level,
                      cudaStream_t st);
 void launch_judge(int n, const double* E, int check, Ctl* ctl, int level, cudaStream_t st);
+
+// --- emulated FP64 products on tensor cores (ozaki.cu) ---------------------------
+size_t oz_xs_bytes(int n);
+struct SyrkOzPlan {     // emulated-FP64 Gram: output tiles (128 x 64) and row slabs
+  int ntiles, slabs;
+  int64_t rows_per_slab;
+  int8_t ti[20], tj[20];       // I block (128 columns), J block (64 columns) of each tile
+  int8_t tile_of[4][8];        // (I, J) -> tile, -1 where no tile
+};
+SyrkOzPlan syrk_oz_plan(int64_t m, int n);
+size_t syrk_oz_part_bytes(const SyrkOzPlan& P);
+size_t syrk_oz_colhi_bytes(int n);
+void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOzPlan& P, uint32_t* colHi,
+                    long long* part, double* out, Ctl* ctl, int level, cudaStream_t st);
+void launch_finalize_oz(int64_t m, int n, double* Q, int64_t ldq, const double* XT, uint32_t* colE,
+                        unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st);
 
 // --- learned selector (selector.cu) --------------------------------------------
 int selector_num_params();

@@ -1,0 +1,165 @@
+// FP64 products on FP16 tensor cores by exact integer slicing (the
+// error-free splitting of Ozaki, Ogita, Oishi, Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 59, 2012), with
+// balanced (signed) base-256 digits.
+//
+// A value x of a row (or column) whose largest magnitude has biased FP64
+// exponent Eref is rounded to the 63-bit fixed-point integer
+//   I = round(|x| 2^(1085 - Eref)),   0 <= I < 2^63
+// (exact for every x within 2^10 of the maximum), and I is written in eight
+// signed base-256 digits
+//   I = sum_{a=0..7} d_a 2^(56 - 8a),  d_0 in [0, 128], d_{a>0} in [-128, 127],
+// each exact in FP16 (the sign of x is applied to every digit).  A product
+// sum_k x_ik y_kj keeps the digit pairs with a + b <= 7; the pairs of one
+// level L = a + b are accumulated together in FP32 by tcgen05.mma.  Per term
+// a level sums at most 2^15 + 6 * 2^14 = 2^17 in magnitude, so a level
+// accumulated over K <= 128 terms is an integer of magnitude <= 2^24, exact in
+// FP32.  The levels are combined with 64-bit integer arithmetic into the
+// 128-bit
+//   T = sum_L acc_L 2^(8(7-L)) = (sum_{L<4} acc_L 2^(8(3-L))) 2^32 + sum_{L>=4} acc_L 2^(8(7-L))
+// and T 2^(Erow + Ecol - 2114) is rounded once to FP64.  With R_i, C_j the
+// row and column maxima (R_i >= 2^61 units of I), the rounding of I costs at
+// most 2^-62 R_i per operand and the dropped pairs (a + b >= 8, at most
+// 7 * 2^14 of their level units) at most 7.03 * 2^-60 R_i C_j per term, so
+// one term is off by less than 2^-57 R_i C_j, 16 times below the unit
+// roundoff; the sum is rounded once.  Everything outside the tensor cores is
+// 32/64-bit integer work (FP64 instructions issue to a 1/64-rate pipe on this
+// GPU).
+#pragma once
+#include <cstdint>
+#include "common.cuh"
+
+namespace mrcqr {
+namespace oz {
+
+constexpr int kSlices = 8;
+constexpr int kLevels = 8;
+constexpr int kScaleBias = 2114;   // T 2^(Erow + Ecol - kScaleBias) is the product
+
+// Biased FP64 exponent field of |x| from its high word (0 for zero and
+// subnormals, which slice to zero against any normal reference).
+__device__ __forceinline__ uint32_t exp_field(uint32_t hi) { return (hi >> 20) & 0x7FFu; }
+
+// Signed digits d[0..7] of x (FP64 bits hi:lo) against the reference
+// exponent Eref (biased exponent of the row maximum, >= the exponent of x),
+// sign of x included.  Zero, subnormals and a zero reference give zeros.
+__device__ __forceinline__ void digits8(uint32_t hi, uint32_t lo, uint32_t Eref, int* d) {
+  const uint32_t E = exp_field(hi);
+  int64_t v = 0;
+  if (E != 0 && Eref != 0) {
+    const uint64_t M = ((uint64_t)(hi & 0xFFFFFu) << 32 | lo) | (1ull << 52);
+    const int sh = (int)E - (int)Eref + 10;   // I = round(M 2^sh), sh <= 10
+    if (sh >= 0) v = (int64_t)(M << sh);
+    else if (sh > -64) v = (int64_t)((M + (1ull << (-sh - 1))) >> (-sh));
+  }
+#pragma unroll
+  for (int a = kSlices - 1; a > 0; --a) {
+    d[a] = (int)((v + 128) & 255) - 128;
+    v = (v - d[a]) >> 8;
+  }
+  d[0] = (int)v;
+  if (hi >> 31) {
+#pragma unroll
+    for (int a = 0; a < kSlices; ++a) d[a] = -d[a];
+  }
+}
+
+// Exact float of a small signed integer (|v| < 2^22) without a conversion
+// instruction: 1.5 * 2^23 + v has v in its low mantissa bits.
+__device__ __forceinline__ float small_int_to_float(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+
+// Packed FP16 pair of two signed digits.
+__device__ __forceinline__ uint32_t pack_f16x2(int v0, int v1) {
+  const __half2 h = __floats2half2_rn(small_int_to_float(v0), small_int_to_float(v1));
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Adds one level's exact FP32 accumulator (an integer, |v| <= 2^24) into the
+// 64-bit halves of T.
+__device__ __forceinline__ void add_level(int L, float v, long long& hi, long long& lo) {
+  const long long iv = (long long)__float2int_rn(v);
+  if (L < 4) hi += iv << (8 * (3 - L));
+  else lo += iv << (8 * (7 - L));
+}
+
+// Signed 128-bit integer as (high word th, low word tl): two's complement.
+struct I128 {
+  int64_t h;
+  uint64_t l;
+};
+
+__device__ __forceinline__ I128 i128_from_parts(long long hi, long long lo) {   // hi 2^32 + lo
+  I128 r;
+  const uint64_t tl = (uint64_t)hi << 32;
+  r.h = hi >> 32;
+  r.l = tl + (uint64_t)lo;
+  r.h += (lo >> 63) + (r.l < tl ? 1 : 0);
+  return r;
+}
+
+__device__ __forceinline__ void i128_add(I128& a, const I128& b) {
+  const uint64_t l = a.l + b.l;
+  a.h += b.h + (l < a.l ? 1 : 0);
+  a.l = l;
+}
+
+// T 2^scale rounded once to FP64 (round to nearest even).
+__device__ __forceinline__ double i128_to_double(I128 t, int scale) {
+  uint64_t tl = t.l;
+  int64_t th = t.h;
+  const bool neg = th < 0;
+  if (neg) {
+    tl = ~tl + 1ull;
+    th = (int64_t)(~(uint64_t)th + (tl == 0 ? 1ull : 0ull));
+  }
+  const uint64_t uh = (uint64_t)th;
+  if (uh == 0 && tl == 0) return neg ? -0.0 : 0.0;
+  const int p = uh ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)tl);   // msb position
+  uint64_t m;
+  int e2 = p;   // value = m 2^(p - 52) before scaling
+  if (p <= 52) {
+    m = tl << (52 - p);
+  } else {
+    const int sh = p - 52;   // 1 .. 75
+    uint64_t q, rem_hi_bit, sticky;
+    if (sh < 64) {
+      q = (tl >> sh) | (uh << (64 - sh));
+      rem_hi_bit = (tl >> (sh - 1)) & 1ull;
+      sticky = tl & ((1ull << (sh - 1)) - 1ull);
+    } else {
+      const int s2 = sh - 64;   // 0 .. 11
+      q = uh >> s2;
+      if (s2 == 0) {
+        rem_hi_bit = tl >> 63;
+        sticky = tl & 0x7FFFFFFFFFFFFFFFull;
+      } else {
+        rem_hi_bit = (uh >> (s2 - 1)) & 1ull;
+        sticky = (uh & ((1ull << (s2 - 1)) - 1ull)) | tl;
+      }
+    }
+    m = q;
+    if (rem_hi_bit && (sticky || (m & 1ull))) ++m;
+    if (m >> 53) {
+      m >>= 1;
+      ++e2;
+    }
+  }
+  const int E = e2 + scale + 1023;
+  if (E <= 0 || E >= 2047) {   // outside the normal range (subnormal results are rounded twice)
+    const double v = ldexp((double)(m & ((1ull << 53) - 1ull)), e2 - 52 + scale);
+    return neg ? -v : v;
+  }
+  const uint64_t bits = ((uint64_t)(neg ? 1 : 0) << 63) | ((uint64_t)E << 52) | (m & ((1ull << 52) - 1ull));
+  return __longlong_as_double((long long)bits);
+}
+
+// (hi 2^32 + lo) 2^scale rounded once to FP64.
+__device__ __forceinline__ double i128_to_double(long long hi, long long lo, int scale) {
+  return i128_to_double(i128_from_parts(hi, lo), scale);
+}
+
+}  // namespace oz
+}  // namespace mrcqr

@@ -152,13 +152,32 @@ __global__ void __launch_bounds__(32 * (TN / 16) * (TN / 16)) k_syrk(int64_t m, 
 static int syrk_tile(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : 64); }
 int syrk_tile_for(int n) { return syrk_tile(n); }
 
+// CTAs of k_syrk<TN> that fit on the GPU at once (SMs x resident CTAs per SM).
+static int syrk_slots(int TN) {
+  static int cached[3] = {0, 0, 0};
+  const int slot = TN == 16 ? 0 : (TN == 32 ? 1 : 2);
+  if (cached[slot] == 0) {
+    int dev = 0, sms = 152, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int threads = 32 * (TN / 16) * (TN / 16);
+    if (TN == 16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_syrk<16>, threads, 0);
+    else if (TN == 32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_syrk<32>, threads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_syrk<64>, threads, 0);
+    cudaGetLastError();
+    cached[slot] = sms * (per > 0 ? per : 1);
+  }
+  return cached[slot];
+}
+
 int syrk_splits(int64_t m, int n) {
   const int TN = syrk_tile(n);
   const int nt = (n + TN - 1) / TN;
   const int tiles = nt * (nt + 1) / 2;
-  // enough CTAs to fill the GPU a few times over; each split >= 256 rows
-  int splits = (8 * 152 + tiles - 1) / tiles;
-  const int64_t maxs = (m + 255) / 256;
+  // about eight full waves of CTAs, so the last partial wave costs little;
+  // each split keeps at least 64 rows
+  int splits = (8 * syrk_slots(TN) + tiles - 1) / tiles;
+  const int64_t maxs = (m + 63) / 64;
   if (splits > maxs) splits = (int)maxs;
   return splits < 1 ? 1 : splits;
 }
@@ -354,6 +373,21 @@ __global__ void __launch_bounds__(128) k_finalize(int64_t m, int n, double* __re
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < m) finalize_row(r, n, Q, ldq, XT);
+}
+
+// X (column-major, ld ldx, upper triangle read) into the transposed padded
+// triangle XT[k][j] = X[k][j] (k <= j), zero elsewhere.
+__global__ void k_upper_to_xt(int n, int npad, const double* __restrict__ X, int64_t ldx, double* __restrict__ XT) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * npad) return;
+  const int k = (int)(e / npad), j = (int)(e % npad);
+  XT[e] = (j < n && k <= j) ? X[k + (int64_t)j * ldx] : 0.0;
+}
+
+void launch_upper_to_xt(int n, const double* X, int64_t ldx, double* XT, cudaStream_t st) {
+  const int npad = padded(n);
+  const int64_t total = (int64_t)n * npad;
+  k_upper_to_xt<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, npad, X, ldx, XT);
 }
 
 void launch_finalize(int64_t m, int n, double* Q, int64_t ldq, const double* XT, const Ctl* ctl, int level,

@@ -18,10 +18,16 @@ __all__ = ["factor", "factor_ex", "last_status", "factor_batched", "signs", "sam
            "cholqr_precond", "empty_colmajor", "to_colmajor", "version", "PREC", "PREC_NAME", "MrcqrError"]
 
 
+_selector_state = {"loaded": False}
+
+
 def _prec(p) -> int:
-    if isinstance(p, str):
-        return PREC[p.lower()]
-    return int(p)
+    v = PREC[p.lower()] if isinstance(p, str) else int(p)
+    if v == PREC["auto"] and not _selector_state["loaded"]:
+        # the automatic choice needs selector weights: the shipped ones unless the caller set others
+        from . import selector
+        selector.load_into_library()
+    return v
 
 
 def _stream(stream) -> int:
@@ -61,12 +67,12 @@ def version() -> int:
 
 def factor_ex(A: torch.Tensor, Q: torch.Tensor, R: torch.Tensor, prec="fp64", seed: int = 0, s_factor: int = 2,
               check_ortho: bool = True, escalate: bool = True, tol: float = 1e-13, stats_device=None,
-              sketch_variant: int = 0, stream=None) -> None:
+              sketch_variant: int = 0, fp64_products: int = 0, stream=None) -> None:
     """Enqueue MRCQR of A into Q (m x n) and R (n x n); asynchronous."""
     m, n = A.shape
     o = Opts(s_factor=s_factor, check=int(check_ortho), escalate=int(escalate), sketch_variant=sketch_variant,
-             ortho_tol=tol,
-             stats_device=stats_device.data_ptr() if stats_device is not None else None)
+             ortho_tol=tol, stats_device=stats_device.data_ptr() if stats_device is not None else None,
+             fp64_products=fp64_products, reserved1=0)
     rc = _lib.load().mrcqr_factor_ex(m, n, A.data_ptr(), _ld(A, "A"), Q.data_ptr(), _ld(Q, "Q"), R.data_ptr(),
                                      _ld(R, "R"), _prec(prec), seed, ctypes.byref(o), _stream(stream))
     check(rc, "mrcqr_factor_ex")
@@ -212,3 +218,20 @@ def cholqr_precond(A: torch.Tensor, Rs: torch.Tensor, stream=None):
                                            _ld(Q, "Q"), R.data_ptr(), _ld(R, "R"), _stream(stream)),
           "mrcqr_cholqr_precond")
     return Q, R
+
+
+def finalize_q(W: torch.Tensor, X: torch.Tensor, fp64_products: int = 0, stream=None) -> torch.Tensor:
+    """Q = W X with X upper triangular (the upper triangle of X is read); W is overwritten."""
+    m, n = W.shape
+    check(_lib.load().mrcqr_finalize_q(m, n, W.data_ptr(), _ld(W, "W"), X.data_ptr(), _ld(X, "X"),
+                                       int(fp64_products), _stream(stream)), "mrcqr_finalize_q")
+    return W
+
+
+def gram(W: torch.Tensor, fp64_products: int = 0, stream=None) -> torch.Tensor:
+    """Upper triangle of W^T W (strictly lower triangle zero), n x n column-major."""
+    m, n = W.shape
+    G = empty_colmajor(n, n, device=W.device)
+    check(_lib.load().mrcqr_gram(m, n, W.data_ptr(), _ld(W, "W"), G.data_ptr(), int(fp64_products),
+                                 _stream(stream)), "mrcqr_gram")
+    return G

@@ -171,6 +171,14 @@ def save_weights(path, params, mu, sd, costs):
 
 def load_into_library(path: str = DEFAULT_WEIGHTS) -> None:
     _lib.check(_lib.load().mrcqr_selector_load(path.encode()), "mrcqr_selector_load")
+    M._selector_state["loaded"] = True
+
+
+def set_weights(params, mu, sd, costs) -> None:
+    """Install weights held in memory (FP32 arrays) into the library."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (params, mu, sd, costs)]
+    _lib.check(_lib.load().mrcqr_selector_set(*[a.ctypes.data for a in arrs]), "mrcqr_selector_set")
+    M._selector_state["loaded"] = True
 
 
 def measure_costs(m=1 << 16, n=144, reps=5, device="cuda"):

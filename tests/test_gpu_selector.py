@@ -101,14 +101,12 @@ def test_training_on_gpu_reduces_loss(env):
 @pytest.mark.parametrize("forced", [0, 1, 2])
 def test_auto_path_follows_selector_choice(env, forced):
     torch, M, S = env
-    from paper_2606_18411_gb300 import _lib
     # weights whose output bias forces the class `forced`
     theta = np.zeros(SO.NUM_PARAMS, np.float32)
     theta[-3:] = -40.0
     theta[-3 + forced] = 40.0
     mu, sd, costs = np.zeros(16, np.float32), np.ones(16, np.float32), np.array([1, 1.02, 1.9], np.float32)
-    lib = _lib.load()
-    assert lib.mrcqr_selector_set(theta.ctypes.data, mu.ctypes.data, sd.ctypes.data, costs.ctypes.data) == 0
+    S.set_weights(theta, mu, sd, costs)
     A = inputs.make_matrix(8192, 48, 1e6, seed=44)
     Q, R = M.factor(M.to_colmajor(A), prec="auto", seed=2)
     st = M.last_status()
@@ -118,3 +116,33 @@ def test_auto_path_follows_selector_choice(env, forced):
     assert st["prec_used"] == ("fp32" if forced == 0 else ["fp16", "fp32", "fp64"][forced])
     assert O.orthogonality_error(Q.cpu().numpy())[0] <= 1e-13
     assert O.residual_error(A, Q.cpu().numpy(), R.cpu().numpy())[0] <= 1e-13
+
+
+def test_shipped_selector_saves_work_on_held_out_mix(env):
+    """AUTO with the shipped weights on matrices outside the training set:
+    every factorization succeeds (escalation covers a low choice), and the
+    ladder cost of the chosen starts is well below always starting at FP32
+    or FP64 (relative costs stored with the weights)."""
+    torch, M, S = env
+    S.load_into_library()
+    costs = [1.0, 1.0221676451029789, 2.0229150120955177]
+    rng = np.random.default_rng(77)
+    m = 1 << 14
+    tot = {"auto": 0.0, "fp32": 0.0, "fp64": 0.0}
+    levels = ["fp16", "fp32", "fp64"]
+    for i in range(48):
+        n = int(rng.choice([48, 96, 160]))
+        kind = inputs.SPECTRA[int(rng.integers(len(inputs.SPECTRA)))]
+        kappa = float(10.0 ** rng.uniform(0.0, 16.0))
+        A = inputs.make_matrix_torch(m, n, kappa, kind=kind, seed=7_000_003 + i, device="cuda")
+        Q = M.empty_colmajor(m, n)
+        R = M.empty_colmajor(n, n)
+        M.factor_ex(A, Q, R, prec="auto", seed=i)
+        st = M.last_status()
+        assert st["status"] == "OK", (i, n, kappa, kind, st)
+        first, used = levels.index(st["prec_first"]), levels.index(st["prec_used"])
+        tot["auto"] += sum(costs[first:used + 1])
+        label = 0 if S.passes(A, "fp16", seed=i) else (1 if S.passes(A, "fp32", seed=i) else 2)
+        tot["fp32"] += costs[1] if label <= 1 else costs[1] + costs[2]
+        tot["fp64"] += costs[2]
+    assert tot["auto"] <= 0.95 * min(tot["fp32"], tot["fp64"]), tot

@@ -349,3 +349,34 @@ def test_dd_dot_beats_naive_on_cancellation():
     x = np.array([1e16, 1.0, -1e16])
     y = np.array([1.0, 1.0, 1.0])
     assert O.dd_dot(x, y) == 1.0
+
+
+def test_two_product_is_error_free():
+    rng = np.random.default_rng(11)
+    a = rng.standard_normal(200) * 2.0 ** rng.integers(-40, 40, 200)
+    b = rng.standard_normal(200) * 2.0 ** rng.integers(-40, 40, 200)
+    p, e = O.two_product(a, b)
+    for i in range(200):
+        assert Fraction(float(p[i])) + Fraction(float(e[i])) == Fraction(float(a[i])) * Fraction(float(b[i]))
+
+
+def test_product_rounded_is_correctly_rounded_exact_sum():
+    rng = np.random.default_rng(12)
+    W = rng.standard_normal((6, 9)) * 2.0 ** rng.integers(-30, 30, (6, 9))
+    X = np.triu(rng.standard_normal((9, 9)) * 2.0 ** rng.integers(-30, 30, (9, 9)))
+    Q = O.product_rounded(W, X)
+    for i in range(6):
+        for j in range(9):
+            exact = sum(Fraction(float(W[i, k])) * Fraction(float(X[k, j])) for k in range(9))
+            assert Q[i, j] == float(exact)          # float(Fraction) rounds to nearest
+    sub = O.product_rounded(W, X, rows=[4, 1])
+    np.testing.assert_array_equal(sub, Q[[4, 1]])
+
+
+def test_product_rounded_cancellation_and_integers():
+    W = np.array([[1.0, 1e-20, -1.0]])
+    assert O.product_rounded(W, np.ones((3, 1)))[0, 0] == 1e-20
+    rng = np.random.default_rng(13)
+    Wi = rng.integers(-1000, 1000, (20, 12)).astype(float)
+    Xi = np.triu(rng.integers(-1000, 1000, (12, 12))).astype(float)
+    np.testing.assert_array_equal(O.product_rounded(Wi, Xi), Wi @ Xi)
