@@ -65,7 +65,9 @@ typedef struct mrcqr_opts {
   int32_t escalate;   /* 1 (default): on failure re-run at the next precision (Sec. II-C),
                          FP16/BF16 -> FP32 -> FP64 */
   int32_t sketch_variant; /* 0 (default): tensor-core sketch for FP16/BF16/FP32 when A is 16-byte aligned
-                             and lda is even, SIMT otherwise; 1: SIMT; 2: tensor cores when possible */
+                             and lda is even, SIMT otherwise; the FP64 sketch as emulated FP64 on the
+                             tensor cores (unless fp64_products = 1); 1: SIMT (FP64 FMA for FP64);
+                             2: tensor cores when possible */
   double ortho_tol;   /* acceptance threshold on ||I - Q^T Q||_F (default 1e-13) */
   void* stats_device; /* optional DEVICE pointer to an mrcqr_stats_t written at the end */
   int32_t fp64_products; /* 0 (default): the Gram matrix W^T W, the product Q = W R_c^{-1} and
@@ -282,7 +284,8 @@ int mrcqr_mlp_train_step(int batch, const float* X, const int32_t* y, const floa
 /* ---- instrumentation (per-kernel timing) ------ */
 
 /* Sketch kernel variant used by the most recent sketch launch of this
- * process: 1 SIMT, 2 tensor cores (0 before any). */
+ * process: 1 SIMT, 2 tensor cores, 3 emulated FP64 on the tensor cores
+ * (0 before any). */
 int mrcqr_last_sketch_variant(void);
 
 /* Number of kernels this library has launched in this process. */

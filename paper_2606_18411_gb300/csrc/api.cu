@@ -1,5 +1,6 @@
 // C ABI of the MRCQR library: argument checks, the workspace plan, the
 // escalation ladder of Sec. II-C and the per-stream status records.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -29,6 +30,7 @@ struct Plan {
          off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, off_feat = 0, off_oze = 0, off_ozx = 0,
          off_colhi = 0, off_ozpart = 0, total = 0;
   SyrkOzPlan oz{};
+  SketchOzPlan sk{};
 };
 
 Plan make_plan(int64_t m, int n, int s) {
@@ -63,8 +65,9 @@ Plan make_plan(int64_t m, int n, int s) {
   p.off_oze = take(sizeof(uint32_t) * (size_t)((n + 63) / 64 * 64));
   p.off_ozx = take(oz_xs_bytes(n));
   p.oz = syrk_oz_plan(m, n);
+  p.sk = sketch_oz_plan(m, n, s);
   p.off_colhi = take(syrk_oz_colhi_bytes(n));
-  p.off_ozpart = take(syrk_oz_part_bytes(p.oz));
+  p.off_ozpart = take(std::max(syrk_oz_part_bytes(p.oz), sketch_oz_part_bytes(p.sk)));   // used one after the other
   p.total = o;
   return p;
 }
@@ -215,6 +218,30 @@ int make_ladder(int p, bool escalate, int* lv) {
 // Stage 2 + 3 for level `lvl` (R_s already in the workspace).
 int g_sketch_variant_last = 0;
 
+// Sketch Y of level `lvl` (Algorithm 2 steps 2-4).  FP64: emulated FP64 on the
+// tensor cores unless the SIMT variant or FP64-FMA products are asked for.
+// Returns the variant that ran (1 SIMT, 2 tensor cores, 3 emulated FP64).
+int enqueue_sketch(const Plan& p, void* ws, int prec, int variant, int fp64_products, const double* A, int64_t lda,
+                   uint64_t seed, double* Y, Ctl* ctl, int lvl, cudaStream_t st) {
+  const uint32_t* idx = at<uint32_t>(ws, p.off_idx);
+  const double* tab = at<double>(ws, p.off_tab);
+  int used = 0;
+  if (prec == P_FP64 && variant != 1 && fp64_products == 0) {
+    launch(SG_SKETCH, lvl, st, [&] {
+      launch_sketch_oz(p.m, p.n, p.s, A, lda, idx, tab, seed, p.sk, at<uint32_t>(ws, p.off_colhi),
+                       at<long long>(ws, p.off_ozpart), Y, ctl, lvl, st);
+    });
+    return 3;
+  }
+  double* ypart = at<double>(ws, p.off_ypart);
+  launch(SG_SKETCH, lvl, st, [&] {
+    used = launch_sketch(prec, variant, A, lda, p.m, p.n, p.s, idx, tab, at<float>(ws, p.off_tabf), seed, p.chunks,
+                         ypart, ctl, lvl, st);
+  });
+  launch(SG_SKREDUCE, lvl, st, [&] { launch_sketch_reduce(p.m, p.n, p.s, p.chunks, ypart, idx, Y, ctl, lvl, st); });
+  return used;
+}
+
 void enqueue_stage2(const Plan& p, void* ws, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
                     int64_t ldr, int check, Ctl* ctl, int lvl, cudaStream_t st, int fp64_products = 0) {
   double* RsT = at<double>(ws, p.off_rst);
@@ -319,13 +346,8 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
   launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, s, seed, idx, ctl, st); });
   launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, at<float>(ws, p.off_tabf), st); });
   for (int L = 0; L < nlevels; ++L) {
-    double* ypart = at<double>(ws, p.off_ypart);
     double* y = at<double>(ws, p.off_y);
-    launch(SG_SKETCH, L, st, [&] {
-      g_sketch_variant_last = launch_sketch(lv[L], variant, A, lda, m, (int)n, s, idx, tab, at<float>(ws, p.off_tabf),
-                                            seed, p.chunks, ypart, ctl, L, st);
-    });
-    launch(SG_SKREDUCE, L, st, [&] { launch_sketch_reduce(m, (int)n, s, p.chunks, ypart, idx, y, ctl, L, st); });
+    g_sketch_variant_last = enqueue_sketch(p, ws, lv[L], variant, fp64p, A, lda, seed, y, ctl, L, st);
     launch(SG_SQR, L, st, [&] {
       launch_sketch_qr(lv[L], (int)n, s, y, at<void>(ws, p.off_sqr), at<double>(ws, p.off_rs),
                        at<double>(ws, p.off_rst), at<double>(ws, p.off_rinv), ctl, L, st);
@@ -402,15 +424,10 @@ int mrcqr_sketch_ex(int64_t m, int64_t n, const double* A, int64_t lda, int64_t 
   Ctl* ctl = at<Ctl>(ws, p.off_ctl);
   uint32_t* idx = at<uint32_t>(ws, p.off_idx);
   double* tab = at<double>(ws, p.off_tab);
-  double* ypart = at<double>(ws, p.off_ypart);
   launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, sketch_prec, P_FP64, P_FP64, P_FP64, kDefaultTol); });
   launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, (int)s, seed, idx, ctl, st); });
   launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, at<float>(ws, p.off_tabf), st); });
-  launch(SG_SKETCH, 0, st, [&] {
-    g_sketch_variant_last = launch_sketch(sketch_prec, variant, A, lda, m, (int)n, (int)s, idx, tab,
-                                          at<float>(ws, p.off_tabf), seed, p.chunks, ypart, ctl, 0, st);
-  });
-  launch(SG_SKREDUCE, 0, st, [&] { launch_sketch_reduce(m, (int)n, (int)s, p.chunks, ypart, idx, Y, ctl, 0, st); });
+  g_sketch_variant_last = enqueue_sketch(p, ws, sketch_prec, variant, 0, A, lda, seed, Y, ctl, 0, st);
   cudaFreeAsync(ws, st);
   return finish(st);
 }

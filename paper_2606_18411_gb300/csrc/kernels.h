@@ -119,6 +119,15 @@ size_t syrk_oz_part_bytes(const SyrkOzPlan& P);
 size_t syrk_oz_colhi_bytes(int n);
 void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOzPlan& P, uint32_t* colHi,
                     long long* part, double* out, Ctl* ctl, int level, cudaStream_t st);
+struct SketchOzPlan {   // emulated-FP64 sketch: 128-column blocks of A x 64-row sample tiles x row slabs
+  int mblocks, ntiles, slabs;
+  int64_t rows_per_slab;
+};
+SketchOzPlan sketch_oz_plan(int64_t m, int n, int s);
+size_t sketch_oz_part_bytes(const SketchOzPlan& P);
+void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, const uint32_t* idx, const double* tab,
+                      uint64_t seed, const SketchOzPlan& P, uint32_t* colHi, long long* part, double* Y, Ctl* ctl,
+                      int level, cudaStream_t st);
 void launch_finalize_oz(int64_t m, int n, double* Q, int64_t ldq, const double* XT, uint32_t* colE,
                         unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st);
 

@@ -1,7 +1,8 @@
-// Stage-2 products on FP16 tensor cores with exact integer slicing (see
-// ozaki.cuh): the finalize Q = W R_c^{-1} (Algorithm 1 step 3) as an
-// emulated FP64 GEMM whose result is the correctly rounded value of a
-// 56-bit fixed-point product sum.
+// FP64 products of the method on FP16 tensor cores with exact integer
+// slicing (ozaki.cuh): the Gram matrix and the check Q^T Q (Algorithm 1
+// step 1, Sec. II-C), the finalize Q = W R_c^{-1} (Algorithm 1 step 3) and
+// the FP64 sketch (Algorithm 2 steps 2-4 at p = FP64).  Each result entry is
+// the once-rounded value of a 63-bit fixed-point evaluation of its sum.
 #include "kernels.h"
 #include "ozaki.cuh"
 #include "tc.cuh"
@@ -17,6 +18,88 @@ constexpr uint32_t kWPanel = kRowsPerCta * 128;   // one slice of a 128 x 64 FP1
 constexpr uint32_t kXPanel = kTile * 128;          // one slice of a 64 x 64 FP16 block (8 KiB)
 
 constexpr int kGroupChunks = 2;             // K chunks per exact FP32 accumulation (K <= 128)
+
+// The 36 digit-pair MMAs (levels 0..7, four K steps of 16) of one 64-deep K
+// chunk; level L accumulates in TMEM columns [64 L, 64 L + 64).  ab / bb are
+// the shared addresses of digit 0 of the A (128 rows) and B (64 rows) panels,
+// astride / bstride the distance between digits.  Issued by one thread.
+__device__ __forceinline__ void oz_issue_chunk(uint32_t tmem, uint32_t ab, uint32_t astride, uint32_t bb,
+                                               uint32_t bstride, uint32_t idesc, bool group_start) {
+#pragma unroll 1
+  for (int L = 0; L < oz::kLevels; ++L) {
+    const uint32_t d = tmem + (uint32_t)(L * kTile);
+#pragma unroll 1
+    for (int a = 0; a <= L; ++a) {
+      const int b = L - a;
+#pragma unroll
+      for (int kk = 0; kk < kTile; kk += 16) {
+        const uint32_t acc = (group_start && a == 0 && kk == 0) ? 0u : 1u;
+        tc::mma_f16(d, tc::sw128_desc(ab + a * astride + kk * 2), tc::sw128_desc(bb + b * bstride + kk * 2), idesc,
+                    acc);
+      }
+    }
+  }
+}
+
+// Adds the exact level sums of TMEM lane 32 q + lane, columns 16 g .. 16 g + 15
+// (warp w: q = w % 4, g = w / 4) into the 64-bit halves hi / lo.
+__device__ __forceinline__ void oz_readout(uint32_t tmem, int q, int g, long long* hi, long long* lo) {
+  const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 16);
+#pragma unroll 1
+  for (int L = 0; L < oz::kLevels; ++L) {
+    float v[16];
+    tc::tmem_ld16(base + (uint32_t)(L * kTile), v);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int c = 0; c < 16; ++c) oz::add_level(L, v[c], hi[c], lo[c]);
+  }
+}
+
+// Digits of a 64-row chunk of one column of a column-major matrix, against
+// the column's reference exponent E, into K-major SW128 panels: row `prow`
+// of each digit panel (panel stride pstride).  Called by a full warp: lane
+// l takes rows 2l and 2l + 1; flip64 (one bit per row) flips signs.
+__device__ __forceinline__ void oz_slice_col_chunk(const double* __restrict__ col, int64_t r0, int64_t r_end,
+                                                   uint32_t E, uint64_t flip64, unsigned char* panel, int prow,
+                                                   uint32_t pstride, int lane) {
+  const int64_t ra = r0 + 2 * lane;
+  double v0 = 0.0, v1 = 0.0;
+  if (col) {
+    if (ra < r_end) v0 = col[ra];
+    if (ra + 1 < r_end) v1 = col[ra + 1];
+  }
+  const uint32_t f0 = (uint32_t)(flip64 >> (2 * lane)) & 1u, f1 = (uint32_t)(flip64 >> (2 * lane + 1)) & 1u;
+  int d0[oz::kSlices], d1[oz::kSlices];
+  oz::digits8((uint32_t)__double2hiint(v0) ^ (f0 << 31), (uint32_t)__double2loint(v0), E, d0);
+  oz::digits8((uint32_t)__double2hiint(v1) ^ (f1 << 31), (uint32_t)__double2loint(v1), E, d1);
+  unsigned char* dst = panel + tc::sw128_offset(prow, 2 * lane, 2);
+#pragma unroll
+  for (int a = 0; a < oz::kSlices; ++a)
+    *reinterpret_cast<uint32_t*>(dst + a * pstride) = oz::pack_f16x2(d0[a], d1[a]);
+}
+
+// One item's 128 x 64 partial (hi then lo, [column][row] so that a warp's
+// stores are contiguous).
+__device__ __forceinline__ void oz_store_partial(long long* out, int q, int g, int lane, const long long* hi,
+                                                 const long long* lo) {
+  const int il = q * 32 + lane;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int jl = g * 16 + c;
+    out[jl * kRowsPerCta + il] = hi[c];
+    out[kRowsPerCta * kTile + jl * kRowsPerCta + il] = lo[c];
+  }
+}
+
+__device__ __forceinline__ oz::I128 oz_sum_partials(const long long* part, int nslabs, size_t slab_stride, int il,
+                                                    int jl) {
+  oz::I128 acc{0, 0};
+  for (int sl = 0; sl < nslabs; ++sl) {
+    const long long* pp = part + (size_t)sl * slab_stride;
+    oz::i128_add(acc, oz::i128_from_parts(pp[jl * kRowsPerCta + il], pp[kRowsPerCta * kTile + jl * kRowsPerCta + il]));
+  }
+  return acc;
+}
 
 // X = R_c^{-1} (upper, XT[k][j] row-major with row stride npad): per column
 // j the reference exponent of max_k |X[k][j]| and the eight digits of every
@@ -145,21 +228,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         __syncthreads();
         if (tid == 0) {
           tc::fence_after();
-          const uint32_t wb = tc::smem_u32(ws), xb = tc::smem_u32(xs);
-#pragma unroll 1
-          for (int L = 0; L < oz::kLevels; ++L) {
-            const uint32_t d = tmem + (uint32_t)(L * kTile);
-#pragma unroll 1
-            for (int a = 0; a <= L; ++a) {
-              const int b = L - a;
-#pragma unroll
-              for (int kk = 0; kk < kTile; kk += 16) {
-                const uint32_t acc = (group_start && a == 0 && kk == 0) ? 0u : 1u;
-                tc::mma_f16(d, tc::sw128_desc(wb + a * kWPanel + kk * 2), tc::sw128_desc(xb + b * kXPanel + kk * 2),
-                            idesc, acc);
-              }
-            }
-          }
+          oz_issue_chunk(tmem, tc::smem_u32(ws), kWPanel, tc::smem_u32(xs), kXPanel, idesc, group_start);
           tc::mma_commit(&mma_bar);
         }
         const bool ok = tc::mbar_wait(&mma_bar, phase);
@@ -169,17 +238,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           break;
         }
         tc::fence_after();
-        if (group_end) {
-          const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 16);
-#pragma unroll 1
-          for (int L = 0; L < oz::kLevels; ++L) {
-            float v[16];
-            tc::tmem_ld16(base + (uint32_t)(L * kTile), v);
-            tc::tmem_wait_ld();
-#pragma unroll
-            for (int c = 0; c < 16; ++c) oz::add_level(L, v[c], hi[c], lo[c]);
-          }
-        }
+        if (group_end) oz_readout(tmem, q, g, hi, lo);
         tc::fence_before();
         __syncthreads();
       }
@@ -289,27 +348,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int64_t r0 = r_begin + (int64_t)ch * kTile;
       const bool group_start = (ch % kGroupChunks) == 0;
       const bool group_end = (ch % kGroupChunks) == kGroupChunks - 1 || ch == nchunks - 1;
-      const int64_t ra = r0 + 2 * lane;
       // digits of W[r0 .. r0+63, column]: one column per warp, two rows per lane
-#pragma unroll 2
+#pragma unroll 1
       for (int c = warp; c < kRowsPerCta + kTile; c += kOzThreads / 32) {
         if (c >= kRowsPerCta && inner) break;
         const int col = c < kRowsPerCta ? i0 + c : j0 + c - kRowsPerCta;
-        double v0 = 0.0, v1 = 0.0;
-        if (col < n) {
-          const double* src = W + (int64_t)col * ldw;
-          if (ra < r_end) v0 = src[ra];
-          if (ra + 1 < r_end) v1 = src[ra + 1];
-        }
-        int d0[oz::kSlices], d1[oz::kSlices];
-        oz::digits8((uint32_t)__double2hiint(v0), (uint32_t)__double2loint(v0), colE[c], d0);
-        oz::digits8((uint32_t)__double2hiint(v1), (uint32_t)__double2loint(v1), colE[c], d1);
-        unsigned char* dst = c < kRowsPerCta ? as + tc::sw128_offset(c, 2 * lane, 2)
-                                             : bs + tc::sw128_offset(c - kRowsPerCta, 2 * lane, 2);
-        const uint32_t stride = c < kRowsPerCta ? kWPanel : kXPanel;
-#pragma unroll
-        for (int a = 0; a < oz::kSlices; ++a)
-          *reinterpret_cast<uint32_t*>(dst + a * stride) = oz::pack_f16x2(d0[a], d1[a]);
+        const double* src = col < n ? W + (int64_t)col * ldw : nullptr;
+        if (c < kRowsPerCta) oz_slice_col_chunk(src, r0, r_end, colE[c], 0ull, as, c, kWPanel, lane);
+        else oz_slice_col_chunk(src, r0, r_end, colE[c], 0ull, bs, c - kRowsPerCta, kXPanel, lane);
       }
       tc::fence_proxy_async();
       __syncthreads();
@@ -317,21 +363,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         tc::fence_after();
         const uint32_t ab = tc::smem_u32(as);
         const uint32_t bb = inner ? ab + (uint32_t)(j0 - i0) * 128u : tc::smem_u32(bs);
-        const uint32_t bstride = inner ? kWPanel : kXPanel;
-#pragma unroll 1
-        for (int L = 0; L < oz::kLevels; ++L) {
-          const uint32_t d = tmem + (uint32_t)(L * kTile);
-#pragma unroll 1
-          for (int a = 0; a <= L; ++a) {
-            const int b = L - a;
-#pragma unroll
-            for (int kk = 0; kk < kTile; kk += 16) {
-              const uint32_t acc = (group_start && a == 0 && kk == 0) ? 0u : 1u;
-              tc::mma_f16(d, tc::sw128_desc(ab + a * kWPanel + kk * 2), tc::sw128_desc(bb + b * bstride + kk * 2),
-                          idesc, acc);
-            }
-          }
-        }
+        oz_issue_chunk(tmem, ab, kWPanel, bb, inner ? kWPanel : kXPanel, idesc, group_start);
         tc::mma_commit(&mma_bar);
       }
       const bool ok = tc::mbar_wait(&mma_bar, phase);
@@ -341,30 +373,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         break;
       }
       tc::fence_after();
-      if (group_end) {
-        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 16);
-#pragma unroll 1
-        for (int L = 0; L < oz::kLevels; ++L) {
-          float v[16];
-          tc::tmem_ld16(base + (uint32_t)(L * kTile), v);
-          tc::tmem_wait_ld();
-#pragma unroll
-          for (int c = 0; c < 16; ++c) oz::add_level(L, v[c], hi[c], lo[c]);
-        }
-      }
+      if (group_end) oz_readout(tmem, q, g, hi, lo);
       tc::fence_before();
       __syncthreads();
     }
     if (abort) break;
-    // partial of this item: hi at [j][i], lo after it
-    long long* out = part + (size_t)item * (2 * kRowsPerCta * kTile);
-    const int il = q * 32 + lane;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int jl = g * 16 + c;
-      out[jl * kRowsPerCta + il] = hi[c];
-      out[kRowsPerCta * kTile + jl * kRowsPerCta + il] = lo[c];
-    }
+    oz_store_partial(part + (size_t)item * (2 * kRowsPerCta * kTile), q, g, lane, hi, lo);
   }
   if (abort && tid == 0) raise_level_status(ctl, ST_TIMEOUT);
   tc::fence_before();
@@ -388,14 +402,166 @@ __global__ void k_syrk_oz_reduce(int n, const uint32_t* __restrict__ colHi, Syrk
   const int I = i / kRowsPerCta, J = j / kTile;
   const int tile = P.tile_of[I][J];
   const int il = i - I * kRowsPerCta, jl = j - J * kTile;
-  oz::I128 acc{0, 0};
-  for (int s = 0; s < P.slabs; ++s) {
-    const long long* pp = part + (size_t)(s * P.ntiles + tile) * (2 * kRowsPerCta * kTile);
-    oz::i128_add(acc, oz::i128_from_parts(pp[jl * kRowsPerCta + il], pp[kRowsPerCta * kTile + jl * kRowsPerCta + il]));
-  }
+  const oz::I128 acc = oz_sum_partials(part + (size_t)tile * (2 * kRowsPerCta * kTile), P.slabs,
+                                       (size_t)P.ntiles * (2 * kRowsPerCta * kTile), il, jl);
   const uint32_t Ei = oz::exp_field(colHi[i]), Ej = oz::exp_field(colHi[j]);
   out[e] = (Ei == 2047u || Ej == 2047u) ? __longlong_as_double(0x7FF8000000000000ll)
                                         : oz::i128_to_double(acc, (int)Ei + (int)Ej - oz::kScaleBias);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 sketch (Algorithm 2 steps 2-4 with p = FP64) as an emulated GEMM:
+//   P[c][i] = sum_j (d_j A[j][c]) F[i][j],  F[i][j] = cos(pi r_ij / (2m)),
+//   r_ij = k_i (2j + 1) mod 4m,
+// with F[i][j] the FP64 quarter-wave table value (the value the FMA kernel
+// multiplies with) and d_j the Rademacher sign; then Y[i][c] =
+// sqrt(2/s) c_k(i) P[c][i].  A's columns are sliced against their maxima over
+// all m rows, the table values against 2^0 (|F| <= 1).  Work item = (block of
+// 128 columns of A, 64 sampled rows, slab of rows of A).
+__global__ void __launch_bounds__(kOzThreads, 1)
+    k_sketch_oz(int64_t m, int n, int s, const double* __restrict__ A, int64_t lda, const uint32_t* __restrict__ colHi,
+                const uint32_t* __restrict__ idx, const double* __restrict__ tab, uint2 key, SketchOzPlan P,
+                long long* __restrict__ part, Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* as = smem;                                   // 8 digits x (128 columns x 64 rows)
+  unsigned char* fs = smem + oz::kSlices * kWPanel;           // 8 digits x (64 samples x 64 rows)
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ uint32_t colE[kRowsPerCta];
+  __shared__ uint32_t flips[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (tid == 0) {
+    tc::mbar_init(&mma_bar, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = tc::idesc(tc::F16, kRowsPerCta, kTile);
+  const int q = warp & 3, g = warp >> 2;
+  const uint64_t four_m = 4ull * (uint64_t)m;
+  uint32_t phase = 0;
+  bool abort = false;
+  const int ntiles_all = P.mblocks * P.ntiles;
+  const int nitems = ntiles_all * P.slabs;
+  // transform-panel role of this thread: sample fi, rows 8 fg .. 8 fg + 7
+  const int fi = tid & (kTile - 1), fg = tid >> 6;
+
+  for (int item = blockIdx.x; item < nitems && !abort; item += gridDim.x) {
+    const int tile = item % ntiles_all, slab = item / ntiles_all;
+    const int c0 = kRowsPerCta * (tile / P.ntiles), i0 = kTile * (tile % P.ntiles);
+    const int64_t r_begin = (int64_t)slab * P.rows_per_slab;
+    const int64_t r_end = min(m, r_begin + P.rows_per_slab);
+    const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + kTile - 1) / kTile) : 0;
+    __syncthreads();
+    if (tid < kRowsPerCta) colE[tid] = c0 + tid < n ? oz::exp_field(colHi[c0 + tid]) : 0u;
+    // phase of (sample fi, row r_begin + 8 fg) and its advance per chunk
+    const bool fval = i0 + fi < s;
+    const uint64_t k = fval ? (uint64_t)idx[i0 + fi] : 0ull;
+    uint64_t r = fval ? (k * (uint64_t)(2 * (r_begin + 8 * fg) + 1)) % four_m : 0ull;
+    const uint64_t step_chunk = (k * (uint64_t)(2 * kTile)) % four_m;
+    const uint64_t step_row = 2ull * k;   // < 4m
+    long long hi[16], lo[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int64_t r0 = r_begin + (int64_t)ch * kTile;
+      const bool group_start = (ch % kGroupChunks) == 0;
+      const bool group_end = (ch % kGroupChunks) == kGroupChunks - 1 || ch == nchunks - 1;
+      // Rademacher signs of the chunk's rows (bit t: d_{r0 + t} = -1)
+      if (warp < 2) {
+        const int64_t j0 = r0 + 32 * warp + lane;
+        const bool neg = j0 < r_end && row_sign((uint64_t)j0, key) < 0.0;
+        const uint32_t bits = __ballot_sync(0xffffffffu, neg);
+        if (lane == 0) flips[warp] = bits;
+      }
+      // transform digits: sample fi, rows 8 fg .. 8 fg + 7
+      {
+        uint64_t rr = r;
+        unsigned char* dst = fs + tc::sw128_offset(fi, 8 * fg, 2);
+#pragma unroll
+        for (int t2 = 0; t2 < 4; ++t2) {
+          int d0[oz::kSlices], d1[oz::kSlices];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int64_t j = r0 + 8 * fg + 2 * t2 + h;
+            uint32_t whi = 0u, wlo = 0u;
+            if (fval && j < r_end) cos_phase_bits(tab, (int64_t)rr, m, whi, wlo);
+            oz::digits8(whi, wlo, 1023u, h ? d1 : d0);
+            rr += step_row;
+            if (rr >= four_m) rr -= four_m;
+          }
+#pragma unroll
+          for (int b = 0; b < oz::kSlices; ++b)
+            *reinterpret_cast<uint32_t*>(dst + 4 * t2 + b * kXPanel) = oz::pack_f16x2(d0[b], d1[b]);
+        }
+        r += step_chunk;
+        if (r >= four_m) r -= four_m;
+      }
+      __syncthreads();   // signs visible
+      const uint64_t flip64 = (uint64_t)flips[0] | ((uint64_t)flips[1] << 32);
+      // digits of d_j A[j][c]: one column per warp
+#pragma unroll 1
+      for (int c = warp; c < kRowsPerCta; c += kOzThreads / 32) {
+        const int col = c0 + c;
+        oz_slice_col_chunk(col < n ? A + (int64_t)col * lda : nullptr, r0, r_end, colE[c], flip64, as, c, kWPanel,
+                           lane);
+      }
+      tc::fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after();
+        oz_issue_chunk(tmem, tc::smem_u32(as), kWPanel, tc::smem_u32(fs), kXPanel, idesc, group_start);
+        tc::mma_commit(&mma_bar);
+      }
+      const bool ok = tc::mbar_wait(&mma_bar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        abort = true;
+        break;
+      }
+      tc::fence_after();
+      if (group_end) oz_readout(tmem, q, g, hi, lo);
+      tc::fence_before();
+      __syncthreads();
+    }
+    if (abort) break;
+    oz_store_partial(part + (size_t)item * (2 * kRowsPerCta * kTile), q, g, lane, hi, lo);
+  }
+  if (abort && tid == 0) raise_level_status(ctl, ST_TIMEOUT);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// Y (s x n, column-major) from the items' partials: exact sums over the
+// slabs, one rounding, times sqrt(2/s) c_k.  A non-finite column of A gives a
+// NaN column and raises NONFINITE.
+__global__ void k_sketch_oz_reduce(int n, int s, const uint32_t* __restrict__ colHi, const uint32_t* __restrict__ idx,
+                                   SketchOzPlan P, const long long* __restrict__ part, double* __restrict__ Y,
+                                   Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)s * n) return;
+  const int i = (int)(e % s), c = (int)(e / s);
+  const int tile = (c / kRowsPerCta) * P.ntiles + i / kTile;
+  const size_t tstride = 2 * kRowsPerCta * kTile;
+  const oz::I128 acc = oz_sum_partials(part + (size_t)tile * tstride, P.slabs,
+                                       (size_t)P.mblocks * P.ntiles * tstride, c % kRowsPerCta, i % kTile);
+  const uint32_t Ec = oz::exp_field(colHi[c]);
+  const double coef = sqrt(2.0 / (double)s) * (idx[i] == 0 ? 0.70710678118654752440 : 1.0);
+  const double y = Ec == 2047u ? __longlong_as_double(0x7FF8000000000000ll)
+                               : oz::i128_to_double(acc, (int)Ec + 1023 - oz::kScaleBias) * coef;
+  Y[e] = y;
+  if (!isfinite(y)) {
+    ctl->input_nonfinite = 1;
+    raise_level_status(ctl, ST_NONFINITE);
+  }
 }
 
 }  // namespace
@@ -485,6 +651,48 @@ void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOz
   k_syrk_oz<<<nitems < sms ? nitems : sms, kOzThreads, smem, st>>>(m, n, W, ldw, colHi, P, part, ctl, level);
   const int64_t nn = (int64_t)n * n;
   k_syrk_oz_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, colHi, P, part, out, ctl, level);
+}
+
+SketchOzPlan sketch_oz_plan(int64_t m, int n, int s) {
+  SketchOzPlan P{};
+  P.mblocks = (n + kRowsPerCta - 1) / kRowsPerCta;
+  P.ntiles = (s + kTile - 1) / kTile;
+  const int tiles = P.mblocks * P.ntiles;
+  const int sms = num_sms();
+  int slabs = tiles >= sms ? 1 : sms / gcd_int(tiles, sms);
+  const int64_t max_slabs = (m + 4 * kTile - 1) / (4 * kTile);
+  if (slabs > max_slabs) slabs = (int)max_slabs;
+  const int64_t min_slabs = (m + (1 << 20) - 1) >> 20;
+  if (slabs < min_slabs) slabs = (int)min_slabs;
+  if (slabs < 1) slabs = 1;
+  int64_t rps = (m + slabs - 1) / slabs;
+  rps = (rps + kTile - 1) / kTile * kTile;
+  P.rows_per_slab = rps;
+  P.slabs = (int)((m + rps - 1) / rps);
+  return P;
+}
+
+size_t sketch_oz_part_bytes(const SketchOzPlan& P) {
+  return sizeof(long long) * 2 * kRowsPerCta * kTile * (size_t)P.mblocks * P.ntiles * P.slabs;
+}
+
+void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, const uint32_t* idx, const double* tab,
+                      uint64_t seed, const SketchOzPlan& P, uint32_t* colHi, long long* part, double* Y, Ctl* ctl,
+                      int level, cudaStream_t st) {
+  cudaMemsetAsync(colHi, 0, syrk_oz_colhi_bytes(n), st);
+  const int sms = num_sms();
+  int ysplit = (4 * sms + n - 1) / n;
+  const int64_t max_y = (m + 4095) / 4096;
+  if (ysplit > max_y) ysplit = (int)max_y;
+  if (ysplit < 1) ysplit = 1;
+  k_col_hi<<<dim3(n, ysplit), 256, 0, st>>>(m, n, A, lda, (m + ysplit - 1) / ysplit, colHi, ctl, level);
+  const size_t smem = (size_t)oz::kSlices * (kWPanel + kXPanel) + 1024;
+  cudaFuncSetAttribute(k_sketch_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int nitems = P.mblocks * P.ntiles * P.slabs;
+  k_sketch_oz<<<nitems < sms ? nitems : sms, kOzThreads, smem, st>>>(m, n, s, A, lda, colHi, idx, tab, seed_key(seed),
+                                                                      P, part, ctl, level);
+  const int64_t total = (int64_t)s * n;
+  k_sketch_oz_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, colHi, idx, P, part, Y, ctl, level);
 }
 
 }  // namespace mrcqr

@@ -1,5 +1,5 @@
 // Blackwell (sm_100-family) building blocks written as inline PTX: shared
-// memory matrix descriptors for K-major SWIZZLE_128B operands, tcgen05
+// memory matrix descriptors for K-major SWIZZLE_128B / SWIZZLE_64B operands, tcgen05
 // instruction descriptors, TMEM allocation and loads, tcgen05.mma with its
 // mbarrier commit, mbarriers with bounded waits, and 2-D TMA loads.
 #pragma once
@@ -31,6 +31,23 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 __host__ __device__ __forceinline__ uint32_t sw128_offset(int r, int k, int ebytes) {
   const int byte = k * ebytes;
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((byte >> 4) ^ (r & 7))) << 4) + (byte & 15));
+}
+
+// K-major SWIZZLE_64B: rows of 64 bytes, 8-row atoms of 512 bytes (stride
+// byte offset 512); 16-byte chunk c of row r stored at chunk c ^ ((r / 2) % 4).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
+  d |= (uint64_t)4 << 61;   // SWIZZLE_64B
+  return d;
+}
+
+__host__ __device__ __forceinline__ uint32_t sw64_offset(int r, int k, int ebytes) {
+  const int byte = k * ebytes;
+  return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((byte >> 4) ^ ((r >> 1) & 3))) << 4) + (byte & 15));
 }
 
 enum Fmt : uint32_t { F16 = 0, BF16 = 1, TF32 = 2 };

@@ -227,3 +227,75 @@ def test_emulated_gram_deterministic_and_symmetric_in_rows(env):
     a = M.gram(M.to_colmajor(W)).cpu().numpy()
     b = M.gram(M.to_colmajor(W[perm])).cpu().numpy()   # a row permutation changes every slab's content
     np.testing.assert_array_equal(a, b)
+
+
+# --- FP64 sketch as an emulated GEMM --------------------------------------
+def _sketch_exact(A, idx, d, s):
+    """Correctly rounded sum_j F_kj d_j A_jc per sampled row (F the orthonormal
+    DCT row without its sqrt(2/m) c_k factor), times sqrt(2/s) c_k."""
+    m = A.shape[0]
+    F = np.stack([O.dct_row(int(k), m) / O.dct_coefficient(int(k), m) for k in idx])   # cos values
+    P = O.product_rounded(F, d[:, None] * A)
+    coef = np.sqrt(2.0 / s) * np.where(idx == 0, np.sqrt(0.5), 1.0)
+    return coef[:, None] * P, coef, F
+
+
+@pytest.mark.parametrize("m,n,s", [(3000, 40, 80), (4097, 33, 66), (700, 130, 260), (257, 5, 10)])
+def test_emulated_sketch_against_exact(env, m, n, s):
+    torch, M = env
+    A = inputs.make_matrix(m, n, 1e12, seed=m + n)
+    Y = M.sketch(M.to_colmajor(A), s, "fp64", seed=3).cpu().numpy()
+    assert M.last_sketch_variant() == 3
+    d, idx = O.rademacher(m, 3), O.sample_rows(m, s, 3)
+    ref, coef, F = _sketch_exact(A, idx, d, s)
+    # the table's cos values and numpy's may differ by an ulp each: 2^-52 sum |A|
+    C = np.abs(A).max(axis=0)[None, :]
+    bound = coef[:, None] * (2.0 ** -52 * np.abs(A).sum(axis=0)[None, :] + 2.0 ** -57 * m * C) + 2 * U * np.abs(ref)
+    err = np.abs(Y - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
+@pytest.mark.parametrize("m,n,s", [(1 << 16, 128, 256), (20000, 200, 400), (30001, 64, 192), (5000, 512, 1024)])
+def test_emulated_sketch_matches_fma_sketch(env, m, n, s):
+    torch, M = env
+    A = inputs.make_matrix(m, n, 1e14, seed=7 + n)
+    Ad = M.to_colmajor(A)
+    Ye = M.sketch(Ad, s, "fp64", seed=9).cpu().numpy()
+    Yf = M.sketch(Ad, s, "fp64", seed=9, variant=1).cpu().numpy()
+    ref = O.sketch(A, O.sample_rows(m, s, 9), O.rademacher(m, 9)) if m * s <= 1 << 24 else Yf
+    # both references carry FP64 summation error (~u sqrt(m) relative); the emulated sum has none
+    assert np.linalg.norm(Ye - ref) <= 5e-14 * np.linalg.norm(ref)
+    assert np.linalg.norm(Ye - Yf) <= 5e-14 * np.linalg.norm(Yf)
+
+
+def test_emulated_sketch_odd_ld_and_nonfinite(env):
+    torch, M = env
+    m, n = 5000, 30
+    A = inputs.make_matrix(m, n, 1e4, seed=31)
+    Y0 = M.sketch(M.to_colmajor(A), 2 * n, "fp64", seed=1).cpu().numpy()
+    Y1 = M.sketch(M.to_colmajor(A, ld=m + 1), 2 * n, "fp64", seed=1).cpu().numpy()   # no alignment needed
+    assert M.last_sketch_variant() == 3
+    np.testing.assert_array_equal(Y0, Y1)
+    A[123, 7] = np.nan
+    Q = M.empty_colmajor(m, n)
+    R = M.empty_colmajor(n, n)
+    M.factor_ex(M.to_colmajor(A), Q, R, prec="fp64", seed=1)
+    assert M.last_status()["status"] == "NONFINITE"
+
+
+def test_factorization_fp64_sketch_emulated_vs_fma(env):
+    torch, M = env
+    m, n = 40000, 96
+    A = inputs.make_matrix(m, n, 1e16, seed=77)
+    Ad = M.to_colmajor(A)
+    out = []
+    for fp in (0, 1):
+        Q = M.empty_colmajor(m, n)
+        R = M.empty_colmajor(n, n)
+        M.factor_ex(Ad, Q, R, prec="fp64", seed=2, escalate=False, fp64_products=fp)
+        st = M.last_status()
+        assert st["status"] == "OK" and st["prec_used"] == "fp64"
+        Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
+        out.append((O.orthogonality_error(Qh)[0], O.residual_error(A, Qh, Rh)[0]))
+    for o, r in out:
+        assert o <= 1e-13 and r <= 1e-13

@@ -126,8 +126,12 @@ def test_sketch_variants_agree_and_fall_back(M):
     Aodd = M.to_colmajor(A, ld=m + 1)
     _ = M.sketch(Aodd, 2 * n, "fp16", seed=5)
     assert M.last_sketch_variant() == 1
-    # the FP64 sketch has no tensor-core variant
+    # FP64: emulated FP64 on the tensor cores unless the SIMT variant is asked for
     _ = M.sketch(Ad, 2 * n, "fp64", seed=5, variant=2)
+    assert M.last_sketch_variant() == 3
+    _ = M.sketch(Ad, 2 * n, "fp64", seed=5)
+    assert M.last_sketch_variant() == 3
+    _ = M.sketch(Ad, 2 * n, "fp64", seed=5, variant=1)
     assert M.last_sketch_variant() == 1
 
 
