@@ -70,10 +70,11 @@ typedef struct mrcqr_opts {
                              2: tensor cores when possible */
   double ortho_tol;   /* acceptance threshold on ||I - Q^T Q||_F (default 1e-13) */
   void* stats_device; /* optional DEVICE pointer to an mrcqr_stats_t written at the end */
-  int32_t fp64_products; /* 0 (default): the Gram matrix W^T W, the product Q = W R_c^{-1} and
-                            the check Q^T Q as emulated FP64 on the FP16 tensor cores (exact 8-bit
-                            digit slicing, integer recombination, one final rounding; see
-                            mrcqr_gram and mrcqr_finalize_q); 1: FP64 FMA kernels throughout */
+  int32_t fp64_products; /* 0 (default): the FP64 sketch, the off-diagonal updates of W = A R_s^{-1},
+                            the Gram matrix W^T W, the product Q = W R_c^{-1} and the check Q^T Q
+                            as emulated FP64 on the FP16 tensor cores (exact 8-bit digit slicing,
+                            integer recombination, one final rounding; see mrcqr_trsm, mrcqr_gram
+                            and mrcqr_finalize_q); 1: FP64 FMA kernels throughout */
   int32_t reserved1;
 } mrcqr_opts_t;
 
@@ -199,6 +200,19 @@ int mrcqr_sketch_qr(int64_t n, int64_t s, const double* Y, int prec, double* Rs,
  * Status (breakdown) through mrcqr_get_last_status. */
 int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, const double* Rs, double* Q,
                          int64_t ldq, double* R, int64_t ldr, mrcqr_stream_t stream);
+
+/* Algorithm 2 step 7: W = A R^{-1} by substitution on the rows (R upper
+ * triangular with nonzero diagonal).  A: DEVICE double m x n, column-major,
+ * ld lda >= m; R: DEVICE double n x n, column-major, ld ldr >= n, only the
+ * upper triangle is read; W: DEVICE double m x n, ld ldw >= m, must not
+ * overlap A or R.  fp64_products = 0: blocked by 16 columns, the off-diagonal
+ * updates W_{<J} R_{<J,J} as emulated FP64 on the FP16 tensor cores (one
+ * rounding each, then one FP64 subtraction from A_J), the 16 x 16 diagonal
+ * blocks by FP64 substitution; 1: FP64 substitution throughout.
+ * 1 <= n <= 512, 1 <= m < 2^31.  Allocates its workspace with cudaMallocAsync
+ * on `stream`. */
+int mrcqr_trsm(int64_t m, int64_t n, const double* A, int64_t lda, const double* R, int64_t ldr, double* W,
+               int64_t ldw, int fp64_products, mrcqr_stream_t stream);
 
 /* Algorithm 1 step 1 (and the check of Sec. II-C): G = W^T W.  W: DEVICE
  * double m x n, column-major, ld ldw >= m; G: DEVICE double n x n, packed

@@ -28,7 +28,7 @@ struct Plan {
   int n = 0, s = 0, npad = 0, chunks = 0, splits = 0;
   size_t off_ctl = 0, off_idx = 0, off_tab = 0, off_tabf = 0, off_ypart = 0, off_y = 0, off_sqr = 0, off_rs = 0, off_rst = 0,
          off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, off_feat = 0, off_oze = 0, off_ozx = 0,
-         off_colhi = 0, off_ozpart = 0, total = 0;
+         off_colhi = 0, off_ozpart = 0, off_tcole = 0, off_trd = 0, total = 0;
   SyrkOzPlan oz{};
   SketchOzPlan sk{};
 };
@@ -68,6 +68,8 @@ Plan make_plan(int64_t m, int n, int s) {
   p.sk = sketch_oz_plan(m, n, s);
   p.off_colhi = take(syrk_oz_colhi_bytes(n));
   p.off_ozpart = take(std::max(syrk_oz_part_bytes(p.oz), sketch_oz_part_bytes(p.sk)));   // used one after the other
+  p.off_tcole = take(trsm_oz_cole_bytes(n));
+  p.off_trd = take(trsm_oz_rd_bytes(n));
   p.total = o;
   return p;
 }
@@ -250,10 +252,16 @@ void enqueue_stage2(const Plan& p, void* ws, const double* A, int64_t lda, doubl
   double* Rc = at<double>(ws, p.off_rc);
   double* XT = at<double>(ws, p.off_xt);
   double* Rs = at<double>(ws, p.off_rs);
+  const bool emu = fp64_products == 0;
   uint32_t* colhi = at<uint32_t>(ws, p.off_colhi);
   long long* ozpart = at<long long>(ws, p.off_ozpart);
-  const bool emu = fp64_products == 0;
-  launch(SG_TRSM, lvl, st, [&] { launch_trsm(p.m, p.n, A, lda, RsT, rinv, Q, ldq, ctl, lvl, st); });
+  if (emu)
+    launch(SG_TRSM, lvl, st, [&] {
+      launch_trsm_oz(p.m, p.n, A, lda, RsT, rinv, at<uint32_t>(ws, p.off_tcole), at<unsigned char>(ws, p.off_trd), Q,
+                     ldq, ctl, lvl, st);
+    });
+  else
+    launch(SG_TRSM, lvl, st, [&] { launch_trsm(p.m, p.n, A, lda, RsT, rinv, Q, ldq, ctl, lvl, st); });
   double* E = at<double>(ws, p.off_e);
   if (emu) {
     launch(SG_SYRK, lvl, st, [&] { launch_syrk_oz(p.m, p.n, Q, ldq, p.oz, colhi, ozpart, Rc, ctl, lvl, st); });
@@ -474,6 +482,40 @@ int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, con
   launch(SG_PREP, 0, st, [&] { launch_rs_prepare((int)n, Rs, at<double>(ws, p.off_rst), at<double>(ws, p.off_rinv), st); });
   enqueue_stage2(p, ws, A, lda, Q, ldq, R, ldr, 1, ctl, 0, st);
   launch(SG_STATS, 0, st, [&] { k_write_stats<<<1, 1, 0, st>>>(ctl, slot); });
+  cudaFreeAsync(ws, st);
+  return finish(st);
+}
+
+int mrcqr_trsm(int64_t m, int64_t n, const double* A, int64_t lda, const double* R, int64_t ldr, double* W,
+               int64_t ldw, int fp64_products, mrcqr_stream_t stream) {
+  if (!A || !R || !W || n < 1 || n > kMaxN || m < 1 || m >= (int64_t(1) << 31) || lda < m || ldw < m || ldr < n ||
+      (fp64_products != 0 && fp64_products != 1))
+    return MRCQR_ERR_INVALID;
+  const size_t abytes = sizeof(double) * (size_t)((n - 1) * lda + m);
+  const size_t wbytes = sizeof(double) * (size_t)((n - 1) * ldw + m);
+  const size_t rbytes = sizeof(double) * (size_t)((n - 1) * ldr + n);
+  if (overlaps(A, abytes, W, wbytes) || overlaps(R, rbytes, W, wbytes)) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(m, (int)n, (int)n);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, p.total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCQR_ERR_ALLOC;
+  }
+  Ctl* ctl = at<Ctl>(ws, p.off_ctl);
+  double* Rp = at<double>(ws, p.off_rs);
+  double* RsT = at<double>(ws, p.off_rst);
+  double* rinv = at<double>(ws, p.off_rinv);
+  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  cudaMemcpy2DAsync(Rp, sizeof(double) * n, R, sizeof(double) * ldr, sizeof(double) * n, n, cudaMemcpyDeviceToDevice, st);
+  launch(SG_PREP, 0, st, [&] { launch_rs_prepare((int)n, Rp, RsT, rinv, st); });
+  if (fp64_products == 0)
+    launch(SG_TRSM, 0, st, [&] {
+      launch_trsm_oz(m, (int)n, A, lda, RsT, rinv, at<uint32_t>(ws, p.off_tcole), at<unsigned char>(ws, p.off_trd), W,
+                     ldw, ctl, 0, st);
+    });
+  else
+    launch(SG_TRSM, 0, st, [&] { launch_trsm(m, (int)n, A, lda, RsT, rinv, W, ldw, ctl, 0, st); });
   cudaFreeAsync(ws, st);
   return finish(st);
 }

@@ -124,6 +124,10 @@ struct SketchOzPlan {   // emulated-FP64 sketch: 128-column blocks of A x 64-row
   int64_t rows_per_slab;
 };
 SketchOzPlan sketch_oz_plan(int64_t m, int n, int s);
+size_t trsm_oz_rd_bytes(int n);
+size_t trsm_oz_cole_bytes(int n);
+void launch_trsm_oz(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv,
+                    uint32_t* colE, unsigned char* Rd, double* W, int64_t ldw, Ctl* ctl, int level, cudaStream_t st);
 size_t sketch_oz_part_bytes(const SketchOzPlan& P);
 void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, const uint32_t* idx, const double* tab,
                       uint64_t seed, const SketchOzPlan& P, uint32_t* colHi, long long* part, double* Y, Ctl* ctl,

@@ -3,6 +3,13 @@
 // step 1, Sec. II-C), the finalize Q = W R_c^{-1} (Algorithm 1 step 3) and
 // the FP64 sketch (Algorithm 2 steps 2-4 at p = FP64).  Each result entry is
 // the once-rounded value of a 63-bit fixed-point evaluation of its sum.
+//
+// All four run the same two-stage pipeline per CTA (one CTA per SM, 512
+// threads, all 512 TMEM columns = 8 level accumulators of 128 x 64): the
+// threads write the digit panels of K chunk c + 1 (32 deep, K-major
+// SWIZZLE_64B) into one shared-memory stage while the tensor cores run the
+// 36 digit-pair MMAs of chunk c from the other; every 4 chunks (K = 128, the
+// exactness limit) the level sums are read out of TMEM into 64-bit integers.
 #include "kernels.h"
 #include "ozaki.cuh"
 #include "tc.cuh"
@@ -12,31 +19,35 @@ namespace mrcqr {
 namespace {
 
 constexpr int kOzThreads = 512;
-constexpr int kRowsPerCta = 128;             // MMA M
-constexpr int kTile = 64;                    // MMA N and K chunk
-constexpr uint32_t kWPanel = kRowsPerCta * 128;   // one slice of a 128 x 64 FP16 block (16 KiB)
-constexpr uint32_t kXPanel = kTile * 128;          // one slice of a 64 x 64 FP16 block (8 KiB)
+constexpr int kM = 128;                     // MMA M: rows of the A operand
+constexpr int kN = 64;                      // MMA N: rows of the B operand, TMEM columns per level
+constexpr int kK = 32;                      // K depth of a chunk (one 64-byte FP16 row)
+constexpr int kGroupChunks = 4;             // chunks per exact FP32 accumulation (K <= 128)
+constexpr uint32_t kAPanel = kM * 64;       // one digit of a 128 x 32 FP16 block (8 KiB)
+constexpr uint32_t kBPanel = kN * 64;       // one digit of a 64 x 32 FP16 block (4 KiB)
+constexpr uint32_t kStage = oz::kSlices * (kAPanel + kBPanel);   // 96 KiB
+constexpr size_t kSmem = 2 * (size_t)kStage + 1024;
+constexpr size_t kPartElems = 2 * kM * kN;  // hi and lo of one 128 x 64 item
 
-constexpr int kGroupChunks = 2;             // K chunks per exact FP32 accumulation (K <= 128)
-
-// The 36 digit-pair MMAs (levels 0..7, four K steps of 16) of one 64-deep K
-// chunk; level L accumulates in TMEM columns [64 L, 64 L + 64).  ab / bb are
-// the shared addresses of digit 0 of the A (128 rows) and B (64 rows) panels,
-// astride / bstride the distance between digits.  Issued by one thread.
-__device__ __forceinline__ void oz_issue_chunk(uint32_t tmem, uint32_t ab, uint32_t astride, uint32_t bb,
-                                               uint32_t bstride, uint32_t idesc, bool group_start) {
-#pragma unroll 1
-  for (int L = 0; L < oz::kLevels; ++L) {
-    const uint32_t d = tmem + (uint32_t)(L * kTile);
-#pragma unroll 1
-    for (int a = 0; a <= L; ++a) {
-      const int b = L - a;
+// The 36 digit-pair MMAs (levels 0..7, two K steps of 16) of one chunk; level
+// L accumulates in TMEM columns [64 L, 64 L + 64).  ab / bb: shared addresses
+// of digit 0 of the A and B panels.  Issued by one thread, round-robin over
+// the levels (round a takes the pair (a, L - a) of every level L >= a) so that
+// consecutive MMAs mostly update different accumulators; the descriptors are
+// the base descriptors plus the panel offsets (address field in 16-byte units).
+__device__ __forceinline__ void oz_issue_chunk(uint32_t tmem, uint32_t ab, uint32_t bb, uint32_t bstride,
+                                               uint32_t idesc, bool group_start) {
+  const uint64_t da = tc::sw64_desc(ab), db = tc::sw64_desc(bb);
+  const uint32_t first = group_start ? 0u : 1u;
 #pragma unroll
-      for (int kk = 0; kk < kTile; kk += 16) {
-        const uint32_t acc = (group_start && a == 0 && kk == 0) ? 0u : 1u;
-        tc::mma_f16(d, tc::sw128_desc(ab + a * astride + kk * 2), tc::sw128_desc(bb + b * bstride + kk * 2), idesc,
-                    acc);
-      }
+  for (int a = 0; a < oz::kLevels; ++a) {
+#pragma unroll
+    for (int kk = 0; kk < kK; kk += 16) {
+      const uint64_t adesc = da + (uint64_t)((a * kAPanel + kk * 2) >> 4);
+#pragma unroll
+      for (int L = a; L < oz::kLevels; ++L)
+        tc::mma_f16(tmem + (uint32_t)(L * kN), adesc, db + (uint64_t)(((uint32_t)(L - a) * bstride + kk * 2) >> 4),
+                    idesc, (a == 0 && kk == 0) ? first : 1u);
     }
   }
 }
@@ -48,34 +59,141 @@ __device__ __forceinline__ void oz_readout(uint32_t tmem, int q, int g, long lon
 #pragma unroll 1
   for (int L = 0; L < oz::kLevels; ++L) {
     float v[16];
-    tc::tmem_ld16(base + (uint32_t)(L * kTile), v);
+    tc::tmem_ld16(base + (uint32_t)(L * kN), v);
     tc::tmem_wait_ld();
 #pragma unroll
     for (int c = 0; c < 16; ++c) oz::add_level(L, v[c], hi[c], lo[c]);
   }
 }
 
-// Digits of a 64-row chunk of one column of a column-major matrix, against
-// the column's reference exponent E, into K-major SW128 panels: row `prow`
-// of each digit panel (panel stride pstride).  Called by a full warp: lane
-// l takes rows 2l and 2l + 1; flip64 (one bit per row) flips signs.
-__device__ __forceinline__ void oz_slice_col_chunk(const double* __restrict__ col, int64_t r0, int64_t r_end,
-                                                   uint32_t E, uint64_t flip64, unsigned char* panel, int prow,
-                                                   uint32_t pstride, int lane) {
-  const int64_t ra = r0 + 2 * lane;
-  double v0 = 0.0, v1 = 0.0;
-  if (col) {
-    if (ra < r_end) v0 = col[ra];
-    if (ra + 1 < r_end) v1 = col[ra + 1];
-  }
-  const uint32_t f0 = (uint32_t)(flip64 >> (2 * lane)) & 1u, f1 = (uint32_t)(flip64 >> (2 * lane + 1)) & 1u;
+// Digits of two values (FP64 bits, sign flips f0 / f1 applied, scaled by
+// 2^eo0 / 2^eo1) against the reference exponent E, packed in pairs into the
+// eight digit panels at dst.
+__device__ __forceinline__ void oz_store_pair(double v0, double v1, uint32_t f0, uint32_t f1, int E,
+                                              unsigned char* dst, uint32_t pstride, int eo0 = 0, int eo1 = 0) {
   int d0[oz::kSlices], d1[oz::kSlices];
-  oz::digits8((uint32_t)__double2hiint(v0) ^ (f0 << 31), (uint32_t)__double2loint(v0), E, d0);
-  oz::digits8((uint32_t)__double2hiint(v1) ^ (f1 << 31), (uint32_t)__double2loint(v1), E, d1);
-  unsigned char* dst = panel + tc::sw128_offset(prow, 2 * lane, 2);
+  oz::digits8((uint32_t)__double2hiint(v0) ^ (f0 << 31), (uint32_t)__double2loint(v0), E, d0, eo0);
+  oz::digits8((uint32_t)__double2hiint(v1) ^ (f1 << 31), (uint32_t)__double2loint(v1), E, d1, eo1);
 #pragma unroll
   for (int a = 0; a < oz::kSlices; ++a)
     *reinterpret_cast<uint32_t*>(dst + a * pstride) = oz::pack_f16x2(d0[a], d1[a]);
+}
+
+// A 32-row chunk of NC columns of a column-major matrix (column col0 + c,
+// zero beyond n or r_end) in registers: lane l holds rows 2(l % 16) and
+// 2(l % 16) + 1 of columns 32 it + 2 warp + l / 16.  Issued one chunk ahead
+// of its use, so the loads are in flight during the MMAs.
+template <int NC>
+__device__ __forceinline__ void oz_load_cols(const double* __restrict__ X, int64_t ldx, int n, int col0, int64_t r0,
+                                             int64_t r_end, int warp, int lane, double (&v)[NC / 32][2]) {
+  const int p = lane & 15, h = lane >> 4;
+  const int64_t ra = r0 + 2 * p;
+#pragma unroll
+  for (int it = 0; it < NC / 32; ++it) {
+    const int col = col0 + 32 * it + 2 * warp + h;
+    v[it][0] = v[it][1] = 0.0;
+    if (col < n) {
+      const double* src = X + (int64_t)col * ldx;
+      if (ra < r_end) v[it][0] = __ldg(src + ra);
+      if (ra + 1 < r_end) v[it][1] = __ldg(src + ra + 1);
+    }
+  }
+}
+
+// Digits of the values loaded by oz_load_cols (reference exponent E[c], sign
+// flips f0 / f1 of the lane's two rows) into panel rows c.
+template <int NC>
+__device__ __forceinline__ void oz_store_cols(const double (&v)[NC / 32][2], const uint32_t* E, uint32_t f0,
+                                              uint32_t f1, unsigned char* panel, uint32_t pstride, int warp,
+                                              int lane) {
+  const int p = lane & 15, h = lane >> 4;
+#pragma unroll
+  for (int it = 0; it < NC / 32; ++it) {
+    const int c = 32 * it + 2 * warp + h;
+    oz_store_pair(v[it][0], v[it][1], f0, f1, E[c], panel + tc::sw64_offset(c, 2 * p, 2), pstride);
+  }
+}
+
+struct OzPipe {
+  uint64_t* bar;
+  uint32_t tmem, idesc;
+  uint32_t commits;   // MMA batches committed so far (the same count in every thread)
+  int tid, q, g;
+};
+
+// Runs nchunks chunks through the two stages: produce(ch, a, b) writes the
+// digit panels of chunk ch (A at a, B at b); bbase(a, b) gives the B operand
+// base (b, or rows inside a) and bstride its digit stride.  The MMAs of chunk
+// ch overlap with the production of chunk ch + 1.  Level sums are added into
+// hi / lo after every kGroupChunks chunks and after the last.  False when a
+// wait timed out (every thread returns false together).
+template <class Produce, class BBase>
+__device__ __forceinline__ bool oz_run(OzPipe& P, unsigned char* smem, int nchunks, Produce&& produce, BBase&& bbase,
+                                       uint32_t bstride, long long* hi, long long* lo) {
+  for (int ch = 0; ch < nchunks; ++ch) {
+    unsigned char* a = smem + (ch & 1) * kStage;
+    unsigned char* b = a + oz::kSlices * kAPanel;
+    produce(ch, a, b);   // this stage was last read by the MMAs of chunk ch - 2, already complete
+    tc::fence_proxy_async();
+    bool ok = true;
+    if (ch > 0) ok = tc::mbar_wait(P.bar, (P.commits - 1) & 1u);
+    if (__syncthreads_or(!ok)) return false;
+    if (ch > 0 && (ch - 1) % kGroupChunks == kGroupChunks - 1) {   // group closed at ch - 1
+      tc::fence_after();
+      oz_readout(P.tmem, P.q, P.g, hi, lo);
+      tc::fence_before();
+      __syncthreads();
+    }
+    if (P.tid == 0) {
+      tc::fence_after();
+      oz_issue_chunk(P.tmem, tc::smem_u32(a), bbase(a, b), bstride, P.idesc, ch % kGroupChunks == 0);
+      tc::mma_commit(P.bar);
+    }
+    ++P.commits;
+  }
+  if (nchunks > 0) {
+    const bool ok = tc::mbar_wait(P.bar, (P.commits - 1) & 1u);
+    if (__syncthreads_or(!ok)) return false;
+    tc::fence_after();
+    oz_readout(P.tmem, P.q, P.g, hi, lo);
+    tc::fence_before();
+    __syncthreads();
+  }
+  return true;
+}
+
+// CTA prologue / epilogue shared by the kernels: TMEM (512 columns) and the
+// MMA barrier.
+__device__ __forceinline__ OzPipe oz_begin(uint32_t* tmem_slot, uint64_t* bar) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  OzPipe P;
+  P.bar = bar;
+  P.tmem = *tmem_slot;
+  P.idesc = tc::idesc(tc::F16, kM, kN);
+  P.commits = 0;
+  P.tid = tid;
+  P.q = warp & 3;
+  P.g = warp >> 2;
+  return P;
+}
+
+__device__ __forceinline__ void oz_end(const OzPipe& P, bool abort, Ctl* ctl) {
+  if (abort && P.tid == 0) raise_level_status(ctl, ST_TIMEOUT);
+  tc::fence_before();
+  __syncthreads();
+  if ((P.tid >> 5) == 0) tc::tmem_dealloc(P.tmem, 512);
+}
+
+__device__ __forceinline__ unsigned char* oz_smem(unsigned char* raw) {
+  return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
 }
 
 // One item's 128 x 64 partial (hi then lo, [column][row] so that a warp's
@@ -86,8 +204,8 @@ __device__ __forceinline__ void oz_store_partial(long long* out, int q, int g, i
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
     const int jl = g * 16 + c;
-    out[jl * kRowsPerCta + il] = hi[c];
-    out[kRowsPerCta * kTile + jl * kRowsPerCta + il] = lo[c];
+    out[jl * kM + il] = hi[c];
+    out[kM * kN + jl * kM + il] = lo[c];
   }
 }
 
@@ -96,15 +214,20 @@ __device__ __forceinline__ oz::I128 oz_sum_partials(const long long* part, int n
   oz::I128 acc{0, 0};
   for (int sl = 0; sl < nslabs; ++sl) {
     const long long* pp = part + (size_t)sl * slab_stride;
-    oz::i128_add(acc, oz::i128_from_parts(pp[jl * kRowsPerCta + il], pp[kRowsPerCta * kTile + jl * kRowsPerCta + il]));
+    oz::i128_add(acc, oz::i128_from_parts(pp[jl * kM + il], pp[kM * kN + jl * kM + il]));
   }
   return acc;
 }
 
-// X = R_c^{-1} (upper, XT[k][j] row-major with row stride npad): per column
-// j the reference exponent of max_k |X[k][j]| and the eight digits of every
-// X[k][j], stored as K-major SW128 panels: panel (b, t, kc) holds rows
-// j in [64t, 64t+64) and k in [64kc, 64kc+64) of digit b.
+__device__ __forceinline__ double nan64() { return __longlong_as_double(0x7FF8000000000000ll); }
+
+// ---------------------------------------------------------------------------
+// Finalize Q = W X in place (X = R_c^{-1} upper, Algorithm 1 step 3).
+//
+// Prep: per column j of X the reference exponent of max_k |X[k][j]| and the
+// digits of every X[k][j] as K-major SWIZZLE_64B panels: panel
+// ((b * ntiles + t) * nkc + kc) holds rows j in [64t, 64t+64) and k in
+// [32kc, 32kc+32) of digit b.  XT[k][j] = X[k][j], row stride npad.
 __global__ void __launch_bounds__(512) k_oz_prep_x(int n, int npad, int n64, const double* __restrict__ XT,
                                                    uint32_t* __restrict__ colE, unsigned char* __restrict__ Xs,
                                                    const Ctl* ctl, int level) {
@@ -112,12 +235,8 @@ __global__ void __launch_bounds__(512) k_oz_prep_x(int n, int npad, int n64, con
   const int j = blockIdx.x;   // column, < n64
   __shared__ uint32_t red[32];
   uint32_t mx = 0u;
-  for (int k = threadIdx.x; k < n64; k += blockDim.x) {
-    if (k < n && j < n) {
-      const double v = XT[(int64_t)k * npad + j];
-      mx = max(mx, (uint32_t)__double2hiint(v) & 0x7FFFFFFFu);
-    }
-  }
+  for (int k = threadIdx.x; k < n64; k += blockDim.x)
+    if (k < n && j < n) mx = max(mx, (uint32_t)__double2hiint(XT[(int64_t)k * npad + j]) & 0x7FFFFFFFu);
   mx = __reduce_max_sync(0xffffffffu, mx);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
@@ -129,154 +248,119 @@ __global__ void __launch_bounds__(512) k_oz_prep_x(int n, int npad, int n64, con
   __syncthreads();
   const uint32_t E = oz::exp_field(red[0]);
   if (threadIdx.x == 0) colE[j] = E;
-  const int ntiles = n64 / kTile;
-  const int t = j / kTile, jr = j % kTile;
+  const int ntiles = n64 / kN, nkc = n64 / kK;
+  const int t = j / kN, jr = j % kN;
   for (int k = threadIdx.x; k < n64; k += blockDim.x) {
     int d[oz::kSlices];
     const double v = (k < n && j < n) ? XT[(int64_t)k * npad + j] : 0.0;
     oz::digits8((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), E, d);
-    const int kc = k / kTile, kr = k % kTile;
+    const int kc = k / kK, kr = k % kK;
 #pragma unroll
     for (int b = 0; b < oz::kSlices; ++b) {
-      const __half h = __float2half_rn(oz::small_int_to_float(d[b]));
-      unsigned char* panel = Xs + (size_t)((b * ntiles + t) * ntiles + kc) * kXPanel;
-      *reinterpret_cast<__half*>(panel + tc::sw128_offset(jr, kr, 2)) = h;
+      unsigned char* panel = Xs + (size_t)((b * ntiles + t) * nkc + kc) * kBPanel;
+      *reinterpret_cast<__half*>(panel + tc::sw64_offset(jr, kr, 2)) = __float2half_rn(oz::small_int_to_float(d[b]));
     }
   }
 }
 
-// Q = W X in place, 128 rows per CTA, output tiles of 64 columns from right
-// to left (a tile reads only W columns left of its right edge, which are
-// still W).  X upper triangular: tile t needs K chunks 0..t.
+// Main kernel: 128 rows per work block, output tiles of 64 columns from right
+// to left (a tile reads only W columns left of its right edge, still W).
+// X upper triangular: tile t needs K chunks 0 .. 2t + 1.
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_finalize_oz(int64_t m, int n, int n64, double* __restrict__ Q, int64_t ldq, const uint32_t* __restrict__ colE,
                   const unsigned char* __restrict__ Xs, Ctl* ctl, int level) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* ws = smem;                                   // 8 slices x 16 KiB
-  unsigned char* xs = smem + oz::kSlices * kWPanel;           // 8 slices x 8 KiB
+  unsigned char* smem = oz_smem(smem_raw);
   __shared__ __align__(8) uint64_t mma_bar;
-  __shared__ uint32_t tmem_base;
-  __shared__ uint32_t rowE[kRowsPerCta];
-  __shared__ uint32_t redE[4][kRowsPerCta];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ntiles = n64 / kTile;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);   // 8 levels x 64 columns
-  if (tid == 0) {
-    tc::mbar_init(&mma_bar, 1);
-    tc::mbar_fence_init();
-  }
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t idesc = tc::idesc(tc::F16, kRowsPerCta, kTile);
-  const int q = warp & 3, g = warp >> 2;   // TMEM lane quarter, 16-column group
-  uint32_t phase = 0;
+  __shared__ uint32_t tmem_slot;
+  __shared__ uint32_t rowE[kM];
+  __shared__ uint32_t redE[4][kM];
+  OzPipe P = oz_begin(&tmem_slot, &mma_bar);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ntiles = n64 / kN, nkc = n64 / kK;
   bool abort = false;
-  const int64_t nblocks = (m + kRowsPerCta - 1) / kRowsPerCta;
+  const int64_t nblocks = (m + kM - 1) / kM;
 
   for (int64_t rb = blockIdx.x; rb < nblocks && !abort; rb += gridDim.x) {
-    const int64_t r0 = rb * kRowsPerCta;
-    // row reference exponents over all n columns of W
-    {
-      const int r = tid & (kRowsPerCta - 1), c0 = tid >> 7;
+    const int64_t r0 = rb * kM;
+    {   // row reference exponents over all n columns of W
+      const int r = tid & (kM - 1), c0 = tid >> 7;
       uint32_t mx = 0u;
       if (r0 + r < m)
         for (int c = c0; c < n; c += 4) mx = max(mx, (uint32_t)__double2hiint(Q[r0 + r + (int64_t)c * ldq]) & 0x7FFFFFFFu);
       redE[c0][r] = mx;
       __syncthreads();
-      if (tid < kRowsPerCta)
-        rowE[tid] = oz::exp_field(max(max(redE[0][tid], redE[1][tid]), max(redE[2][tid], redE[3][tid])));
+      if (tid < kM) rowE[tid] = oz::exp_field(max(max(redE[0][tid], redE[1][tid]), max(redE[2][tid], redE[3][tid])));
       __syncthreads();
     }
+    const int r = tid & (kM - 1), pp = tid >> 7;   // producer role: row r, column pairs pp + 4 i
+    const bool live = r0 + r < m;
     for (int t = ntiles - 1; t >= 0 && !abort; --t) {
       long long hi[16], lo[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
-      for (int kc = 0; kc <= t; ++kc) {
-        const bool group_start = (kc % kGroupChunks) == 0;
-        const bool group_end = (kc % kGroupChunks) == kGroupChunks - 1 || kc == t;
-        // X digits of (t, kc)
-        for (int i = tid; i < oz::kSlices * (int)(kXPanel / 16); i += kOzThreads) {
-          const int b = i / (kXPanel / 16), o = i % (kXPanel / 16);
-          const uint4* src = reinterpret_cast<const uint4*>(Xs + (size_t)((b * ntiles + t) * ntiles + kc) * kXPanel);
-          reinterpret_cast<uint4*>(xs + b * kXPanel)[o] = src[o];
-        }
-        // W digits of columns [64 kc, 64 kc + 64): thread owns row r and column pairs
-        {
-          const int r = tid & (kRowsPerCta - 1);
-          const uint32_t Er = rowE[r];
-          const bool live = r0 + r < m;
-#pragma unroll 2
-          for (int p = tid >> 7; p < kTile / 2; p += 4) {
-            const int k0 = kc * kTile + 2 * p;
-            int d0[oz::kSlices], d1[oz::kSlices];
-            double v0 = 0.0, v1 = 0.0;
-            if (live && k0 < n) v0 = Q[r0 + r + (int64_t)k0 * ldq];
-            if (live && k0 + 1 < n) v1 = Q[r0 + r + (int64_t)(k0 + 1) * ldq];
-            oz::digits8((uint32_t)__double2hiint(v0), (uint32_t)__double2loint(v0), Er, d0);
-            oz::digits8((uint32_t)__double2hiint(v1), (uint32_t)__double2loint(v1), Er, d1);
+      double v[4][2];
+      auto load_w = [&](int kc) {   // W of columns [32 kc, 32 kc + 32): row r, column pairs pp + 4 i
 #pragma unroll
-            for (int a = 0; a < oz::kSlices; ++a)
-              *reinterpret_cast<uint32_t*>(ws + a * kWPanel + tc::sw128_offset(r, 2 * p, 2)) = oz::pack_f16x2(d0[a], d1[a]);
-          }
+        for (int i = 0; i < 4; ++i) {
+          const int k0 = kc * kK + 2 * (pp + 4 * i);
+          v[i][0] = (live && k0 < n) ? Q[r0 + r + (int64_t)k0 * ldq] : 0.0;
+          v[i][1] = (live && k0 + 1 < n) ? Q[r0 + r + (int64_t)(k0 + 1) * ldq] : 0.0;
         }
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-          tc::fence_after();
-          oz_issue_chunk(tmem, tc::smem_u32(ws), kWPanel, tc::smem_u32(xs), kXPanel, idesc, group_start);
-          tc::mma_commit(&mma_bar);
+      };
+      load_w(0);
+      const int nch = 2 * (t + 1);
+      auto produce = [&](int kc, unsigned char* a, unsigned char* b) {
+        // X digits of (t, kc): 32 KiB, four asynchronous 16-byte copies per thread
+        const uint4* src = reinterpret_cast<const uint4*>(Xs);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int e = tid + kOzThreads * i;          // < 2048
+          const int dg = e / (kBPanel / 16), o = e % (kBPanel / 16);
+          tc::cp_async16(b + dg * kBPanel + 16 * o, src + (size_t)((dg * ntiles + t) * nkc + kc) * (kBPanel / 16) + o);
         }
-        const bool ok = tc::mbar_wait(&mma_bar, phase);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-          abort = true;
-          break;
-        }
-        tc::fence_after();
-        if (group_end) oz_readout(tmem, q, g, hi, lo);
-        tc::fence_before();
-        __syncthreads();
+        const uint32_t Er = rowE[r];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          oz_store_pair(v[i][0], v[i][1], 0u, 0u, Er, a + tc::sw64_offset(r, 2 * (pp + 4 * i), 2), kAPanel);
+        if (kc + 1 < nch) load_w(kc + 1);
+        tc::cp_async_wait_all();
+      };
+      auto bbase = [&](unsigned char*, unsigned char* b) { return tc::smem_u32(b); };
+      if (!oz_run(P, smem, nch, produce, bbase, kBPanel, hi, lo)) {
+        abort = true;
+        break;
       }
-      if (abort) break;
       // write Q[:, 64t + 16g + c] for this thread's row
-      const int r = q * 32 + lane;
-      if (r0 + r < m) {
-        const int scale_r = (int)rowE[r] - oz::kScaleBias;
+      const int rr = P.q * 32 + lane;
+      if (r0 + rr < m) {
+        const int scale_r = (int)rowE[rr] - oz::kScaleBias;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const int j = t * kTile + g * 16 + c;
+          const int j = t * kN + P.g * 16 + c;
           if (j < n) {
             const uint32_t ce = colE[j];
-            const double out = (rowE[r] == 2047u || ce == 2047u)   // non-finite operands
-                                   ? __longlong_as_double(0x7FF8000000000000ll)
-                                   : oz::i128_to_double(hi[c], lo[c], scale_r + (int)ce);
-            Q[r0 + r + (int64_t)j * ldq] = out;
+            Q[r0 + rr + (int64_t)j * ldq] = (rowE[rr] == 2047u || ce == 2047u)   // non-finite operands
+                                                ? nan64()
+                                                : oz::i128_to_double(hi[c], lo[c], scale_r + (int)ce);
           }
         }
       }
       __syncthreads();
     }
   }
-  if (abort && tid == 0) raise_level_status(ctl, ST_TIMEOUT);
-  tc::fence_before();
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+  oz_end(P, abort, ctl);
 }
 
-
 // ---------------------------------------------------------------------------
-// Gram G = W^T W (Algorithm 1 step 1) and the check matrix Q^T Q as emulated
-// FP64.  Every column of W is sliced against the exponent of its maximum over
-// all m rows, so the level sums of all rows share one scale: a work item
-// (output tile of 128 x 64 entries, slab of rows) reads its exact level sums
-// out of TMEM every 128 rows into 64-bit integer pairs, and a reduction adds
-// the items' 128-bit values (exact, so the order does not matter) and rounds
-// each entry once.
+// Gram G = W^T W (Algorithm 1 step 1) and the check matrix Q^T Q.  Every
+// column of W is sliced against the exponent of its maximum over all m rows,
+// so the level sums of all rows share one scale: a work item (output tile of
+// 128 x 64 entries, slab of rows) reads its exact level sums out of TMEM
+// every 128 rows into 64-bit integer pairs, and a reduction adds the items'
+// 128-bit values (exact, so the order does not matter) and rounds each entry
+// once.
 
 // Column maxima (as the high word of |x|, whose exponent field is the
 // reference exponent) over all rows; colHi must be zero on entry.
@@ -304,91 +388,59 @@ __global__ void __launch_bounds__(256) k_col_hi(int64_t m, int n, const double* 
 
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_syrk_oz(int64_t m, int n, const double* __restrict__ W, int64_t ldw, const uint32_t* __restrict__ colHi,
-              SyrkOzPlan P, long long* __restrict__ part, Ctl* ctl, int level) {
+              SyrkOzPlan SP, long long* __restrict__ part, Ctl* ctl, int level) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* as = smem;                                   // 8 digits x (128 columns x 64 rows)
-  unsigned char* bs = smem + oz::kSlices * kWPanel;           // 8 digits x (64 columns x 64 rows)
+  unsigned char* smem = oz_smem(smem_raw);
   __shared__ __align__(8) uint64_t mma_bar;
-  __shared__ uint32_t tmem_base;
-  __shared__ uint32_t colE[kRowsPerCta + kTile];
+  __shared__ uint32_t tmem_slot;
+  __shared__ uint32_t colE[kM + kN];
+  OzPipe P = oz_begin(&tmem_slot, &mma_bar);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
-  if (tid == 0) {
-    tc::mbar_init(&mma_bar, 1);
-    tc::mbar_fence_init();
-  }
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t idesc = tc::idesc(tc::F16, kRowsPerCta, kTile);
-  const int q = warp & 3, g = warp >> 2;
-  uint32_t phase = 0;
   bool abort = false;
-  const int nitems = P.ntiles * P.slabs;
+  const int nitems = SP.ntiles * SP.slabs;
 
   for (int item = blockIdx.x; item < nitems && !abort; item += gridDim.x) {
-    const int tile = item % P.ntiles, slab = item / P.ntiles;
-    const int i0 = kRowsPerCta * P.ti[tile], j0 = kTile * P.tj[tile];
-    const bool inner = (P.tj[tile] >> 1) == P.ti[tile];   // J block inside the I block
-    const int64_t r_begin = (int64_t)slab * P.rows_per_slab;
-    const int64_t r_end = min(m, r_begin + P.rows_per_slab);
-    const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + kTile - 1) / kTile) : 0;
+    const int tile = item % SP.ntiles, slab = item / SP.ntiles;
+    const int i0 = kM * SP.ti[tile], j0 = kN * SP.tj[tile];
+    const bool inner = (SP.tj[tile] >> 1) == SP.ti[tile];   // J block inside the I block
+    const int64_t r_begin = (int64_t)slab * SP.rows_per_slab;
+    const int64_t r_end = min(m, r_begin + SP.rows_per_slab);
+    const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + kK - 1) / kK) : 0;
     __syncthreads();
-    if (tid < kRowsPerCta) colE[tid] = i0 + tid < n ? oz::exp_field(colHi[i0 + tid]) : 0u;
-    else if (tid < kRowsPerCta + kTile) colE[tid] = j0 + tid - kRowsPerCta < n ? oz::exp_field(colHi[j0 + tid - kRowsPerCta]) : 0u;
+    if (tid < kM) colE[tid] = i0 + tid < n ? oz::exp_field(colHi[i0 + tid]) : 0u;
+    else if (tid < kM + kN) colE[tid] = j0 + tid - kM < n ? oz::exp_field(colHi[j0 + tid - kM]) : 0u;
     __syncthreads();
     long long hi[16], lo[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      const int64_t r0 = r_begin + (int64_t)ch * kTile;
-      const bool group_start = (ch % kGroupChunks) == 0;
-      const bool group_end = (ch % kGroupChunks) == kGroupChunks - 1 || ch == nchunks - 1;
-      // digits of W[r0 .. r0+63, column]: one column per warp, two rows per lane
-#pragma unroll 1
-      for (int c = warp; c < kRowsPerCta + kTile; c += kOzThreads / 32) {
-        if (c >= kRowsPerCta && inner) break;
-        const int col = c < kRowsPerCta ? i0 + c : j0 + c - kRowsPerCta;
-        const double* src = col < n ? W + (int64_t)col * ldw : nullptr;
-        if (c < kRowsPerCta) oz_slice_col_chunk(src, r0, r_end, colE[c], 0ull, as, c, kWPanel, lane);
-        else oz_slice_col_chunk(src, r0, r_end, colE[c], 0ull, bs, c - kRowsPerCta, kXPanel, lane);
+    double va[kM / 32][2];
+    oz_load_cols<kM>(W, ldw, n, i0, r_begin, r_end, warp, lane, va);
+    auto produce = [&](int ch, unsigned char* a, unsigned char* b) {
+      const int64_t r0 = r_begin + (int64_t)ch * kK;
+      oz_store_cols<kM>(va, colE, 0u, 0u, a, kAPanel, warp, lane);
+      if (ch + 1 < nchunks) oz_load_cols<kM>(W, ldw, n, i0, r0 + kK, r_end, warp, lane, va);
+      if (!inner) {   // second operand of an off-diagonal tile: loaded and sliced at once
+        double vb[kN / 32][2];
+        oz_load_cols<kN>(W, ldw, n, j0, r0, r_end, warp, lane, vb);
+        oz_store_cols<kN>(vb, colE + kM, 0u, 0u, b, kBPanel, warp, lane);
       }
-      tc::fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after();
-        const uint32_t ab = tc::smem_u32(as);
-        const uint32_t bb = inner ? ab + (uint32_t)(j0 - i0) * 128u : tc::smem_u32(bs);
-        oz_issue_chunk(tmem, ab, kWPanel, bb, inner ? kWPanel : kXPanel, idesc, group_start);
-        tc::mma_commit(&mma_bar);
-      }
-      const bool ok = tc::mbar_wait(&mma_bar, phase);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        abort = true;
-        break;
-      }
-      tc::fence_after();
-      if (group_end) oz_readout(tmem, q, g, hi, lo);
-      tc::fence_before();
-      __syncthreads();
+    };
+    auto bbase = [&](unsigned char* a, unsigned char* b) {
+      return inner ? tc::smem_u32(a) + (uint32_t)(j0 - i0) * 64u : tc::smem_u32(b);
+    };
+    if (!oz_run(P, smem, nchunks, produce, bbase, inner ? kAPanel : kBPanel, hi, lo)) {
+      abort = true;
+      break;
     }
-    if (abort) break;
-    oz_store_partial(part + (size_t)item * (2 * kRowsPerCta * kTile), q, g, lane, hi, lo);
+    oz_store_partial(part + (size_t)item * kPartElems, P.q, P.g, lane, hi, lo);
   }
-  if (abort && tid == 0) raise_level_status(ctl, ST_TIMEOUT);
-  tc::fence_before();
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+  oz_end(P, abort, ctl);
 }
 
 // Upper triangle of G from the items' partials (exact 128-bit sums over the
 // slabs, one rounding); lower triangle zero.
-__global__ void k_syrk_oz_reduce(int n, const uint32_t* __restrict__ colHi, SyrkOzPlan P,
+__global__ void k_syrk_oz_reduce(int n, const uint32_t* __restrict__ colHi, SyrkOzPlan SP,
                                  const long long* __restrict__ part, double* __restrict__ out, const Ctl* ctl,
                                  int level) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
@@ -399,14 +451,12 @@ __global__ void k_syrk_oz_reduce(int n, const uint32_t* __restrict__ colHi, Syrk
     out[e] = 0.0;
     return;
   }
-  const int I = i / kRowsPerCta, J = j / kTile;
-  const int tile = P.tile_of[I][J];
-  const int il = i - I * kRowsPerCta, jl = j - J * kTile;
-  const oz::I128 acc = oz_sum_partials(part + (size_t)tile * (2 * kRowsPerCta * kTile), P.slabs,
-                                       (size_t)P.ntiles * (2 * kRowsPerCta * kTile), il, jl);
+  const int I = i / kM, J = j / kN;
+  const int tile = SP.tile_of[I][J];
+  const oz::I128 acc =
+      oz_sum_partials(part + (size_t)tile * kPartElems, SP.slabs, (size_t)SP.ntiles * kPartElems, i - I * kM, j - J * kN);
   const uint32_t Ei = oz::exp_field(colHi[i]), Ej = oz::exp_field(colHi[j]);
-  out[e] = (Ei == 2047u || Ej == 2047u) ? __longlong_as_double(0x7FF8000000000000ll)
-                                        : oz::i128_to_double(acc, (int)Ei + (int)Ej - oz::kScaleBias);
+  out[e] = (Ei == 2047u || Ej == 2047u) ? nan64() : oz::i128_to_double(acc, (int)Ei + (int)Ej - oz::kScaleBias);
 }
 
 // ---------------------------------------------------------------------------
@@ -420,143 +470,100 @@ __global__ void k_syrk_oz_reduce(int n, const uint32_t* __restrict__ colHi, Syrk
 // 128 columns of A, 64 sampled rows, slab of rows of A).
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_sketch_oz(int64_t m, int n, int s, const double* __restrict__ A, int64_t lda, const uint32_t* __restrict__ colHi,
-                const uint32_t* __restrict__ idx, const double* __restrict__ tab, uint2 key, SketchOzPlan P,
+                const uint32_t* __restrict__ idx, const double* __restrict__ tab, uint2 key, SketchOzPlan SP,
                 long long* __restrict__ part, Ctl* ctl, int level) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* as = smem;                                   // 8 digits x (128 columns x 64 rows)
-  unsigned char* fs = smem + oz::kSlices * kWPanel;           // 8 digits x (64 samples x 64 rows)
+  unsigned char* smem = oz_smem(smem_raw);
   __shared__ __align__(8) uint64_t mma_bar;
-  __shared__ uint32_t tmem_base;
-  __shared__ uint32_t colE[kRowsPerCta];
-  __shared__ uint32_t flips[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ uint32_t colE[kM];
+  OzPipe P = oz_begin(&tmem_slot, &mma_bar);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
-  if (tid == 0) {
-    tc::mbar_init(&mma_bar, 1);
-    tc::mbar_fence_init();
-  }
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t idesc = tc::idesc(tc::F16, kRowsPerCta, kTile);
-  const int q = warp & 3, g = warp >> 2;
   const uint64_t four_m = 4ull * (uint64_t)m;
-  uint32_t phase = 0;
   bool abort = false;
-  const int ntiles_all = P.mblocks * P.ntiles;
-  const int nitems = ntiles_all * P.slabs;
-  // transform-panel role of this thread: sample fi, rows 8 fg .. 8 fg + 7
-  const int fi = tid & (kTile - 1), fg = tid >> 6;
+  const int ntiles_all = SP.mblocks * SP.ntiles;
+  const int nitems = ntiles_all * SP.slabs;
+  // transform-panel role: sample fi, rows 4 fg .. 4 fg + 3 of each chunk
+  const int fi = tid & (kN - 1), fg = tid >> 6;
+  // sign role: rows 2 (lane % 16), 2 (lane % 16) + 1 of each chunk
+  const int sp = lane & 15;
 
   for (int item = blockIdx.x; item < nitems && !abort; item += gridDim.x) {
     const int tile = item % ntiles_all, slab = item / ntiles_all;
-    const int c0 = kRowsPerCta * (tile / P.ntiles), i0 = kTile * (tile % P.ntiles);
-    const int64_t r_begin = (int64_t)slab * P.rows_per_slab;
-    const int64_t r_end = min(m, r_begin + P.rows_per_slab);
-    const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + kTile - 1) / kTile) : 0;
+    const int c0 = kM * (tile / SP.ntiles), i0 = kN * (tile % SP.ntiles);
+    const int64_t r_begin = (int64_t)slab * SP.rows_per_slab;
+    const int64_t r_end = min(m, r_begin + SP.rows_per_slab);
+    const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + kK - 1) / kK) : 0;
     __syncthreads();
-    if (tid < kRowsPerCta) colE[tid] = c0 + tid < n ? oz::exp_field(colHi[c0 + tid]) : 0u;
-    // phase of (sample fi, row r_begin + 8 fg) and its advance per chunk
+    if (tid < kM) colE[tid] = c0 + tid < n ? oz::exp_field(colHi[c0 + tid]) : 0u;
+    __syncthreads();
+    // phase of (sample fi, row r_begin + 4 fg), its advance per chunk and per row
     const bool fval = i0 + fi < s;
     const uint64_t k = fval ? (uint64_t)idx[i0 + fi] : 0ull;
-    uint64_t r = fval ? (k * (uint64_t)(2 * (r_begin + 8 * fg) + 1)) % four_m : 0ull;
-    const uint64_t step_chunk = (k * (uint64_t)(2 * kTile)) % four_m;
+    uint64_t r = fval ? (k * (uint64_t)(2 * (r_begin + 4 * fg) + 1)) % four_m : 0ull;
+    const uint64_t step_chunk = (k * (uint64_t)(2 * kK)) % four_m;
     const uint64_t step_row = 2ull * k;   // < 4m
     long long hi[16], lo[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      const int64_t r0 = r_begin + (int64_t)ch * kTile;
-      const bool group_start = (ch % kGroupChunks) == 0;
-      const bool group_end = (ch % kGroupChunks) == kGroupChunks - 1 || ch == nchunks - 1;
-      // Rademacher signs of the chunk's rows (bit t: d_{r0 + t} = -1)
-      if (warp < 2) {
-        const int64_t j0 = r0 + 32 * warp + lane;
-        const bool neg = j0 < r_end && row_sign((uint64_t)j0, key) < 0.0;
-        const uint32_t bits = __ballot_sync(0xffffffffu, neg);
-        if (lane == 0) flips[warp] = bits;
-      }
-      // transform digits: sample fi, rows 8 fg .. 8 fg + 7
-      {
-        uint64_t rr = r;
-        unsigned char* dst = fs + tc::sw128_offset(fi, 8 * fg, 2);
+    // chunk 0 ahead: A values, table values of this thread's four rows
+    double va[kM / 32][2];
+    uint32_t whi[4], wlo[4];
+    auto load_chunk = [&](int64_t r0) {
+      oz_load_cols<kM>(A, lda, n, c0, r0, r_end, warp, lane, va);
+      uint64_t rr = r;
 #pragma unroll
-        for (int t2 = 0; t2 < 4; ++t2) {
-          int d0[oz::kSlices], d1[oz::kSlices];
+      for (int t = 0; t < 4; ++t) {
+        whi[t] = wlo[t] = 0u;
+        if (fval && r0 + 4 * fg + t < r_end) cos_phase_bits(tab, (int64_t)rr, m, whi[t], wlo[t]);
+        rr += step_row;
+        if (rr >= four_m) rr -= four_m;
+      }
+      r += step_chunk;
+      if (r >= four_m) r -= four_m;
+    };
+    load_chunk(r_begin);
+    auto produce = [&](int ch, unsigned char* a, unsigned char* b) {
+      const int64_t r0 = r_begin + (int64_t)ch * kK;
+      // Rademacher signs of this lane's two rows
+      const int64_t j0 = r0 + 2 * sp;
+      const uint32_t f0 = (j0 < r_end && row_sign((uint64_t)j0, key) < 0.0) ? 1u : 0u;
+      const uint32_t f1 = (j0 + 1 < r_end && row_sign((uint64_t)(j0 + 1), key) < 0.0) ? 1u : 0u;
+      oz_store_cols<kM>(va, colE, f0, f1, a, kAPanel, warp, lane);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int64_t j = r0 + 8 * fg + 2 * t2 + h;
-            uint32_t whi = 0u, wlo = 0u;
-            if (fval && j < r_end) cos_phase_bits(tab, (int64_t)rr, m, whi, wlo);
-            oz::digits8(whi, wlo, 1023u, h ? d1 : d0);
-            rr += step_row;
-            if (rr >= four_m) rr -= four_m;
-          }
-#pragma unroll
-          for (int b = 0; b < oz::kSlices; ++b)
-            *reinterpret_cast<uint32_t*>(dst + 4 * t2 + b * kXPanel) = oz::pack_f16x2(d0[b], d1[b]);
-        }
-        r += step_chunk;
-        if (r >= four_m) r -= four_m;
-      }
-      __syncthreads();   // signs visible
-      const uint64_t flip64 = (uint64_t)flips[0] | ((uint64_t)flips[1] << 32);
-      // digits of d_j A[j][c]: one column per warp
-#pragma unroll 1
-      for (int c = warp; c < kRowsPerCta; c += kOzThreads / 32) {
-        const int col = c0 + c;
-        oz_slice_col_chunk(col < n ? A + (int64_t)col * lda : nullptr, r0, r_end, colE[c], flip64, as, c, kWPanel,
-                           lane);
-      }
-      tc::fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after();
-        oz_issue_chunk(tmem, tc::smem_u32(as), kWPanel, tc::smem_u32(fs), kXPanel, idesc, group_start);
-        tc::mma_commit(&mma_bar);
-      }
-      const bool ok = tc::mbar_wait(&mma_bar, phase);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        abort = true;
-        break;
-      }
-      tc::fence_after();
-      if (group_end) oz_readout(tmem, q, g, hi, lo);
-      tc::fence_before();
-      __syncthreads();
+      for (int t2 = 0; t2 < 2; ++t2)
+        oz_store_pair(__hiloint2double((int)whi[2 * t2], (int)wlo[2 * t2]),
+                      __hiloint2double((int)whi[2 * t2 + 1], (int)wlo[2 * t2 + 1]), 0u, 0u, 1023u,
+                      b + tc::sw64_offset(fi, 4 * fg + 2 * t2, 2), kBPanel);
+      if (ch + 1 < nchunks) load_chunk(r0 + kK);
+    };
+    auto bbase = [&](unsigned char*, unsigned char* b) { return tc::smem_u32(b); };
+    if (!oz_run(P, smem, nchunks, produce, bbase, kBPanel, hi, lo)) {
+      abort = true;
+      break;
     }
-    if (abort) break;
-    oz_store_partial(part + (size_t)item * (2 * kRowsPerCta * kTile), q, g, lane, hi, lo);
+    oz_store_partial(part + (size_t)item * kPartElems, P.q, P.g, lane, hi, lo);
   }
-  if (abort && tid == 0) raise_level_status(ctl, ST_TIMEOUT);
-  tc::fence_before();
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+  oz_end(P, abort, ctl);
 }
 
 // Y (s x n, column-major) from the items' partials: exact sums over the
 // slabs, one rounding, times sqrt(2/s) c_k.  A non-finite column of A gives a
 // NaN column and raises NONFINITE.
 __global__ void k_sketch_oz_reduce(int n, int s, const uint32_t* __restrict__ colHi, const uint32_t* __restrict__ idx,
-                                   SketchOzPlan P, const long long* __restrict__ part, double* __restrict__ Y,
+                                   SketchOzPlan SP, const long long* __restrict__ part, double* __restrict__ Y,
                                    Ctl* ctl, int level) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)s * n) return;
   const int i = (int)(e % s), c = (int)(e / s);
-  const int tile = (c / kRowsPerCta) * P.ntiles + i / kTile;
-  const size_t tstride = 2 * kRowsPerCta * kTile;
-  const oz::I128 acc = oz_sum_partials(part + (size_t)tile * tstride, P.slabs,
-                                       (size_t)P.mblocks * P.ntiles * tstride, c % kRowsPerCta, i % kTile);
+  const int tile = (c / kM) * SP.ntiles + i / kN;
+  const oz::I128 acc = oz_sum_partials(part + (size_t)tile * kPartElems, SP.slabs,
+                                       (size_t)SP.mblocks * SP.ntiles * kPartElems, c % kM, i % kN);
   const uint32_t Ec = oz::exp_field(colHi[c]);
   const double coef = sqrt(2.0 / (double)s) * (idx[i] == 0 ? 0.70710678118654752440 : 1.0);
-  const double y = Ec == 2047u ? __longlong_as_double(0x7FF8000000000000ll)
-                               : oz::i128_to_double(acc, (int)Ec + 1023 - oz::kScaleBias) * coef;
+  const double y = Ec == 2047u ? nan64() : oz::i128_to_double(acc, (int)Ec + 1023 - oz::kScaleBias) * coef;
   Y[e] = y;
   if (!isfinite(y)) {
     ctl->input_nonfinite = 1;
@@ -564,30 +571,264 @@ __global__ void k_sketch_oz_reduce(int n, int s, const uint32_t* __restrict__ co
   }
 }
 
-}  // namespace
+// ---------------------------------------------------------------------------
+// W = A R^{-1} (Algorithm 2 step 7, R = R_s upper triangular; rows of W by
+// substitution, Sec. II-A), blocked by 16 columns.  For sub-block J:
+//   B_J = A_J - W_{<J} R_{<J,J}   emulated FP64 product (one rounding), then
+//                                  one FP64 subtraction;
+//   W_J = B_J R_JJ^{-1}           substitution in FP64 on the 16 x 16 block,
+//                                  as the FMA kernel does it.
+// The FP64 work falls from n^2/2 to 8n fused multiply-adds per row.  128 rows
+// per work block, 256 threads, two CTAs per SM (one CTA's substitution runs
+// while the other's MMAs do).  The product is formed as (W D)(D^-1 R) with
+// D = diag(2^e_k), 2^e_k the binade of the largest entry of row k of R: a
+// graded R (rows falling by many orders, the usual shape of R_s) then pairs
+// balanced operands, and the digit error stays relative to |W| |R| as in
+// substitution.  W's digits are taken against the running maxima of the rows
+// of W D, R's against the column maxima of D^-1 R above the diagonal block.
+constexpr int kTB = 16;                           // sub-block width = MMA N
+constexpr int kTThreads = 256;
+constexpr uint32_t kTAPanel = kM * 64;            // one digit, 128 rows x 32 K (8 KiB)
+constexpr uint32_t kTBPanel = kTB * 64;           // one digit, 16 rows x 32 K (1 KiB)
+constexpr size_t kTSmem = (size_t)oz::kSlices * (kTAPanel + kTBPanel) + sizeof(double) * kM * kTB + 1024;
 
-size_t oz_xs_bytes(int n) {
-  const int n64 = (n + kTile - 1) / kTile * kTile;
-  const int nt = n64 / kTile;
-  return (size_t)oz::kSlices * nt * nt * kXPanel;
+// e_k = unbiased exponent of max_c |R[k][c]| (0 for a zero row): the
+// diagonal scaling of the product.  One warp per row.
+__global__ void __launch_bounds__(256) k_oz_row_scale(int n, int npad, const double* __restrict__ RT,
+                                                      int* __restrict__ eR, const Ctl* ctl, int level) {
+  if (ctl && (level_inactive(ctl, level) || ctl->lvl_status != 0)) return;
+  const int k = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k >= n) return;
+  uint32_t mx = 0u;
+  for (int c = lane; c < n; c += 32) mx = max(mx, (uint32_t)__double2hiint(RT[(int64_t)k * npad + c]) & 0x7FFFFFFFu);
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (lane == 0) {
+    const int E = (int)oz::exp_field(mx);
+    eR[k] = (E == 0 || E == 2047) ? 0 : E - 1023;
+  }
 }
 
-void launch_finalize_oz(int64_t m, int n, double* Q, int64_t ldq, const double* XT, uint32_t* colE,
-                        unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st) {
+// Digits of D^-1 R: panel (J, kc) holds columns [16J, 16J+16) (as rows) and
+// rows k in [32kc, 32kc+32) of R 2^-e_k, zero for k >= 16J; colE[c] = the
+// largest exponent of R[k][c] 2^-e_k over k < 16 (c / 16) (2047 when a used
+// entry is not finite).  RT[k][c] = R[k][c], row stride npad.
+__global__ void __launch_bounds__(256) k_oz_prep_r(int n, int npad, int nkc, const double* __restrict__ RT,
+                                                   const int* __restrict__ eR, int* __restrict__ colE,
+                                                   unsigned char* __restrict__ Rd, const Ctl* ctl, int level) {
+  if (ctl && (level_inactive(ctl, level) || ctl->lvl_status != 0)) return;
+  const int c = blockIdx.x;   // column, < 16 ceil(n / 16)
+  const int J = c / kTB, kend = kTB * J;
+  __shared__ int red[8];
+  __shared__ int bad[8];
+  int mx = -100000, nf = 0;
+  for (int k = threadIdx.x; k < kend; k += blockDim.x)
+    if (c < n) {
+      const int E = (int)oz::exp_field((uint32_t)__double2hiint(RT[(int64_t)k * npad + c]));
+      if (E == 2047) nf = 1;
+      else if (E != 0) mx = max(mx, E - eR[k]);
+    }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  nf = __reduce_or_sync(0xffffffffu, nf);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = mx;
+    bad[threadIdx.x >> 5] = nf;
+  }
+  __syncthreads();
+  int E = red[0], anybad = bad[0];
+  for (int w = 1; w < 8; ++w) {
+    E = max(E, red[w]);
+    anybad |= bad[w];
+  }
+  if (E == -100000) E = 0;   // no nonzero entry: every digit is zero
+  if (threadIdx.x == 0) colE[c] = anybad ? 2047 : E;
+  const int nch = (kend + kK - 1) / kK;
+  for (int k = threadIdx.x; k < nch * kK; k += blockDim.x) {
+    int d[oz::kSlices];
+    const double x = (c < n && k < kend) ? RT[(int64_t)k * npad + c] : 0.0;
+    oz::digits8((uint32_t)__double2hiint(x), (uint32_t)__double2loint(x), E, d, k < n ? -eR[k] : 0);
+    unsigned char* panel = Rd + (size_t)(J * nkc + k / kK) * oz::kSlices * kTBPanel;
+#pragma unroll
+    for (int b = 0; b < oz::kSlices; ++b)
+      *reinterpret_cast<__half*>(panel + b * kTBPanel + tc::sw64_offset(c % kTB, k % kK, 2)) =
+          __float2half_rn(oz::small_int_to_float(d[b]));
+  }
+}
+
+__global__ void __launch_bounds__(kTThreads, 2)
+    k_trsm_oz(int64_t m, int n, const double* __restrict__ A, int64_t lda, const double* __restrict__ RT,
+              const double* __restrict__ rinv, const int* __restrict__ eR, const int* __restrict__ colE,
+              const unsigned char* __restrict__ Rd, int nkc, double* W, int64_t ldw, Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = oz_smem(smem_raw);
+  unsigned char* as = smem;                                             // 8 x 8 KiB
+  unsigned char* bs = smem + oz::kSlices * kTAPanel;                    // 8 x 1 KiB
+  double* Bblk = reinterpret_cast<double*>(bs + oz::kSlices * kTBPanel);   // [16][128]
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int rowX[kM];             // running max exponent of W D per row (kNonfinite: a non-finite entry)
+  __shared__ int eRs[512];             // e_k
+  __shared__ double Rd16[kTB][kTB + 1];   // diagonal block R_JJ
+  __shared__ double rinv16[kTB];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, 128);
+  if (tid == 0) {
+    tc::mbar_init(&mma_bar, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = tc::idesc(tc::F16, kM, kTB);
+  const int q = warp & 3, g = warp >> 2;   // readout: lanes 32 q.., columns 8 g..8 g + 7
   const int npad = (n + 31) / 32 * 32;
-  const int n64 = (n + kTile - 1) / kTile * kTile;
-  k_oz_prep_x<<<n64, 512, 0, st>>>(n, npad, n64, XT, colE, Xs, ctl, level);
-  const size_t smem = (size_t)oz::kSlices * (kWPanel + kXPanel) + 1024;
-  cudaFuncSetAttribute(k_finalize_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t nblocks = (m + kRowsPerCta - 1) / kRowsPerCta;
-  const unsigned grid = (unsigned)(nblocks < sms ? nblocks : sms);
-  k_finalize_oz<<<grid, kOzThreads, smem, st>>>(m, n, n64, Q, ldq, colE, Xs, ctl, level);
+  const int nsub = (n + kTB - 1) / kTB;
+  uint32_t commits = 0;
+  bool abort = false;
+  const int64_t nblocks = (m + kM - 1) / kM;
+  const int pr = tid & (kM - 1), ph = tid >> 7;   // producer role: row pr, column pairs ph + 2 i
+  constexpr int kNoEntry = -100000, kNonfinite = 100000;
+  for (int k = tid; k < n; k += kTThreads) eRs[k] = eR[k];
+
+  for (int64_t rb = blockIdx.x; rb < nblocks && !abort; rb += gridDim.x) {
+    const int64_t r0 = rb * kM;
+    if (tid < kM) rowX[tid] = kNoEntry;
+    __syncthreads();
+    for (int J = 0; J < nsub && !abort; ++J) {
+      const int c0 = J * kTB;
+      // diagonal block and reciprocals of this sub-block
+      {
+        const int a = tid / kTB, b = tid % kTB;   // 256 threads = 16 x 16
+        Rd16[a][b] = (c0 + a < n && c0 + b < n) ? RT[(int64_t)(c0 + a) * npad + c0 + b] : 0.0;
+        if (tid < kTB) rinv16[tid] = rinv[c0 + tid];
+      }
+      // B_J = A_J - W_{<J} R_{<J,J}, thread (row 32 q + lane, columns 8 g .. 8 g + 7)
+      const int rr = q * 32 + lane;
+      const bool rlive = r0 + rr < m;
+      double bv[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int col = c0 + 8 * g + c;
+        bv[c] = (rlive && col < n) ? A[r0 + rr + (int64_t)col * lda] : 0.0;
+      }
+      if (J > 0) {
+        long long hi[8], lo[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) hi[c] = lo[c] = 0;
+        const int nch = (c0 + kK - 1) / kK;
+        const bool plive = r0 + pr < m;
+        const int Er = rowX[pr];
+        for (int kc = 0; kc < nch; ++kc) {
+          // R digits of (J, kc): 8 KiB, two asynchronous 16-byte copies per thread
+          const uint4* src = reinterpret_cast<const uint4*>(Rd + (size_t)(J * nkc + kc) * oz::kSlices * kTBPanel);
+#pragma unroll
+          for (int i = 0; i < 2; ++i) tc::cp_async16(bs + 16 * (tid + kTThreads * i), src + tid + kTThreads * i);
+          // W digits of columns [32 kc, 32 kc + 32) (zero from c0 on): row pr, column pairs ph + 2 i
+          double v[8][2];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k0 = kc * kK + 2 * (ph + 2 * i);
+            v[i][0] = (plive && k0 < c0) ? W[r0 + pr + (int64_t)k0 * ldw] : 0.0;
+            v[i][1] = (plive && k0 + 1 < c0) ? W[r0 + pr + (int64_t)(k0 + 1) * ldw] : 0.0;
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k0 = kc * kK + 2 * (ph + 2 * i);
+            oz_store_pair(v[i][0], v[i][1], 0u, 0u, Er, as + tc::sw64_offset(pr, 2 * (ph + 2 * i), 2), kTAPanel,
+                          k0 < n ? eRs[k0] : 0, k0 + 1 < n ? eRs[k0 + 1] : 0);
+          }
+          tc::cp_async_wait_all();
+          tc::fence_proxy_async();
+          tc::fence_before();
+          __syncthreads();
+          if (tid == 0) {
+            tc::fence_after();
+            const uint64_t da = tc::sw64_desc(tc::smem_u32(as)), db = tc::sw64_desc(tc::smem_u32(bs));
+            const uint32_t first = (kc % kGroupChunks) == 0 ? 0u : 1u;
+#pragma unroll
+            for (int a = 0; a < oz::kLevels; ++a)
+#pragma unroll
+              for (int kk = 0; kk < kK; kk += 16)
+#pragma unroll
+                for (int L = a; L < oz::kLevels; ++L)
+                  tc::mma_f16(tmem + (uint32_t)(L * kTB), da + (uint64_t)((a * kTAPanel + kk * 2) >> 4),
+                              db + (uint64_t)(((L - a) * kTBPanel + kk * 2) >> 4), idesc,
+                              (a == 0 && kk == 0) ? first : 1u);
+            tc::mma_commit(&mma_bar);
+          }
+          const bool ok = tc::mbar_wait(&mma_bar, commits & 1u);
+          ++commits;
+          if (__syncthreads_or(!ok)) {
+            abort = true;
+            break;
+          }
+          tc::fence_after();
+          if (kc % kGroupChunks == kGroupChunks - 1 || kc == nch - 1) {
+            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 8);
+#pragma unroll 1
+            for (int L = 0; L < oz::kLevels; ++L) {
+              float f[8];
+              tc::tmem_ld8(base + (uint32_t)(L * kTB), f);
+              tc::tmem_wait_ld();
+#pragma unroll
+              for (int c = 0; c < 8; ++c) oz::add_level(L, f[c], hi[c], lo[c]);
+            }
+          }
+          tc::fence_before();
+          __syncthreads();   // panels and accumulators free for the next chunk
+        }
+        if (abort) break;
+        const int Erow = rowX[rr];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int col = c0 + 8 * g + c;
+          if (col < n) {
+            const int ce = colE[col];
+            const double p = (Erow == kNonfinite || ce == 2047)
+                                 ? nan64()
+                                 : oz::i128_to_double(hi[c], lo[c], Erow + ce - oz::kScaleBias);
+            bv[c] -= p;
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) Bblk[(8 * g + c) * kM + rr] = bv[c];
+      __syncthreads();
+      // substitution on the diagonal block, one thread per row
+      if (tid < kM) {
+        double t[kTB];
+#pragma unroll
+        for (int c = 0; c < kTB; ++c) t[c] = Bblk[c * kM + tid];
+        int mx = rowX[tid];
+#pragma unroll
+        for (int c = 0; c < kTB; ++c) {
+          t[c] *= rinv16[c];
+#pragma unroll
+          for (int c2 = c + 1; c2 < kTB; ++c2) t[c2] = fma(-t[c], Rd16[c][c2], t[c2]);
+        }
+        if (r0 + tid < m) {
+#pragma unroll
+          for (int c = 0; c < kTB; ++c)
+            if (c0 + c < n) {
+              W[r0 + tid + (int64_t)(c0 + c) * ldw] = t[c];
+              const int E = (int)oz::exp_field((uint32_t)__double2hiint(t[c]));
+              if (E == 2047) mx = kNonfinite;
+              else if (E != 0 && mx != kNonfinite) mx = max(mx, E + eRs[c0 + c]);
+            }
+        }
+        rowX[tid] = mx;
+      }
+      __syncthreads();
+    }
+  }
+  if (abort && tid == 0) raise_level_status(ctl, ST_TIMEOUT);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
 
-static int num_sms() {
+int num_sms() {
   static int cached = 0;
   if (!cached) {
     int dev = 0, sms = 0;
@@ -598,101 +839,140 @@ static int num_sms() {
   return cached;
 }
 
-static int gcd_int(int a, int b) { return b ? gcd_int(b, a % b) : a; }
+int gcd_int(int a, int b) { return b ? gcd_int(b, a % b) : a; }
+
+// Row slabs so that tiles x slabs is a multiple of the SM count where the
+// rows allow it; at least 256 rows per slab, at most 2^20 (the 64-bit halves
+// of an item stay below 2^61).
+int choose_slabs(int64_t m, int tiles, int64_t* rows_per_slab) {
+  const int sms = num_sms();
+  int slabs = tiles >= sms ? 1 : sms / gcd_int(tiles, sms);
+  const int64_t max_slabs = (m + 255) / 256;
+  if (slabs > max_slabs) slabs = (int)max_slabs;
+  const int64_t min_slabs = (m + (1 << 20) - 1) >> 20;
+  if (slabs < min_slabs) slabs = (int)min_slabs;
+  if (slabs < 1) slabs = 1;
+  int64_t rps = (m + slabs - 1) / slabs;
+  rps = (rps + kK - 1) / kK * kK;
+  *rows_per_slab = rps;
+  return (int)((m + rps - 1) / rps);
+}
+
+void launch_col_hi(int64_t m, int n, const double* X, int64_t ldx, uint32_t* colHi, const Ctl* ctl, int level,
+                   cudaStream_t st);
+
+template <class K>
+void set_smem(K kernel) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+}
+
+}  // namespace
+
+size_t oz_xs_bytes(int n) {
+  const int n64 = (n + kN - 1) / kN * kN;
+  return (size_t)oz::kSlices * (n64 / kN) * (n64 / kK) * kBPanel;
+}
+
+size_t syrk_oz_colhi_bytes(int n) { return sizeof(uint32_t) * (size_t)((n + kM - 1) / kM * kM); }
+
+namespace {
+void launch_col_hi(int64_t m, int n, const double* X, int64_t ldx, uint32_t* colHi, const Ctl* ctl, int level,
+                   cudaStream_t st) {
+  cudaMemsetAsync(colHi, 0, syrk_oz_colhi_bytes(n), st);
+  int ysplit = (4 * num_sms() + n - 1) / n;
+  const int64_t max_y = (m + 4095) / 4096;
+  if (ysplit > max_y) ysplit = (int)max_y;
+  if (ysplit < 1) ysplit = 1;
+  k_col_hi<<<dim3(n, ysplit), 256, 0, st>>>(m, n, X, ldx, (m + ysplit - 1) / ysplit, colHi, ctl, level);
+}
+}  // namespace
+
+void launch_finalize_oz(int64_t m, int n, double* Q, int64_t ldq, const double* XT, uint32_t* colE,
+                        unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st) {
+  const int npad = (n + 31) / 32 * 32;
+  const int n64 = (n + kN - 1) / kN * kN;
+  k_oz_prep_x<<<n64, 512, 0, st>>>(n, npad, n64, XT, colE, Xs, ctl, level);
+  set_smem(k_finalize_oz);
+  const int64_t nblocks = (m + kM - 1) / kM;
+  const unsigned grid = (unsigned)(nblocks < num_sms() ? nblocks : num_sms());
+  k_finalize_oz<<<grid, kOzThreads, kSmem, st>>>(m, n, n64, Q, ldq, colE, Xs, ctl, level);
+}
 
 SyrkOzPlan syrk_oz_plan(int64_t m, int n) {
   SyrkOzPlan P{};
-  const int nI = (n + kRowsPerCta - 1) / kRowsPerCta, nJ = (n + kTile - 1) / kTile;
+  const int nI = (n + kM - 1) / kM, nJ = (n + kN - 1) / kN;
   for (int I = 0; I < 4; ++I)
     for (int J = 0; J < 8; ++J) P.tile_of[I][J] = -1;
   for (int I = 0; I < nI; ++I)
     for (int J = 0; J < nJ; ++J)
-      if (kTile * J + kTile - 1 >= kRowsPerCta * I) {
+      if (kN * J + kN - 1 >= kM * I) {
         P.ti[P.ntiles] = (int8_t)I;
         P.tj[P.ntiles] = (int8_t)J;
         P.tile_of[I][J] = (int8_t)P.ntiles;
         ++P.ntiles;
       }
-  // items = tiles x slabs a multiple of the SM count where the rows allow it
-  const int sms = num_sms();
-  int slabs = sms / gcd_int(P.ntiles, sms);
-  const int64_t max_slabs = (m + 4 * kTile - 1) / (4 * kTile);   // at least 256 rows each
-  if (slabs > max_slabs) slabs = (int)max_slabs;
-  // at most 2^20 rows per slab: the 64-bit halves of an item stay below 2^61
-  const int64_t min_slabs = (m + (1 << 20) - 1) >> 20;
-  if (slabs < min_slabs) slabs = (int)min_slabs;
-  if (slabs < 1) slabs = 1;
-  int64_t rps = (m + slabs - 1) / slabs;
-  rps = (rps + kTile - 1) / kTile * kTile;
-  P.rows_per_slab = rps;
-  P.slabs = (int)((m + rps - 1) / rps);
+  P.slabs = choose_slabs(m, P.ntiles, &P.rows_per_slab);
   return P;
 }
 
-size_t syrk_oz_part_bytes(const SyrkOzPlan& P) {
-  return sizeof(long long) * 2 * kRowsPerCta * kTile * (size_t)P.ntiles * P.slabs;
-}
-
-size_t syrk_oz_colhi_bytes(int n) { return sizeof(uint32_t) * (size_t)((n + kRowsPerCta - 1) / kRowsPerCta * kRowsPerCta); }
+size_t syrk_oz_part_bytes(const SyrkOzPlan& P) { return sizeof(long long) * kPartElems * (size_t)P.ntiles * P.slabs; }
 
 void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOzPlan& P, uint32_t* colHi,
                     long long* part, double* out, Ctl* ctl, int level, cudaStream_t st) {
-  cudaMemsetAsync(colHi, 0, syrk_oz_colhi_bytes(n), st);
-  const int sms = num_sms();
-  int ysplit = (4 * sms + n - 1) / n;
-  const int64_t max_y = (m + 4095) / 4096;
-  if (ysplit > max_y) ysplit = (int)max_y;
-  if (ysplit < 1) ysplit = 1;
-  const int64_t rpc = (m + ysplit - 1) / ysplit;
-  k_col_hi<<<dim3(n, ysplit), 256, 0, st>>>(m, n, W, ldw, rpc, colHi, ctl, level);
-  const size_t smem = (size_t)oz::kSlices * (kWPanel + kXPanel) + 1024;
-  cudaFuncSetAttribute(k_syrk_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  launch_col_hi(m, n, W, ldw, colHi, ctl, level, st);
+  set_smem(k_syrk_oz);
   const int nitems = P.ntiles * P.slabs;
-  k_syrk_oz<<<nitems < sms ? nitems : sms, kOzThreads, smem, st>>>(m, n, W, ldw, colHi, P, part, ctl, level);
+  k_syrk_oz<<<nitems < num_sms() ? nitems : num_sms(), kOzThreads, kSmem, st>>>(m, n, W, ldw, colHi, P, part, ctl,
+                                                                               level);
   const int64_t nn = (int64_t)n * n;
   k_syrk_oz_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, colHi, P, part, out, ctl, level);
 }
 
 SketchOzPlan sketch_oz_plan(int64_t m, int n, int s) {
   SketchOzPlan P{};
-  P.mblocks = (n + kRowsPerCta - 1) / kRowsPerCta;
-  P.ntiles = (s + kTile - 1) / kTile;
-  const int tiles = P.mblocks * P.ntiles;
-  const int sms = num_sms();
-  int slabs = tiles >= sms ? 1 : sms / gcd_int(tiles, sms);
-  const int64_t max_slabs = (m + 4 * kTile - 1) / (4 * kTile);
-  if (slabs > max_slabs) slabs = (int)max_slabs;
-  const int64_t min_slabs = (m + (1 << 20) - 1) >> 20;
-  if (slabs < min_slabs) slabs = (int)min_slabs;
-  if (slabs < 1) slabs = 1;
-  int64_t rps = (m + slabs - 1) / slabs;
-  rps = (rps + kTile - 1) / kTile * kTile;
-  P.rows_per_slab = rps;
-  P.slabs = (int)((m + rps - 1) / rps);
+  P.mblocks = (n + kM - 1) / kM;
+  P.ntiles = (s + kN - 1) / kN;
+  P.slabs = choose_slabs(m, P.mblocks * P.ntiles, &P.rows_per_slab);
   return P;
 }
 
 size_t sketch_oz_part_bytes(const SketchOzPlan& P) {
-  return sizeof(long long) * 2 * kRowsPerCta * kTile * (size_t)P.mblocks * P.ntiles * P.slabs;
+  return sizeof(long long) * kPartElems * (size_t)P.mblocks * P.ntiles * P.slabs;
 }
 
 void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, const uint32_t* idx, const double* tab,
                       uint64_t seed, const SketchOzPlan& P, uint32_t* colHi, long long* part, double* Y, Ctl* ctl,
                       int level, cudaStream_t st) {
-  cudaMemsetAsync(colHi, 0, syrk_oz_colhi_bytes(n), st);
-  const int sms = num_sms();
-  int ysplit = (4 * sms + n - 1) / n;
-  const int64_t max_y = (m + 4095) / 4096;
-  if (ysplit > max_y) ysplit = (int)max_y;
-  if (ysplit < 1) ysplit = 1;
-  k_col_hi<<<dim3(n, ysplit), 256, 0, st>>>(m, n, A, lda, (m + ysplit - 1) / ysplit, colHi, ctl, level);
-  const size_t smem = (size_t)oz::kSlices * (kWPanel + kXPanel) + 1024;
-  cudaFuncSetAttribute(k_sketch_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  launch_col_hi(m, n, A, lda, colHi, ctl, level, st);
+  set_smem(k_sketch_oz);
   const int nitems = P.mblocks * P.ntiles * P.slabs;
-  k_sketch_oz<<<nitems < sms ? nitems : sms, kOzThreads, smem, st>>>(m, n, s, A, lda, colHi, idx, tab, seed_key(seed),
-                                                                      P, part, ctl, level);
+  k_sketch_oz<<<nitems < num_sms() ? nitems : num_sms(), kOzThreads, kSmem, st>>>(m, n, s, A, lda, colHi, idx, tab,
+                                                                                 seed_key(seed), P, part, ctl, level);
   const int64_t total = (int64_t)s * n;
   k_sketch_oz_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, colHi, idx, P, part, Y, ctl, level);
+}
+
+size_t trsm_oz_rd_bytes(int n) {
+  const int nsub = (n + kTB - 1) / kTB, nkc = (n + kK - 1) / kK;
+  return (size_t)nsub * nkc * oz::kSlices * kTBPanel;
+}
+
+size_t trsm_oz_cole_bytes(int n) { return 2 * sizeof(int) * (size_t)((n + kTB - 1) / kTB * kTB); }
+
+void launch_trsm_oz(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv,
+                    uint32_t* colE_ws, unsigned char* Rd, double* W, int64_t ldw, Ctl* ctl, int level, cudaStream_t st) {
+  const int npad = (n + 31) / 32 * 32;
+  const int nkc = (n + kK - 1) / kK;
+  const int n16 = (n + kTB - 1) / kTB * kTB;
+  int* colE = reinterpret_cast<int*>(colE_ws);
+  int* eR = colE + n16;
+  k_oz_row_scale<<<(n + 7) / 8, 256, 0, st>>>(n, npad, RT, eR, ctl, level);
+  k_oz_prep_r<<<n16, 256, 0, st>>>(n, npad, nkc, RT, eR, colE, Rd, ctl, level);
+  cudaFuncSetAttribute(k_trsm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
+  const int64_t nblocks = (m + kM - 1) / kM;
+  const int64_t slots = 2 * (int64_t)num_sms();
+  k_trsm_oz<<<(unsigned)(nblocks < slots ? nblocks : slots), kTThreads, kTSmem, st>>>(m, n, A, lda, RT, rinv, eR,
+                                                                                       colE, Rd, nkc, W, ldw, ctl, level);
 }
 
 }  // namespace mrcqr

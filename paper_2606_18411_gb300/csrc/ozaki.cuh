@@ -41,24 +41,31 @@ constexpr int kScaleBias = 2114;   // T 2^(Erow + Ecol - kScaleBias) is the prod
 // subnormals, which slice to zero against any normal reference).
 __device__ __forceinline__ uint32_t exp_field(uint32_t hi) { return (hi >> 20) & 0x7FFu; }
 
-// Signed digits d[0..7] of x (FP64 bits hi:lo) against the reference
-// exponent Eref (biased exponent of the row maximum, >= the exponent of x),
-// sign of x included.  Zero, subnormals and a zero reference give zeros.
-__device__ __forceinline__ void digits8(uint32_t hi, uint32_t lo, uint32_t Eref, int* d) {
-  const uint32_t E = exp_field(hi);
-  int64_t v = 0;
-  if (E != 0 && Eref != 0) {
+// Signed digits d[0..7] of x 2^eoff (FP64 bits hi:lo of x) against the
+// reference exponent Eref (biased; >= the exponent of x 2^eoff), sign of x
+// included.  Zero and subnormal x give zeros.  The power-of-two scale eoff
+// (a diagonal scaling D of a product (X D)(D^-1 Y)) never rounds.
+// Adding 128 at each of the seven low byte positions turns the plain bytes of
+// the sum into the balanced digits plus 128 (the carries do the rest).
+__device__ __forceinline__ void digits8(uint32_t hi, uint32_t lo, int Eref, int* d, int eoff = 0) {
+  const int E = (int)exp_field(hi);
+  uint64_t v = 0;
+  if (E != 0) {
     const uint64_t M = ((uint64_t)(hi & 0xFFFFFu) << 32 | lo) | (1ull << 52);
-    const int sh = (int)E - (int)Eref + 10;   // I = round(M 2^sh), sh <= 10
-    if (sh >= 0) v = (int64_t)(M << sh);
-    else if (sh > -64) v = (int64_t)((M + (1ull << (-sh - 1))) >> (-sh));
+    const int sh = E + eoff - Eref + 10;   // I = round(M 2^sh), sh <= 10
+    if (sh >= 0) v = M << sh;
+    else if (sh > -64) v = (M + (1ull << (-sh - 1))) >> (-sh);
   }
-#pragma unroll
-  for (int a = kSlices - 1; a > 0; --a) {
-    d[a] = (int)((v + 128) & 255) - 128;
-    v = (v - d[a]) >> 8;
-  }
-  d[0] = (int)v;
+  v += 0x0080808080808080ull;
+  const uint32_t l = (uint32_t)v, h = (uint32_t)(v >> 32);
+  d[0] = (int)(h >> 24);
+  d[1] = (int)((h >> 16) & 255u) - 128;
+  d[2] = (int)((h >> 8) & 255u) - 128;
+  d[3] = (int)(h & 255u) - 128;
+  d[4] = (int)(l >> 24) - 128;
+  d[5] = (int)((l >> 16) & 255u) - 128;
+  d[6] = (int)((l >> 8) & 255u) - 128;
+  d[7] = (int)(l & 255u) - 128;
   if (hi >> 31) {
 #pragma unroll
     for (int a = 0; a < kSlices; ++a) d[a] = -d[a];

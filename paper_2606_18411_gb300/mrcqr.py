@@ -235,3 +235,12 @@ def gram(W: torch.Tensor, fp64_products: int = 0, stream=None) -> torch.Tensor:
     check(_lib.load().mrcqr_gram(m, n, W.data_ptr(), _ld(W, "W"), G.data_ptr(), int(fp64_products),
                                  _stream(stream)), "mrcqr_gram")
     return G
+
+
+def trsm(A: torch.Tensor, R: torch.Tensor, fp64_products: int = 0, stream=None) -> torch.Tensor:
+    """W = A R^{-1} (R upper triangular; its upper triangle is read), column-major m x n."""
+    m, n = A.shape
+    W = empty_colmajor(m, n, device=A.device)
+    check(_lib.load().mrcqr_trsm(m, n, A.data_ptr(), _ld(A, "A"), R.data_ptr(), _ld(R, "R"), W.data_ptr(),
+                                 _ld(W, "W"), int(fp64_products), _stream(stream)), "mrcqr_trsm")
+    return W

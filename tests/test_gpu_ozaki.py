@@ -299,3 +299,56 @@ def test_factorization_fp64_sketch_emulated_vs_fma(env):
         out.append((O.orthogonality_error(Qh)[0], O.residual_error(A, Qh, Rh)[0]))
     for o, r in out:
         assert o <= 1e-13 and r <= 1e-13
+
+
+# --- W = A R^{-1} with emulated off-diagonal updates ------------------------
+def _upper(n, kind, seed):
+    rng = np.random.default_rng(seed)
+    R = np.triu(rng.standard_normal((n, n)) * 0.3) + np.diag(1.0 + rng.random(n))
+    if kind == "graded":                       # diagonal from 1 down to 1e-10, rows scaled with it
+        R = np.diag(10.0 ** (-10.0 * np.arange(n) / max(n - 1, 1))) @ R
+    elif kind == "cliff":                      # second half of the rows 1e-12 smaller
+        R[n // 2:] *= 1e-12
+    return R
+
+
+@pytest.mark.parametrize("m,n,kind", [(1000, 17, "plain"), (777, 64, "graded"), (1500, 100, "cliff"),
+                                      (700, 130, "plain"), (513, 256, "graded"), (300, 512, "plain"),
+                                      (129, 33, "cliff"), (5000, 16, "plain")])
+def test_emulated_trsm_backward_error(env, m, n, kind):
+    torch, M = env
+    rng = np.random.default_rng(m * 3 + n)
+    A = rng.standard_normal((m, n))
+    R = _upper(n, kind, seed=n)
+    Ad, Rd = M.to_colmajor(A), M.to_colmajor(R)
+    We = M.trsm(Ad, Rd, fp64_products=0).cpu().numpy()
+    Wf = M.trsm(Ad, Rd, fp64_products=1).cpu().numpy()
+    rows = np.arange(m) if m * n <= 100_000 else rng.choice(m, 100_000 // n, replace=False)
+    scale = np.linalg.norm(np.abs(We[rows]) @ np.abs(R))
+    res = {}
+    for name, Wx in (("emu", We), ("fma", Wf)):
+        WR = O.product_rounded(Wx[rows], R)
+        res[name] = np.linalg.norm(A[rows] - WR)
+    # backward stable like substitution: ||A - W R|| = O(n u) || |W| |R| ||
+    assert res["emu"] <= 4 * n * U * scale, (res, scale)
+    assert res["emu"] <= 4 * res["fma"] + 8 * U * scale, res
+    if n <= 64 and kind == "plain":   # well-conditioned triangle: the oracle's substitution agrees closely
+        Wo = O.trsm_right_upper(A[rows], R)
+        assert np.linalg.norm(We[rows] - Wo) <= 1e-12 * np.linalg.norm(Wo)
+
+
+def test_emulated_trsm_full_height_and_ld(env):
+    torch, M = env
+    m, n = (1 << 20) + 77, 128
+    rng = np.random.default_rng(5)
+    R = _upper(n, "graded", seed=5)
+    At = torch.randn(n, m, dtype=torch.float64, device="cuda").t()           # column-major
+    W = M.trsm(At, M.to_colmajor(R)).cpu().numpy()
+    rows = np.concatenate([rng.choice(m, 400, replace=False), [0, 127, 128, m - 1]])
+    A = At[rows].cpu().numpy()
+    WR = O.product_rounded(W[rows], R)
+    assert np.linalg.norm(A - WR) <= 4 * n * U * np.linalg.norm(np.abs(W[rows]) @ np.abs(R))
+    # odd leading dimensions give the same W
+    A2 = M.to_colmajor(A, ld=len(rows) + 3)
+    W2 = M.trsm(A2, M.to_colmajor(R, ld=n + 1)).cpu().numpy()
+    np.testing.assert_array_equal(W2, M.trsm(M.to_colmajor(A), M.to_colmajor(R)).cpu().numpy())
