@@ -71,12 +71,13 @@ __device__ __forceinline__ void oz_readout(uint32_t tmem, int q, int g, long lon
 // eight digit panels at dst.
 __device__ __forceinline__ void oz_store_pair(double v0, double v1, uint32_t f0, uint32_t f1, int E,
                                               unsigned char* dst, uint32_t pstride, int eo0 = 0, int eo1 = 0) {
-  int d0[oz::kSlices], d1[oz::kSlices];
-  oz::digits8((uint32_t)__double2hiint(v0) ^ (f0 << 31), (uint32_t)__double2loint(v0), E, d0, eo0);
-  oz::digits8((uint32_t)__double2hiint(v1) ^ (f1 << 31), (uint32_t)__double2loint(v1), E, d1, eo1);
+  const uint32_t h0 = (uint32_t)__double2hiint(v0), h1 = (uint32_t)__double2hiint(v1);
+  const uint64_t J0 = oz::biased_fixed63(h0, (uint32_t)__double2loint(v0), E, eo0);
+  const uint64_t J1 = oz::biased_fixed63(h1, (uint32_t)__double2loint(v1), E, eo1);
+  uint32_t w[oz::kSlices];
+  oz::digits8_pack(J0, J1, (h0 >> 31) ^ f0, (h1 >> 31) ^ f1, w);
 #pragma unroll
-  for (int a = 0; a < oz::kSlices; ++a)
-    *reinterpret_cast<uint32_t*>(dst + a * pstride) = oz::pack_f16x2(d0[a], d1[a]);
+  for (int a = 0; a < oz::kSlices; ++a) *reinterpret_cast<uint32_t*>(dst + a * pstride) = w[a];
 }
 
 // A 32-row chunk of NC columns of a column-major matrix (column col0 + c,

@@ -41,13 +41,14 @@ constexpr int kScaleBias = 2114;   // T 2^(Erow + Ecol - kScaleBias) is the prod
 // subnormals, which slice to zero against any normal reference).
 __device__ __forceinline__ uint32_t exp_field(uint32_t hi) { return (hi >> 20) & 0x7FFu; }
 
-// Signed digits d[0..7] of x 2^eoff (FP64 bits hi:lo of x) against the
-// reference exponent Eref (biased; >= the exponent of x 2^eoff), sign of x
-// included.  Zero and subnormal x give zeros.  The power-of-two scale eoff
-// (a diagonal scaling D of a product (X D)(D^-1 Y)) never rounds.
-// Adding 128 at each of the seven low byte positions turns the plain bytes of
-// the sum into the balanced digits plus 128 (the carries do the rest).
-__device__ __forceinline__ void digits8(uint32_t hi, uint32_t lo, int Eref, int* d, int eoff = 0) {
+// The fixed-point integer I = round(|x| 2^eoff 2^(1085 - Eref)) of x (FP64
+// bits hi:lo) against the reference exponent Eref (biased; >= the exponent of
+// x 2^eoff), plus 128 at each of the seven low byte positions: the plain
+// bytes of the result are the balanced digits (the top byte d_0, the others
+// d_a + 128; the carries do the rest).  Zero and subnormal x give I = 0.  The
+// power-of-two scale eoff (a diagonal scaling D of a product (X D)(D^-1 Y))
+// never rounds.
+__device__ __forceinline__ uint64_t biased_fixed63(uint32_t hi, uint32_t lo, int Eref, int eoff) {
   const int E = (int)exp_field(hi);
   uint64_t v = 0;
   if (E != 0) {
@@ -56,7 +57,12 @@ __device__ __forceinline__ void digits8(uint32_t hi, uint32_t lo, int Eref, int*
     if (sh >= 0) v = M << sh;
     else if (sh > -64) v = (M + (1ull << (-sh - 1))) >> (-sh);
   }
-  v += 0x0080808080808080ull;
+  return v + 0x0080808080808080ull;
+}
+
+// Signed digits d[0..7] of x 2^eoff (see biased_fixed63), sign of x included.
+__device__ __forceinline__ void digits8(uint32_t hi, uint32_t lo, int Eref, int* d, int eoff = 0) {
+  const uint64_t v = biased_fixed63(hi, lo, Eref, eoff);
   const uint32_t l = (uint32_t)v, h = (uint32_t)(v >> 32);
   d[0] = (int)(h >> 24);
   d[1] = (int)((h >> 16) & 255u) - 128;
@@ -69,6 +75,30 @@ __device__ __forceinline__ void digits8(uint32_t hi, uint32_t lo, int Eref, int*
   if (hi >> 31) {
 #pragma unroll
     for (int a = 0; a < kSlices; ++a) d[a] = -d[a];
+  }
+}
+
+// The eight digits of two values as packed FP16 pairs (digit a of x0 in the
+// low half of out[a], of x1 in the high half), straight from the bytes of
+// their biased fixed-point words J0, J1 and their signs: FP16 bits
+// 0x6580 + byte are the value 1536 + d_a (one binade, spacing 1), and one
+// fused multiply-add (1536 + d) s - 1536 s = s d per pair applies the sign
+// exactly.
+__device__ __forceinline__ void digits8_pack(uint64_t J0, uint64_t J1, uint32_t neg0, uint32_t neg1, uint32_t* out) {
+  const uint32_t l0 = (uint32_t)J0, h0 = (uint32_t)(J0 >> 32), l1 = (uint32_t)J1, h1 = (uint32_t)(J1 >> 32);
+  const uint32_t sgn = (neg0 << 15) | (neg1 << 31);
+  const uint32_t sb = 0x3C003C00u | sgn;   // (+-1, +-1)
+  const uint32_t cb = 0xE600E600u ^ sgn;   // (-+1536, -+1536)
+  const __half2 s2 = *reinterpret_cast<const __half2*>(&sb);
+  const __half2 c2 = *reinterpret_cast<const __half2*>(&cb);
+#pragma unroll
+  for (int a = 0; a < kSlices; ++a) {
+    const int k = a < 4 ? 3 - a : 7 - a;   // byte of the 32-bit word holding digit a
+    const uint32_t w0 = a < 4 ? h0 : l0, w1 = a < 4 ? h1 : l1;
+    uint32_t t = __byte_perm(w0, w1, (uint32_t)(k | (k << 4) | ((4 + k) << 8) | ((4 + k) << 12))) & 0x00FF00FFu;
+    t += a == 0 ? 0x66006600u : 0x65806580u;
+    const __half2 r = __hfma2(*reinterpret_cast<const __half2*>(&t), s2, c2);
+    out[a] = *reinterpret_cast<const uint32_t*>(&r);
   }
 }
 
