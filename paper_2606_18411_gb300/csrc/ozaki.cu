@@ -29,25 +29,28 @@ constexpr uint32_t kStage = oz::kSlices * (kAPanel + kBPanel);   // 96 KiB
 constexpr size_t kSmem = 2 * (size_t)kStage + 1024;
 constexpr size_t kPartElems = 2 * kM * kN;  // hi and lo of one 128 x 64 item
 
-// The 36 digit-pair MMAs (levels 0..7, two K steps of 16) of one chunk; level
-// L accumulates in TMEM columns [64 L, 64 L + 64).  ab / bb: shared addresses
-// of digit 0 of the A and B panels.  Issued by one thread, round-robin over
-// the levels (round a takes the pair (a, L - a) of every level L >= a) so that
-// consecutive MMAs mostly update different accumulators; the descriptors are
-// the base descriptors plus the panel offsets (address field in 16-byte units).
-__device__ __forceinline__ void oz_issue_chunk(uint32_t tmem, uint32_t ab, uint32_t bb, uint32_t bstride,
-                                               uint32_t idesc, bool group_start) {
+// The digit-pair products of one chunk (two K steps of 16).  Level L
+// accumulates in TMEM columns [64 L, 64 L + 64).  The eight digit panels of B
+// are contiguous, so digits 0 .. 7 - a stacked along N form one operand, and
+// a single MMA of A digit a against it (N = 64 (8 - a), split at N = 256)
+// written at TMEM column 64 a adds A_a B_b to level a + b for every b at once:
+// 12 MMAs per K step instead of one per pair (36), with no discarded pairs.
+// Issued by one thread; the first MMA (a = 0) of a group overwrites all eight
+// levels.  ab / bb: shared addresses of digit 0 of the A and B panels.
+__device__ __forceinline__ void oz_issue_chunk(uint32_t tmem, uint32_t ab, uint32_t bb, bool group_start) {
   const uint64_t da = tc::sw64_desc(ab), db = tc::sw64_desc(bb);
-  const uint32_t first = group_start ? 0u : 1u;
 #pragma unroll
-  for (int a = 0; a < oz::kLevels; ++a) {
+  for (int kk = 0; kk < kK; kk += 16) {
 #pragma unroll
-    for (int kk = 0; kk < kK; kk += 16) {
+    for (int a = 0; a < oz::kLevels; ++a) {
       const uint64_t adesc = da + (uint64_t)((a * kAPanel + kk * 2) >> 4);
+      const int ntot = kN * (oz::kLevels - a);
 #pragma unroll
-      for (int L = a; L < oz::kLevels; ++L)
-        tc::mma_f16(tmem + (uint32_t)(L * kN), adesc, db + (uint64_t)(((uint32_t)(L - a) * bstride + kk * 2) >> 4),
-                    idesc, (a == 0 && kk == 0) ? first : 1u);
+      for (int p0 = 0; p0 < ntot; p0 += 256) {
+        const int nn = ntot - p0 < 256 ? ntot - p0 : 256;
+        tc::mma_f16(tmem + (uint32_t)(kN * a + p0), adesc, db + (uint64_t)((p0 * 64 + kk * 2) >> 4),
+                    tc::idesc(tc::F16, kM, nn), (kk == 0 && a == 0 && group_start) ? 0u : 1u);
+      }
     }
   }
 }
@@ -70,7 +73,8 @@ __device__ __forceinline__ void oz_readout(uint32_t tmem, int q, int g, long lon
 // 2^eo0 / 2^eo1) against the reference exponent E, packed in pairs into the
 // eight digit panels at dst.
 __device__ __forceinline__ void oz_store_pair(double v0, double v1, uint32_t f0, uint32_t f1, int E,
-                                              unsigned char* dst, uint32_t pstride, int eo0 = 0, int eo1 = 0) {
+                                              unsigned char* dst, uint32_t pstride, int eo0 = 0, int eo1 = 0,
+                                              unsigned char* dst2 = nullptr, uint32_t pstride2 = 0) {
   const uint32_t h0 = (uint32_t)__double2hiint(v0), h1 = (uint32_t)__double2hiint(v1);
   const uint64_t J0 = oz::biased_fixed63(h0, (uint32_t)__double2loint(v0), E, eo0);
   const uint64_t J1 = oz::biased_fixed63(h1, (uint32_t)__double2loint(v1), E, eo1);
@@ -78,6 +82,10 @@ __device__ __forceinline__ void oz_store_pair(double v0, double v1, uint32_t f0,
   oz::digits8_pack(J0, J1, (h0 >> 31) ^ f0, (h1 >> 31) ^ f1, w);
 #pragma unroll
   for (int a = 0; a < oz::kSlices; ++a) *reinterpret_cast<uint32_t*>(dst + a * pstride) = w[a];
+  if (dst2) {
+#pragma unroll
+    for (int a = 0; a < oz::kSlices; ++a) *reinterpret_cast<uint32_t*>(dst2 + a * pstride2) = w[a];
+  }
 }
 
 // A 32-row chunk of NC columns of a column-major matrix (column col0 + c,
@@ -102,16 +110,20 @@ __device__ __forceinline__ void oz_load_cols(const double* __restrict__ X, int64
 }
 
 // Digits of the values loaded by oz_load_cols (reference exponent E[c], sign
-// flips f0 / f1 of the lane's two rows) into panel rows c.
+// flips f0 / f1 of the lane's two rows) into panel rows c.  With dup >= 0 the
+// rows c in [dup, dup + kN) are also written to rows c - dup of the B panels
+// at bpanel (a diagonal Gram tile, whose B operand is part of its A operand).
 template <int NC>
 __device__ __forceinline__ void oz_store_cols(const double (&v)[NC / 32][2], const uint32_t* E, uint32_t f0,
                                               uint32_t f1, unsigned char* panel, uint32_t pstride, int warp,
-                                              int lane) {
+                                              int lane, int dup = -1, unsigned char* bpanel = nullptr) {
   const int p = lane & 15, h = lane >> 4;
 #pragma unroll
   for (int it = 0; it < NC / 32; ++it) {
     const int c = 32 * it + 2 * warp + h;
-    oz_store_pair(v[it][0], v[it][1], f0, f1, E[c], panel + tc::sw64_offset(c, 2 * p, 2), pstride);
+    const bool d = dup >= 0 && c >= dup && c < dup + kN;   // uniform per it (dup a multiple of 64)
+    oz_store_pair(v[it][0], v[it][1], f0, f1, E[c], panel + tc::sw64_offset(c, 2 * p, 2), pstride, 0, 0,
+                  d ? bpanel + tc::sw64_offset(c - dup, 2 * p, 2) : nullptr, kBPanel);
   }
 }
 
@@ -123,14 +135,14 @@ struct OzPipe {
 };
 
 // Runs nchunks chunks through the two stages: produce(ch, a, b) writes the
-// digit panels of chunk ch (A at a, B at b); bbase(a, b) gives the B operand
-// base (b, or rows inside a) and bstride its digit stride.  The MMAs of chunk
+// digit panels of chunk ch (A at a, B at b, each digit's panel contiguous
+// after the previous one).  The MMAs of chunk
 // ch overlap with the production of chunk ch + 1.  Level sums are added into
 // hi / lo after every kGroupChunks chunks and after the last.  False when a
 // wait timed out (every thread returns false together).
-template <class Produce, class BBase>
-__device__ __forceinline__ bool oz_run(OzPipe& P, unsigned char* smem, int nchunks, Produce&& produce, BBase&& bbase,
-                                       uint32_t bstride, long long* hi, long long* lo) {
+template <class Produce>
+__device__ __forceinline__ bool oz_run(OzPipe& P, unsigned char* smem, int nchunks, Produce&& produce, long long* hi,
+                                       long long* lo) {
   for (int ch = 0; ch < nchunks; ++ch) {
     unsigned char* a = smem + (ch & 1) * kStage;
     unsigned char* b = a + oz::kSlices * kAPanel;
@@ -147,7 +159,7 @@ __device__ __forceinline__ bool oz_run(OzPipe& P, unsigned char* smem, int nchun
     }
     if (P.tid == 0) {
       tc::fence_after();
-      oz_issue_chunk(P.tmem, tc::smem_u32(a), bbase(a, b), bstride, P.idesc, ch % kGroupChunks == 0);
+      oz_issue_chunk(P.tmem, tc::smem_u32(a), tc::smem_u32(b), ch % kGroupChunks == 0);
       tc::mma_commit(P.bar);
     }
     ++P.commits;
@@ -328,8 +340,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (kc + 1 < nch) load_w(kc + 1);
         tc::cp_async_wait_all();
       };
-      auto bbase = [&](unsigned char*, unsigned char* b) { return tc::smem_u32(b); };
-      if (!oz_run(P, smem, nch, produce, bbase, kBPanel, hi, lo)) {
+      if (!oz_run(P, smem, nch, produce, hi, lo)) {
         abort = true;
         break;
       }
@@ -419,7 +430,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     oz_load_cols<kM>(W, ldw, n, i0, r_begin, r_end, warp, lane, va);
     auto produce = [&](int ch, unsigned char* a, unsigned char* b) {
       const int64_t r0 = r_begin + (int64_t)ch * kK;
-      oz_store_cols<kM>(va, colE, 0u, 0u, a, kAPanel, warp, lane);
+      oz_store_cols<kM>(va, colE, 0u, 0u, a, kAPanel, warp, lane, inner ? j0 - i0 : -1, b);
       if (ch + 1 < nchunks) oz_load_cols<kM>(W, ldw, n, i0, r0 + kK, r_end, warp, lane, va);
       if (!inner) {   // second operand of an off-diagonal tile: loaded and sliced at once
         double vb[kN / 32][2];
@@ -427,10 +438,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         oz_store_cols<kN>(vb, colE + kM, 0u, 0u, b, kBPanel, warp, lane);
       }
     };
-    auto bbase = [&](unsigned char* a, unsigned char* b) {
-      return inner ? tc::smem_u32(a) + (uint32_t)(j0 - i0) * 64u : tc::smem_u32(b);
-    };
-    if (!oz_run(P, smem, nchunks, produce, bbase, inner ? kAPanel : kBPanel, hi, lo)) {
+    if (!oz_run(P, smem, nchunks, produce, hi, lo)) {
       abort = true;
       break;
     }
@@ -539,8 +547,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                       b + tc::sw64_offset(fi, 4 * fg + 2 * t2, 2), kBPanel);
       if (ch + 1 < nchunks) load_chunk(r0 + kK);
     };
-    auto bbase = [&](unsigned char*, unsigned char* b) { return tc::smem_u32(b); };
-    if (!oz_run(P, smem, nchunks, produce, bbase, kBPanel, hi, lo)) {
+    if (!oz_run(P, smem, nchunks, produce, hi, lo)) {
       abort = true;
       break;
     }
@@ -681,7 +688,6 @@ __global__ void __launch_bounds__(kTThreads, 2)
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t idesc = tc::idesc(tc::F16, kM, kTB);
   const int q = warp & 3, g = warp >> 2;   // readout: lanes 32 q.., columns 8 g..8 g + 7
   const int npad = (n + 31) / 32 * 32;
   const int nsub = (n + kTB - 1) / kTB;
@@ -747,15 +753,14 @@ __global__ void __launch_bounds__(kTThreads, 2)
             tc::fence_after();
             const uint64_t da = tc::sw64_desc(tc::smem_u32(as)), db = tc::sw64_desc(tc::smem_u32(bs));
             const uint32_t first = (kc % kGroupChunks) == 0 ? 0u : 1u;
+            // one MMA per A digit against the stacked R digits 0 .. 7 - a (N = 16 (8 - a))
 #pragma unroll
-            for (int a = 0; a < oz::kLevels; ++a)
+            for (int kk = 0; kk < kK; kk += 16)
 #pragma unroll
-              for (int kk = 0; kk < kK; kk += 16)
-#pragma unroll
-                for (int L = a; L < oz::kLevels; ++L)
-                  tc::mma_f16(tmem + (uint32_t)(L * kTB), da + (uint64_t)((a * kTAPanel + kk * 2) >> 4),
-                              db + (uint64_t)(((L - a) * kTBPanel + kk * 2) >> 4), idesc,
-                              (a == 0 && kk == 0) ? first : 1u);
+              for (int a = 0; a < oz::kLevels; ++a)
+                tc::mma_f16(tmem + (uint32_t)(a * kTB), da + (uint64_t)((a * kTAPanel + kk * 2) >> 4),
+                            db + (uint64_t)((kk * 2) >> 4), tc::idesc(tc::F16, kM, kTB * (oz::kLevels - a)),
+                            (a == 0 && kk == 0) ? first : 1u);
             tc::mma_commit(&mma_bar);
           }
           const bool ok = tc::mbar_wait(&mma_bar, commits & 1u);
