@@ -4,8 +4,10 @@
 // sketch; R_s is normalised to a positive diagonal (rows flipped) and
 // promoted to FP64 (Algorithm 2 step 6).
 //
-// One CTA of 1024 threads walks the columns; the working copy of Y stays in
-// global memory (L2-resident: at most 1024 x 512 words).  Output: R_s
+// Sketches of up to 1024 rows take the blocked form (panel kernel + trailing
+// updates, below); larger ones, and the batched path, one CTA of 1024 threads
+// that walks the columns with the working copy of Y in global memory
+// (L2-resident).  Output: R_s
 // column-major (n x n), its transpose padded to a row stride npad (for the
 // TRSM's uniform row loads, zeros in the padding) and 1/diag(R_s).
 #include <type_traits>
@@ -102,10 +104,228 @@ __global__ void __launch_bounds__(kSqrThreads) k_sketch_qr(int n, int s, const d
   sketch_qr_block<T>(n, s, Y, W, Rs, RsT, rinv);
 }
 
+
+// ---------------------------------------------------------------------------
+// Blocked form for s <= 1024 (the single-CTA kernel above keeps the larger
+// sketches): panels of kQB columns are factored by one CTA in shared memory,
+// and the columns right of a panel are updated by one warp per column (the
+// column in registers), so the O(s n^2) reflector applications are spread
+// over the GPU instead of one SM (FP64 issues at 1/64 of the FP32 rate here).
+// The working copy holds LAPACK's geqrf layout: beta_j = +-||x|| on the
+// diagonal, the reflector v (v_j = 1 implicit) below it; tau = 2 / ||v||^2
+// is recomputed from v where it is needed, so no extra storage is used.
+constexpr int kQB = 16;          // panel width
+constexpr int kQMaxS = 1024;     // rows handled by the blocked form
+constexpr int kQPanelThreads = 512;
+
+__global__ void k_sqr_copy(int64_t total, const double* __restrict__ Y, void* __restrict__ Wk, int fp64,
+                           const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    if (fp64) static_cast<double*>(Wk)[e] = Y[e];
+    else static_cast<float*>(Wk)[e] = (float)Y[e];
+  }
+}
+
+// Block-wide reduction of two values (sum or max), 512 threads.
+template <typename T, bool kMax>
+__device__ __forceinline__ void block_reduce2(T& a, T& b, T* red /* >= 2 * 16 */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T ta = __shfl_xor_sync(0xffffffffu, a, o), tb = __shfl_xor_sync(0xffffffffu, b, o);
+    if (kMax) { a = max(a, ta); b = max(b, tb); }
+    else { a += ta; b += tb; }
+  }
+  if (lane == 0) { red[warp] = a; red[16 + warp] = b; }
+  __syncthreads();
+  a = red[0];
+  b = red[16];
+  for (int w = 1; w < nw; ++w) {
+    if (kMax) { a = max(a, red[w]); b = max(b, red[16 + w]); }
+    else { a += red[w]; b += red[16 + w]; }
+  }
+  __syncthreads();
+}
+
+// Panel [c0, c1) of the s x n working copy (column-major, ld s), rows c0 .. s-1.
+template <typename T>
+__global__ void __launch_bounds__(kQPanelThreads) k_sqr_panel(int s, int c0, int c1, T* __restrict__ Wk,
+                                                              const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  extern __shared__ unsigned char sqr_smem[];
+  T* P = reinterpret_cast<T*>(sqr_smem);   // [kQB][rows]
+  __shared__ T red[32];
+  __shared__ T sh_beta, sh_scale, sh_tau;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int rows = s - c0, b = c1 - c0;
+  for (int e = tid; e < b * rows; e += blockDim.x) {
+    const int c = e / rows, i = e % rows;
+    P[c * rows + i] = Wk[(int64_t)(c0 + c) * s + c0 + i];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < b; ++jj) {
+    T* x = P + jj * rows;
+    // scaled 2-norm of x[jj..]: max first, then sums of squares with and without x[jj]
+    T amax = T(0), dummy = T(0);
+    for (int i = jj + tid; i < rows; i += blockDim.x) amax = max(amax, (T)fabs(x[i]));
+    block_reduce2<T, true>(amax, dummy, red);
+    T ss = T(0), tail = T(0);
+    if (amax > T(0)) {
+      const T inv = T(1) / amax;
+      for (int i = jj + tid; i < rows; i += blockDim.x) {
+        const T v = x[i] * inv;
+        ss = fma(v, v, ss);
+        if (i > jj) tail = fma(v, v, tail);
+      }
+    }
+    block_reduce2<T, false>(ss, tail, red);
+    if (tid == 0) {
+      const T x0 = x[jj];
+      const T nrm = amax * sqrt(ss);
+      const T beta = x0 >= T(0) ? -nrm : nrm;
+      if (nrm > T(0)) {
+        const T d = x0 - beta;   // |d| = |x0| + nrm: no cancellation
+        const T r = amax / d;
+        sh_scale = T(1) / d;
+        sh_tau = T(2) / (T(1) + tail * r * r);   // 2 / ||v||^2, v = (1, x[jj+1..] / d)
+      } else {
+        sh_scale = T(0);
+        sh_tau = T(0);
+      }
+      sh_beta = beta;
+    }
+    __syncthreads();
+    const T scale = sh_scale, tau = sh_tau;
+    for (int i = jj + 1 + tid; i < rows; i += blockDim.x) x[i] *= scale;
+    __syncthreads();
+    if (tid == 0) x[jj] = sh_beta;
+    // apply H = I - tau v v^T to panel columns jj+1 .. b-1 (one warp per column)
+    for (int c = jj + 1 + warp; c < b; c += nw) {
+      T* y = P + c * rows;
+      T d = lane == 0 ? y[jj] : T(0);
+      for (int i = jj + 1 + lane; i < rows; i += 32) d = fma(x[i], y[i], d);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      const T f = tau * d;
+      if (lane == 0) y[jj] -= f;
+      for (int i = jj + 1 + lane; i < rows; i += 32) y[i] = fma(-f, x[i], y[i]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < b * rows; e += blockDim.x) {
+    const int c = e / rows, i = e % rows;
+    Wk[(int64_t)(c0 + c) * s + c0 + i] = P[c * rows + i];
+  }
+}
+
+// Columns c >= c1: apply the panel's reflectors j = c0 .. c1-1 in order
+// (one warp per column; lane l holds rows c0 + l + 32 t, t < kR, with
+// 32 kR >= s - c0).
+template <typename T, int kR>
+__global__ void __launch_bounds__(32) k_sqr_update(int s, int c0, int c1, T* __restrict__ Wk, const Ctl* ctl,
+                                                   int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int lane = threadIdx.x;
+  const int c = c1 + blockIdx.x;
+  T* y = Wk + (int64_t)c * s;
+  const T* V = Wk;
+  T xr[kR];
+#pragma unroll
+  for (int t = 0; t < kR; ++t) {
+    const int i = c0 + lane + 32 * t;
+    xr[t] = i < s ? y[i] : T(0);
+  }
+  for (int j = c0; j < c1; ++j) {
+    const T* v = V + (int64_t)j * s;
+    T d = T(0), vv = T(0);
+#pragma unroll
+    for (int t = 0; t < kR; ++t) {
+      const int i = c0 + lane + 32 * t;
+      if (i > j && i < s) {
+        const T vi = v[i];
+        d = fma(vi, xr[t], d);
+        vv = fma(vi, vi, vv);
+      } else if (i == j) {
+        d += xr[t];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      d += __shfl_xor_sync(0xffffffffu, d, o);
+      vv += __shfl_xor_sync(0xffffffffu, vv, o);
+    }
+    const T f = (T(2) / (T(1) + vv)) * d;
+#pragma unroll
+    for (int t = 0; t < kR; ++t) {
+      const int i = c0 + lane + 32 * t;
+      if (i > j && i < s) xr[t] = fma(-f, v[i], xr[t]);
+      else if (i == j) xr[t] -= f;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kR; ++t) {
+    const int i = c0 + lane + 32 * t;
+    if (i < s) y[i] = xr[t];
+  }
+}
+
+// R_s (column-major), its padded transpose and 1/diag from the factored
+// working copy, rows flipped to a positive diagonal.
+template <typename T>
+__global__ void k_sqr_out(int n, int s, const T* __restrict__ Wk, double* __restrict__ Rs, double* __restrict__ RsT,
+                          double* __restrict__ rinv, const Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int npad = padded(n);
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (int64_t)npad * n) {
+    const int r = (int)(e / npad), c = (int)(e % npad);
+    const double beta = (double)Wk[(int64_t)r * s + r];
+    const double sg = beta < 0.0 ? -1.0 : 1.0;
+    double v = 0.0;
+    if (c < n) {
+      if (r < c) v = (double)Wk[(int64_t)c * s + r] * sg;
+      else if (r == c) v = fabs(beta);
+    }
+    RsT[(int64_t)r * npad + c] = v;
+    if (c < n) Rs[(int64_t)c * n + r] = v;
+  }
+  if (e < npad) rinv[e] = e < n ? 1.0 / fabs((double)Wk[e * s + e]) : 0.0;
+}
+
+template <typename T>
+void launch_sqr_blocked(int n, int s, const double* Y, T* Wk, double* Rs, double* RsT, double* rinv, Ctl* ctl,
+                        int level, cudaStream_t st) {
+  const int64_t total = (int64_t)s * n;
+  k_sqr_copy<<<(unsigned)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024), 256, 0, st>>>(
+      total, Y, Wk, std::is_same<T, double>::value ? 1 : 0, ctl, level);
+  cudaFuncSetAttribute(k_sqr_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(sizeof(T) * (size_t)kQB * (size_t)kQMaxS));
+  for (int c0 = 0; c0 < n; c0 += kQB) {
+    const int c1 = c0 + kQB < n ? c0 + kQB : n;
+    const size_t smem = sizeof(T) * (size_t)kQB * (size_t)(s - c0);
+    k_sqr_panel<T><<<1, kQPanelThreads, smem, st>>>(s, c0, c1, Wk, ctl, level);
+    if (c1 < n) {
+      const int rows = s - c0;
+      const unsigned g = (unsigned)(n - c1);
+      if (rows <= 256) k_sqr_update<T, 8><<<g, 32, 0, st>>>(s, c0, c1, Wk, ctl, level);
+      else if (rows <= 512) k_sqr_update<T, 16><<<g, 32, 0, st>>>(s, c0, c1, Wk, ctl, level);
+      else k_sqr_update<T, 32><<<g, 32, 0, st>>>(s, c0, c1, Wk, ctl, level);
+    }
+  }
+  const int64_t tot = (int64_t)padded(n) * n;
+  k_sqr_out<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, s, Wk, Rs, RsT, rinv, ctl, level);
+}
+
 size_t sqr_workspace_bytes(int n, int s) { return (size_t)n * (size_t)s * sizeof(double); }
 
 void launch_sketch_qr(int prec, int n, int s, const double* Y, void* work, double* Rs, double* RsT, double* rinv,
                       Ctl* ctl, int level, cudaStream_t st) {
+  if (s <= kQMaxS) {
+    if (prec == P_FP64) launch_sqr_blocked<double>(n, s, Y, (double*)work, Rs, RsT, rinv, ctl, level, st);
+    else launch_sqr_blocked<float>(n, s, Y, (float*)work, Rs, RsT, rinv, ctl, level, st);
+    return;
+  }
   if (prec == P_FP64)
     k_sketch_qr<double><<<1, kSqrThreads, 0, st>>>(n, s, Y, (double*)work, Rs, RsT, rinv, ctl, level);
   else

@@ -269,7 +269,63 @@ __global__ void __launch_bounds__(1024) k_chol(int n, double* __restrict__ G, Ct
   if (!chol_block(n, G) && threadIdx.x == 0) raise_level_status(ctl, ST_BREAKDOWN);
 }
 
+// The same elimination with the upper triangle of G held in shared memory
+// (n <= kCholSmemN); the finished row k of R_c goes straight to G.
+constexpr int kCholSmemN = 160;
+
+__global__ void __launch_bounds__(1024) k_chol_smem(int n, double* __restrict__ G, Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  extern __shared__ double S[];   // S[j n + i] = G[i][j], i <= j
+  __shared__ double piv;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t e = tid; e < nn; e += blockDim.x) S[e] = G[e];
+  __syncthreads();
+  bool ok = true;
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      const double d = S[(int64_t)k * n + k];
+      piv = (d > 0.0 && isfinite(d)) ? sqrt(d) : -1.0;
+    }
+    __syncthreads();
+    const double p = piv;
+    if (!(p > 0.0)) {
+      ok = false;
+      break;
+    }
+    const double ip = 1.0 / p;
+    for (int j = k + 1 + tid; j < n; j += blockDim.x) {
+      const double r = S[(int64_t)j * n + k] * ip;
+      S[(int64_t)j * n + k] = r;
+      G[(int64_t)j * n + k] = r;
+    }
+    if (tid == 0) G[(int64_t)k * n + k] = p;
+    __syncthreads();
+    for (int j = k + 1 + ty; j < n; j += 32) {
+      const double rkj = S[(int64_t)j * n + k];
+      for (int i = k + 1 + tx; i <= j; i += 32)
+        S[(int64_t)j * n + i] = fma(-S[(int64_t)i * n + k], rkj, S[(int64_t)j * n + i]);
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) raise_level_status(ctl, ST_BREAKDOWN);
+    return;
+  }
+  for (int64_t e = tid; e < nn; e += blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i > j) G[e] = 0.0;
+  }
+}
+
 void launch_chol(int n, double* G, Ctl* ctl, int level, cudaStream_t st) {
+  if (n <= kCholSmemN) {
+    const size_t smem = sizeof(double) * (size_t)n * n;
+    cudaFuncSetAttribute(k_chol_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(double) * kCholSmemN * kCholSmemN));
+    k_chol_smem<<<1, 1024, smem, st>>>(n, G, ctl, level);
+    return;
+  }
   k_chol<<<1, 1024, 0, st>>>(n, G, ctl, level);
 }
 
@@ -296,16 +352,58 @@ __device__ __forceinline__ void trinv_column(int n, const double* __restrict__ R
   }
 }
 
-__global__ void k_trinv(int n, const double* __restrict__ Rc, double* __restrict__ XT, const Ctl* ctl, int level) {
+// Single-problem form: one warp per column j, which solves R_c x = e_j by a
+// backward column sweep (x_i = b_i / R_ii, then b_k -= R_ki x_i for k < i);
+// lane l holds rows l + 32 t (t < NT, 32 NT >= n), so every step is one
+// broadcast and NT independent FMAs instead of a serial dot product.
+template <int NT>
+__global__ void __launch_bounds__(128) k_trinv(int n, const double* __restrict__ Rc, double* __restrict__ XT,
+                                               const Ctl* ctl, int level) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double rdiag[32 * NT];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rdiag[i] = 1.0 / Rc[(int64_t)i * n + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int npad = (n + kPad - 1) / kPad * kPad;
-  if (j < npad) trinv_column(n, Rc, XT, j);
+  if (j >= npad) return;
+  if (j >= n) {
+    for (int i = lane; i < n; i += 32) XT[(int64_t)i * npad + j] = 0.0;
+    return;
+  }
+  for (int i = j + 1 + lane; i < n; i += 32) XT[(int64_t)i * npad + j] = 0.0;
+  double b[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) b[t] = (lane + 32 * t == j) ? 1.0 : 0.0;
+  for (int i = j; i >= 0; --i) {
+    const int ti = i >> 5, li = i & 31;
+    double bi = 0.0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+      if (t == ti) bi = b[t];
+    const double xi = __shfl_sync(0xffffffffu, bi, li) * rdiag[i];
+    const double* col = Rc + (int64_t)i * n;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int k = lane + 32 * t;
+      if (k < i) b[t] = fma(-col[k], xi, b[t]);
+      else if (k == i) b[t] = xi;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int k = lane + 32 * t;
+    if (k <= j) XT[(int64_t)k * npad + j] = b[t];
+  }
 }
 
 void launch_trinv(int n, const double* Rc, double* RcinvT, const Ctl* ctl, int level, cudaStream_t st) {
   const int npad = padded(n);
-  k_trinv<<<(npad + 63) / 64, 64, 0, st>>>(n, Rc, RcinvT, ctl, level);
+  const unsigned grid = (unsigned)((npad + 3) / 4);
+  if (n <= 64) k_trinv<2><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level);
+  else if (n <= 128) k_trinv<4><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level);
+  else if (n <= 256) k_trinv<8><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level);
+  else k_trinv<16><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level);
 }
 
 // R = R_c R_s (Algorithm 2 step 9), upper x upper; R col-major with ld ldr,
