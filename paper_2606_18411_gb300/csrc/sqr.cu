@@ -127,89 +127,106 @@ __global__ void k_sqr_copy(int64_t total, const double* __restrict__ Y, void* __
   }
 }
 
-// Block-wide reduction of two values (sum or max), 512 threads.
-template <typename T, bool kMax>
-__device__ __forceinline__ void block_reduce2(T& a, T& b, T* red /* >= 2 * 16 */) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Warp-wide sum and max.
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const T ta = __shfl_xor_sync(0xffffffffu, a, o), tb = __shfl_xor_sync(0xffffffffu, b, o);
-    if (kMax) { a = max(a, ta); b = max(b, tb); }
-    else { a += ta; b += tb; }
-  }
-  if (lane == 0) { red[warp] = a; red[16 + warp] = b; }
-  __syncthreads();
-  a = red[0];
-  b = red[16];
-  for (int w = 1; w < nw; ++w) {
-    if (kMax) { a = max(a, red[w]); b = max(b, red[16 + w]); }
-    else { a += red[w]; b += red[16 + w]; }
-  }
-  __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T wmax(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
-// Panel [c0, c1) of the s x n working copy (column-major, ld s), rows c0 .. s-1.
+// Householder reflector of x[jj..rows) by one warp (the column's owner):
+// beta = -sign(x0) ||x||, v = (1, x[jj+1..] / (x0 - beta)), tau = 2 / ||v||^2.
+// x[jj] <- beta, x[jj+1..] <- v[1..]; returns tau (0 for a zero column).
+// The norm is scaled by the column maximum, so FP32 neither overflows nor
+// underflows.
+template <typename T>
+__device__ __forceinline__ T house_warp(T* x, int jj, int rows, int lane) {
+  T amax = T(0);
+  for (int i = jj + lane; i < rows; i += 32) amax = max(amax, (T)fabs(x[i]));
+  amax = wmax(amax);
+  if (!(amax > T(0))) return T(0);
+  const T inv = T(1) / amax;
+  T t0 = T(0), t1 = T(0);
+  int i = jj + 1 + lane;
+  for (; i + 32 < rows; i += 64) {
+    const T a = x[i] * inv, b = x[i + 32] * inv;
+    t0 = fma(a, a, t0);
+    t1 = fma(b, b, t1);
+  }
+  if (i < rows) {
+    const T a = x[i] * inv;
+    t0 = fma(a, a, t0);
+  }
+  const T tail = wsum(t0 + t1);   // sum of (x_i / amax)^2 over i > jj
+  const T x0 = x[jj], y0 = x0 * inv;
+  const T nrm = amax * sqrt(fma(y0, y0, tail));
+  const T beta = x0 >= T(0) ? -nrm : nrm;
+  const T d = x0 - beta;   // |d| = |x0| + nrm: no cancellation
+  const T scale = T(1) / d;
+  const T r = amax * scale;
+  const T tau = T(2) / fma(tail * r, r, T(1));
+  __syncwarp();
+  for (int k = jj + 1 + lane; k < rows; k += 32) x[k] *= scale;
+  if (lane == 0) x[jj] = beta;
+  __syncwarp();
+  return tau;
+}
+
+// y <- (I - tau v v^T) y over rows jj..rows-1, v = (1, x[jj+1..]), one warp.
+template <typename T>
+__device__ __forceinline__ void house_apply_warp(const T* x, T* y, T tau, int jj, int rows, int lane) {
+  T d0 = lane == 0 ? y[jj] : T(0), d1 = T(0);
+  int i = jj + 1 + lane;
+  for (; i + 32 < rows; i += 64) {
+    d0 = fma(x[i], y[i], d0);
+    d1 = fma(x[i + 32], y[i + 32], d1);
+  }
+  if (i < rows) d0 = fma(x[i], y[i], d0);
+  const T f = tau * wsum(d0 + d1);
+  if (lane == 0) y[jj] -= f;
+  for (int k = jj + 1 + lane; k < rows; k += 32) y[k] = fma(-f, x[k], y[k]);
+  __syncwarp();
+}
+
+// Panel [c0, c1) of the s x n working copy (column-major, ld s), rows c0 .. s-1,
+// factored in shared memory; warp w owns panel column w.  Step jj: the owner
+// of column jj has already applied reflectors 0 .. jj-1 to it and forms
+// reflector jj; after one barrier every warp right of it applies it to its own
+// column, the owner of jj+1 first and then straight on to its reflector.
 template <typename T>
 __global__ void __launch_bounds__(kQPanelThreads) k_sqr_panel(int s, int c0, int c1, T* __restrict__ Wk,
                                                               const Ctl* ctl, int level) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ unsigned char sqr_smem[];
   T* P = reinterpret_cast<T*>(sqr_smem);   // [kQB][rows]
-  __shared__ T red[32];
-  __shared__ T sh_beta, sh_scale, sh_tau;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  __shared__ T taus[kQB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = s - c0, b = c1 - c0;
   for (int e = tid; e < b * rows; e += blockDim.x) {
     const int c = e / rows, i = e % rows;
     P[c * rows + i] = Wk[(int64_t)(c0 + c) * s + c0 + i];
   }
   __syncthreads();
+  if (warp == 0) {
+    const T t = house_warp(P, 0, rows, lane);
+    if (lane == 0) taus[0] = t;
+  }
+  __syncthreads();
   for (int jj = 0; jj < b; ++jj) {
-    T* x = P + jj * rows;
-    // scaled 2-norm of x[jj..]: max first, then sums of squares with and without x[jj]
-    T amax = T(0), dummy = T(0);
-    for (int i = jj + tid; i < rows; i += blockDim.x) amax = max(amax, (T)fabs(x[i]));
-    block_reduce2<T, true>(amax, dummy, red);
-    T ss = T(0), tail = T(0);
-    if (amax > T(0)) {
-      const T inv = T(1) / amax;
-      for (int i = jj + tid; i < rows; i += blockDim.x) {
-        const T v = x[i] * inv;
-        ss = fma(v, v, ss);
-        if (i > jj) tail = fma(v, v, tail);
+    if (warp > jj && warp < b) {
+      T* y = P + warp * rows;
+      house_apply_warp(P + jj * rows, y, taus[jj], jj, rows, lane);
+      if (warp == jj + 1) {
+        const T t = house_warp(y, jj + 1, rows, lane);
+        if (lane == 0) taus[jj + 1] = t;
       }
-    }
-    block_reduce2<T, false>(ss, tail, red);
-    if (tid == 0) {
-      const T x0 = x[jj];
-      const T nrm = amax * sqrt(ss);
-      const T beta = x0 >= T(0) ? -nrm : nrm;
-      if (nrm > T(0)) {
-        const T d = x0 - beta;   // |d| = |x0| + nrm: no cancellation
-        const T r = amax / d;
-        sh_scale = T(1) / d;
-        sh_tau = T(2) / (T(1) + tail * r * r);   // 2 / ||v||^2, v = (1, x[jj+1..] / d)
-      } else {
-        sh_scale = T(0);
-        sh_tau = T(0);
-      }
-      sh_beta = beta;
-    }
-    __syncthreads();
-    const T scale = sh_scale, tau = sh_tau;
-    for (int i = jj + 1 + tid; i < rows; i += blockDim.x) x[i] *= scale;
-    __syncthreads();
-    if (tid == 0) x[jj] = sh_beta;
-    // apply H = I - tau v v^T to panel columns jj+1 .. b-1 (one warp per column)
-    for (int c = jj + 1 + warp; c < b; c += nw) {
-      T* y = P + c * rows;
-      T d = lane == 0 ? y[jj] : T(0);
-      for (int i = jj + 1 + lane; i < rows; i += 32) d = fma(x[i], y[i], d);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      const T f = tau * d;
-      if (lane == 0) y[jj] -= f;
-      for (int i = jj + 1 + lane; i < rows; i += 32) y[i] = fma(-f, x[i], y[i]);
     }
     __syncthreads();
   }
@@ -238,24 +255,20 @@ __global__ void __launch_bounds__(32) k_sqr_update(int s, int c0, int c1, T* __r
   }
   for (int j = c0; j < c1; ++j) {
     const T* v = V + (int64_t)j * s;
-    T d = T(0), vv = T(0);
+    T d[2] = {T(0), T(0)}, vv[2] = {T(0), T(0)};
 #pragma unroll
     for (int t = 0; t < kR; ++t) {
       const int i = c0 + lane + 32 * t;
       if (i > j && i < s) {
         const T vi = v[i];
-        d = fma(vi, xr[t], d);
-        vv = fma(vi, vi, vv);
+        d[t & 1] = fma(vi, xr[t], d[t & 1]);
+        vv[t & 1] = fma(vi, vi, vv[t & 1]);
       } else if (i == j) {
-        d += xr[t];
+        d[t & 1] += xr[t];
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      d += __shfl_xor_sync(0xffffffffu, d, o);
-      vv += __shfl_xor_sync(0xffffffffu, vv, o);
-    }
-    const T f = (T(2) / (T(1) + vv)) * d;
+    const T dd = wsum(d[0] + d[1]), vs = wsum(vv[0] + vv[1]);
+    const T f = (T(2) / (T(1) + vs)) * dd;
 #pragma unroll
     for (int t = 0; t < kR; ++t) {
       const int i = c0 + lane + 32 * t;
