@@ -302,7 +302,9 @@ int mrcqr_mlp_train_step(int batch, const float* X, const int32_t* y, const floa
  * (0 before any). */
 int mrcqr_last_sketch_variant(void);
 
-/* Number of kernels this library has launched in this process. */
+/* Number of kernels this library has launched from the host in this process
+ * (every <<<...>>> launch site counts itself; replaying a captured CUDA graph
+ * runs its kernels without passing through the launch sites again). */
 uint64_t mrcqr_launch_count(void);
 
 /* Name of a profiling stage id (sketch, trsm, syrk, ...). */

@@ -110,8 +110,8 @@ __global__ void k_write_stats(const Ctl* ctl, mrcqr_stats_t* out) {
 }
 
 // Instrumentation: a host-side count of kernel launches and, between
-// mrcqr_profile_begin/end, a CUDA-event pair around every launch.
-std::atomic<uint64_t> g_launches{0};
+// mrcqr_profile_begin/end, a CUDA-event pair around every launch group.
+std::atomic<uint64_t> g_kernels{0};
 
 struct ProfRec {
   int stage, level;
@@ -147,7 +147,6 @@ void launch(int stage, int level, cudaStream_t st, F&& f) {
   } else {
     f();
   }
-  g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
 enum Stage {
@@ -300,6 +299,8 @@ int finish(cudaStream_t st) {
 
 }  // namespace
 
+void mrcqr::note_launch() { g_kernels.fetch_add(1, std::memory_order_relaxed); }
+
 extern "C" {
 
 int mrcqr_version(void) { return kVersion; }
@@ -350,7 +351,7 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
   Ctl* ctl = at<Ctl>(ws, p.off_ctl);
   uint32_t* idx = at<uint32_t>(ws, p.off_idx);
   double* tab = at<double>(ws, p.off_tab);
-  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, nlevels, lv[0], lv[1], lv[2], lv[3], tol); });
+  launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, nlevels, lv[0], lv[1], lv[2], lv[3], tol); } });
   launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, s, seed, idx, ctl, st); });
   launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, at<float>(ws, p.off_tabf), st); });
   for (int L = 0; L < nlevels; ++L) {
@@ -367,9 +368,9 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
     }
     enqueue_stage2(p, ws, A, lda, Q, ldq, R, ldr, check, ctl, L, st, fp64p);
   }
-  launch(SG_STATS, 0, st, [&] { k_write_stats<<<1, 1, 0, st>>>(ctl, slot); });
+  launch(SG_STATS, 0, st, [&] { { ::mrcqr::note_launch(); k_write_stats<<<1, 1, 0, st>>>(ctl, slot); } });
   if (opts && opts->stats_device)
-    launch(SG_STATS, 0, st, [&] { k_write_stats<<<1, 1, 0, st>>>(ctl, (mrcqr_stats_t*)opts->stats_device); });
+    launch(SG_STATS, 0, st, [&] { { ::mrcqr::note_launch(); k_write_stats<<<1, 1, 0, st>>>(ctl, (mrcqr_stats_t*)opts->stats_device); } });
   cudaFreeAsync(ws, st);
   return finish(st);
 }
@@ -432,7 +433,7 @@ int mrcqr_sketch_ex(int64_t m, int64_t n, const double* A, int64_t lda, int64_t 
   Ctl* ctl = at<Ctl>(ws, p.off_ctl);
   uint32_t* idx = at<uint32_t>(ws, p.off_idx);
   double* tab = at<double>(ws, p.off_tab);
-  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, sketch_prec, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, sketch_prec, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
   launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, (int)s, seed, idx, ctl, st); });
   launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, at<float>(ws, p.off_tabf), st); });
   g_sketch_variant_last = enqueue_sketch(p, ws, sketch_prec, variant, 0, A, lda, seed, Y, ctl, 0, st);
@@ -453,7 +454,7 @@ int mrcqr_sketch_qr(int64_t n, int64_t s, const double* Y, int prec, double* Rs,
     return MRCQR_ERR_ALLOC;
   }
   Ctl* ctl = at<Ctl>(ws, o_ctl);
-  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, prec, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, prec, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
   launch(SG_SQR, 0, st, [&] {
     launch_sketch_qr(prec, (int)n, (int)s, Y, at<void>(ws, o_w), Rs, at<double>(ws, o_rst), at<double>(ws, o_rinv),
                      ctl, 0, st);
@@ -477,11 +478,11 @@ int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, con
     return MRCQR_ERR_ALLOC;
   }
   Ctl* ctl = at<Ctl>(ws, p.off_ctl);
-  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
   cudaMemcpyAsync(at<double>(ws, p.off_rs), Rs, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st);
   launch(SG_PREP, 0, st, [&] { launch_rs_prepare((int)n, Rs, at<double>(ws, p.off_rst), at<double>(ws, p.off_rinv), st); });
   enqueue_stage2(p, ws, A, lda, Q, ldq, R, ldr, 1, ctl, 0, st);
-  launch(SG_STATS, 0, st, [&] { k_write_stats<<<1, 1, 0, st>>>(ctl, slot); });
+  launch(SG_STATS, 0, st, [&] { { ::mrcqr::note_launch(); k_write_stats<<<1, 1, 0, st>>>(ctl, slot); } });
   cudaFreeAsync(ws, st);
   return finish(st);
 }
@@ -506,7 +507,7 @@ int mrcqr_trsm(int64_t m, int64_t n, const double* A, int64_t lda, const double*
   double* Rp = at<double>(ws, p.off_rs);
   double* RsT = at<double>(ws, p.off_rst);
   double* rinv = at<double>(ws, p.off_rinv);
-  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
   cudaMemcpy2DAsync(Rp, sizeof(double) * n, R, sizeof(double) * ldr, sizeof(double) * n, n, cudaMemcpyDeviceToDevice, st);
   launch(SG_PREP, 0, st, [&] { launch_rs_prepare((int)n, Rp, RsT, rinv, st); });
   if (fp64_products == 0)
@@ -535,7 +536,7 @@ int mrcqr_gram(int64_t m, int64_t n, const double* W, int64_t ldw, double* G, in
     return MRCQR_ERR_ALLOC;
   }
   Ctl* ctl = at<Ctl>(ws, p.off_ctl);
-  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
   if (fp64_products == 0) {
     launch(SG_SYRK, 0, st, [&] {
       launch_syrk_oz(m, (int)n, W, ldw, p.oz, at<uint32_t>(ws, p.off_colhi), at<long long>(ws, p.off_ozpart), G, ctl,
@@ -567,7 +568,7 @@ int mrcqr_finalize_q(int64_t m, int64_t n, double* Q, int64_t ldq, const double*
   }
   Ctl* ctl = at<Ctl>(ws, p.off_ctl);
   double* XT = at<double>(ws, p.off_xt);
-  launch(SG_INIT, 0, st, [&] { k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); });
+  launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
   launch(SG_PREP, 0, st, [&] { launch_upper_to_xt((int)n, X, ldx, XT, st); });
   if (fp64_products == 1)
     launch(SG_FINALIZE, 0, st, [&] { launch_finalize(m, (int)n, Q, ldq, XT, ctl, 0, st); });
@@ -580,7 +581,7 @@ int mrcqr_finalize_q(int64_t m, int64_t n, double* Q, int64_t ldq, const double*
   return finish(st);
 }
 
-uint64_t mrcqr_launch_count(void) { return g_launches.load(); }
+uint64_t mrcqr_launch_count(void) { return g_kernels.load(); }
 
 int mrcqr_last_sketch_variant(void) { return g_sketch_variant_last; }
 

@@ -6,6 +6,10 @@
 
 namespace mrcqr {
 
+// Counts one kernel launch (every launch site of the library calls it just
+// before its <<<...>>>); read through mrcqr_launch_count.
+void note_launch();
+
 // One problem of a grouped (batched) launch: caller buffers, shape, tuned
 // split sizes and its slice of the batch workspace.
 struct Prob {

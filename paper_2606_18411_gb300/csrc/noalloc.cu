@@ -95,7 +95,7 @@ extern "C" int mrcqr_sketch_qr_noalloc(int64_t n, int64_t s, const double* Y, in
   void* work = base + kCtlBytes;
   double* RsT = reinterpret_cast<double*>(base + kCtlBytes + kWorkBytes);
   double* rinv = reinterpret_cast<double*>(base + kCtlBytes + kWorkBytes + kRstBytes);
-  k_noalloc_init<<<1, 1, 0, st>>>(ctl, prec);
+  { ::mrcqr::note_launch(); k_noalloc_init<<<1, 1, 0, st>>>(ctl, prec); }
   mrcqr::launch_sketch_qr(prec, (int)n, (int)s, Y, work, Rs, RsT, rinv, ctl, 0, st);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -889,7 +889,7 @@ void launch_col_hi(int64_t m, int n, const double* X, int64_t ldx, uint32_t* col
   const int64_t max_y = (m + 4095) / 4096;
   if (ysplit > max_y) ysplit = (int)max_y;
   if (ysplit < 1) ysplit = 1;
-  k_col_hi<<<dim3(n, ysplit), 256, 0, st>>>(m, n, X, ldx, (m + ysplit - 1) / ysplit, colHi, ctl, level);
+  { ::mrcqr::note_launch(); k_col_hi<<<dim3(n, ysplit), 256, 0, st>>>(m, n, X, ldx, (m + ysplit - 1) / ysplit, colHi, ctl, level); }
 }
 }  // namespace
 
@@ -897,11 +897,11 @@ void launch_finalize_oz(int64_t m, int n, double* Q, int64_t ldq, const double* 
                         unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st) {
   const int npad = (n + 31) / 32 * 32;
   const int n64 = (n + kN - 1) / kN * kN;
-  k_oz_prep_x<<<n64, 512, 0, st>>>(n, npad, n64, XT, colE, Xs, ctl, level);
+  { ::mrcqr::note_launch(); k_oz_prep_x<<<n64, 512, 0, st>>>(n, npad, n64, XT, colE, Xs, ctl, level); }
   set_smem(k_finalize_oz);
   const int64_t nblocks = (m + kM - 1) / kM;
   const unsigned grid = (unsigned)(nblocks < num_sms() ? nblocks : num_sms());
-  k_finalize_oz<<<grid, kOzThreads, kSmem, st>>>(m, n, n64, Q, ldq, colE, Xs, ctl, level);
+  { ::mrcqr::note_launch(); k_finalize_oz<<<grid, kOzThreads, kSmem, st>>>(m, n, n64, Q, ldq, colE, Xs, ctl, level); }
 }
 
 SyrkOzPlan syrk_oz_plan(int64_t m, int n) {
@@ -928,10 +928,10 @@ void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOz
   launch_col_hi(m, n, W, ldw, colHi, ctl, level, st);
   set_smem(k_syrk_oz);
   const int nitems = P.ntiles * P.slabs;
-  k_syrk_oz<<<nitems < num_sms() ? nitems : num_sms(), kOzThreads, kSmem, st>>>(m, n, W, ldw, colHi, P, part, ctl,
-                                                                               level);
+  { ::mrcqr::note_launch(); k_syrk_oz<<<nitems < num_sms() ? nitems : num_sms(), kOzThreads, kSmem, st>>>(m, n, W, ldw, colHi, P, part, ctl,
+                                                                               level); }
   const int64_t nn = (int64_t)n * n;
-  k_syrk_oz_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, colHi, P, part, out, ctl, level);
+  { ::mrcqr::note_launch(); k_syrk_oz_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, colHi, P, part, out, ctl, level); }
 }
 
 SketchOzPlan sketch_oz_plan(int64_t m, int n, int s) {
@@ -952,10 +952,10 @@ void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, con
   launch_col_hi(m, n, A, lda, colHi, ctl, level, st);
   set_smem(k_sketch_oz);
   const int nitems = P.mblocks * P.ntiles * P.slabs;
-  k_sketch_oz<<<nitems < num_sms() ? nitems : num_sms(), kOzThreads, kSmem, st>>>(m, n, s, A, lda, colHi, idx, tab,
-                                                                                 seed_key(seed), P, part, ctl, level);
+  { ::mrcqr::note_launch(); k_sketch_oz<<<nitems < num_sms() ? nitems : num_sms(), kOzThreads, kSmem, st>>>(m, n, s, A, lda, colHi, idx, tab,
+                                                                                 seed_key(seed), P, part, ctl, level); }
   const int64_t total = (int64_t)s * n;
-  k_sketch_oz_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, colHi, idx, P, part, Y, ctl, level);
+  { ::mrcqr::note_launch(); k_sketch_oz_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, colHi, idx, P, part, Y, ctl, level); }
 }
 
 size_t trsm_oz_rd_bytes(int n) {
@@ -972,13 +972,13 @@ void launch_trsm_oz(int64_t m, int n, const double* A, int64_t lda, const double
   const int n16 = (n + kTB - 1) / kTB * kTB;
   int* colE = reinterpret_cast<int*>(colE_ws);
   int* eR = colE + n16;
-  k_oz_row_scale<<<(n + 7) / 8, 256, 0, st>>>(n, npad, RT, eR, ctl, level);
-  k_oz_prep_r<<<n16, 256, 0, st>>>(n, npad, nkc, RT, eR, colE, Rd, ctl, level);
+  { ::mrcqr::note_launch(); k_oz_row_scale<<<(n + 7) / 8, 256, 0, st>>>(n, npad, RT, eR, ctl, level); }
+  { ::mrcqr::note_launch(); k_oz_prep_r<<<n16, 256, 0, st>>>(n, npad, nkc, RT, eR, colE, Rd, ctl, level); }
   cudaFuncSetAttribute(k_trsm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
   const int64_t nblocks = (m + kM - 1) / kM;
   const int64_t slots = 2 * (int64_t)num_sms();
-  k_trsm_oz<<<(unsigned)(nblocks < slots ? nblocks : slots), kTThreads, kTSmem, st>>>(m, n, A, lda, RT, rinv, eR,
-                                                                                       colE, Rd, nkc, W, ldw, ctl, level);
+  { ::mrcqr::note_launch(); k_trsm_oz<<<(unsigned)(nblocks < slots ? nblocks : slots), kTThreads, kTSmem, st>>>(m, n, A, lda, RT, rinv, eR,
+                                                                                       colE, Rd, nkc, W, ldw, ctl, level); }
 }
 
 }  // namespace mrcqr

@@ -451,7 +451,7 @@ int selector_set(const float* params, const float* mu, const float* sd, const fl
 }
 
 void launch_features(const double* Rs, int n, int64_t m, float* out, const Ctl* ctl, int level, cudaStream_t st) {
-  k_features<<<1, kFeatThreads, 0, st>>>(Rs, n, m, out, ctl, level);
+  { ::mrcqr::note_launch(); k_features<<<1, kFeatThreads, 0, st>>>(Rs, n, m, out, ctl, level); }
 }
 
 bool launch_mlp_select(const float* feat, Ctl* ctl, cudaStream_t st) {
@@ -463,7 +463,7 @@ bool launch_mlp_select(const float* feat, Ctl* ctl, cudaStream_t st) {
     if (dev >= (int)g_sel.size() || !g_sel[dev].w) return false;
     S = Sel{g_sel[dev].w, g_sel[dev].aux, g_sel[dev].aux + 16, g_sel[dev].aux + 32};
   }
-  k_mlp_select<<<1, 64, 0, st>>>(S, feat, ctl);
+  { ::mrcqr::note_launch(); k_mlp_select<<<1, 64, 0, st>>>(S, feat, ctl); }
   return true;
 }
 
@@ -471,7 +471,7 @@ void launch_mlp_forward(const unsigned short* w, const float* mu, const float* s
                         const float* X, float* logits, int32_t* choice, cudaStream_t st) {
   const Sel S{w, mu, sd, costs};
   const int grid = batch < 152 * 16 ? batch : 152 * 16;
-  if (batch > 0) k_mlp_forward<<<grid, 64, 0, st>>>(S, batch, X, logits, choice);
+  if (batch > 0) { ::mrcqr::note_launch(); k_mlp_forward<<<grid, 64, 0, st>>>(S, batch, X, logits, choice); }
 }
 
 void launch_mlp_grad(const unsigned short* w, const float* mu, const float* sd, int batch, const float* X,
@@ -479,18 +479,18 @@ void launch_mlp_grad(const unsigned short* w, const float* mu, const float* sd, 
                      cudaStream_t st) {
   const Sel S{w, mu, sd, nullptr};
   const int per = (batch + nparts - 1) / nparts;
-  k_mlp_grad_partial<<<nparts, 64, 0, st>>>(S, batch, per, X, y, class_w, part, loss_part);
+  { ::mrcqr::note_launch(); k_mlp_grad_partial<<<nparts, 64, 0, st>>>(S, batch, per, X, y, class_w, part, loss_part); }
 }
 
 void launch_mlp_reduce_adamw(int nparts, const float* part, const float* loss_part, float* master, float* mom,
                              float* var, unsigned short* wbf16, float lr, float beta1, float beta2, float eps,
                              float wd, int step, int apply, float* grad_out, float* loss_out, cudaStream_t st) {
-  k_mlp_reduce_adamw<<<(kNParams + 255) / 256, 256, 0, st>>>(nparts, part, loss_part, master, mom, var, wbf16, lr,
-                                                             beta1, beta2, eps, wd, step, apply, grad_out, loss_out);
+  { ::mrcqr::note_launch(); k_mlp_reduce_adamw<<<(kNParams + 255) / 256, 256, 0, st>>>(nparts, part, loss_part, master, mom, var, wbf16, lr,
+                                                             beta1, beta2, eps, wd, step, apply, grad_out, loss_out); }
 }
 
 void launch_to_bf16(int n, const float* src, unsigned short* dst, cudaStream_t st) {
-  k_to_bf16<<<(n + 255) / 256, 256, 0, st>>>(n, src, dst);
+  { ::mrcqr::note_launch(); k_to_bf16<<<(n + 255) / 256, 256, 0, st>>>(n, src, dst); }
 }
 
 }  // namespace mrcqr

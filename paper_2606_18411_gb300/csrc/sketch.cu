@@ -89,7 +89,7 @@ void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ct
   while (P < s) P <<= 1;
   const size_t smem = sizeof(uint32_t) * (size_t)(s + H + P);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_sample<<<1, 1024, smem, st>>>(m, s, seed_key(seed), idx, ctl);
+  { ::mrcqr::note_launch(); k_sample<<<1, 1024, smem, st>>>(m, s, seed_key(seed), idx, ctl); }
 }
 
 // ---------------------------------------------------------------------------
@@ -105,7 +105,7 @@ __global__ void k_costab(int64_t m, double* __restrict__ tab, float* __restrict_
 
 void launch_costab(int64_t m, double* tab, float* tabf, cudaStream_t st) {
   const int64_t nq = m + 1;
-  k_costab<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(m, tab, tabf);
+  { ::mrcqr::note_launch(); k_costab<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(m, tab, tabf); }
 }
 
 // fl_p exactly as the tensor-core sketch computes it (integer RNE on the
@@ -124,7 +124,7 @@ __global__ void k_round(int prec, int64_t count, const double* __restrict__ x, d
 }
 
 void launch_round(int prec, int64_t count, const double* x, double* y, cudaStream_t st) {
-  k_round<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(prec, count, x, y);
+  { ::mrcqr::note_launch(); k_round<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(prec, count, x, y); }
 }
 
 __global__ void k_signs(int64_t m, uint2 key, double* __restrict__ out) {
@@ -133,7 +133,7 @@ __global__ void k_signs(int64_t m, uint2 key, double* __restrict__ out) {
 }
 
 void launch_signs(int64_t m, uint64_t seed, double* out, cudaStream_t st) {
-  k_signs<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, seed_key(seed), out);
+  { ::mrcqr::note_launch(); k_signs<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, seed_key(seed), out); }
 }
 
 // ---------------------------------------------------------------------------
@@ -291,10 +291,10 @@ int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m
   const int64_t rpc = rows_per_chunk(m, chunks);
   const uint2 key = seed_key(seed);
   switch (prec) {
-    case P_FP16: k_sketch_simt<P_FP16><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); break;
-    case P_BF16: k_sketch_simt<P_BF16><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); break;
-    case P_FP32: k_sketch_simt<P_FP32><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); break;
-    default: k_sketch_simt<P_FP64><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); break;
+    case P_FP16: { ::mrcqr::note_launch(); k_sketch_simt<P_FP16><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); } break;
+    case P_BF16: { ::mrcqr::note_launch(); k_sketch_simt<P_BF16><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); } break;
+    case P_FP32: { ::mrcqr::note_launch(); k_sketch_simt<P_FP32><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); } break;
+    default: { ::mrcqr::note_launch(); k_sketch_simt<P_FP64><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); } break;
   }
   return 1;
 }
@@ -328,7 +328,7 @@ void launch_sketch_reduce(int64_t m, int n, int s, int chunks, const double* Ypa
                           Ctl* ctl, int level, cudaStream_t st) {
   (void)m;
   const int64_t total = (int64_t)s * n;
-  k_sketch_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, chunks, Ypart, idx, Y, ctl, level);
+  { ::mrcqr::note_launch(); k_sketch_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, chunks, Ypart, idx, Y, ctl, level); }
 }
 
 // ---------------------------------------------------------------------------
@@ -403,7 +403,7 @@ __global__ void kg_sketch_reduce(Group g, int level) {
 }  // namespace
 
 void launch_g_init(const Group& g, cudaStream_t st) {
-  if (g.nitems) kg_init<<<(g.nitems + 127) / 128, 128, 0, st>>>(g);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_init<<<(g.nitems + 127) / 128, 128, 0, st>>>(g); }
 }
 static size_t g_sample_smem(int max_s) {
   int H = 1;
@@ -418,22 +418,22 @@ void prepare_g_kernels(int max_s) {
 }
 
 void launch_g_sample(const Group& g, int max_s, cudaStream_t st) {
-  if (g.nitems) kg_sample<<<gridS(g.nitems), 1024, g_sample_smem(max_s), st>>>(g);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_sample<<<gridS(g.nitems), 1024, g_sample_smem(max_s), st>>>(g); }
 }
 void launch_g_costab(const Group& g, cudaStream_t st) {
-  if (g.nitems) kg_costab<<<gridS(g.nitems), 256, 0, st>>>(g);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_costab<<<gridS(g.nitems), 256, 0, st>>>(g); }
 }
 void launch_g_sketch(const Group& g, int prec, int level, cudaStream_t st) {
   if (!g.nitems) return;
   switch (prec) {
-    case P_FP16: kg_sketch<P_FP16><<<gridS(g.nitems), 256, 0, st>>>(g, level); break;
-    case P_BF16: kg_sketch<P_BF16><<<gridS(g.nitems), 256, 0, st>>>(g, level); break;
-    case P_FP32: kg_sketch<P_FP32><<<gridS(g.nitems), 256, 0, st>>>(g, level); break;
-    default: kg_sketch<P_FP64><<<gridS(g.nitems), 256, 0, st>>>(g, level); break;
+    case P_FP16: { ::mrcqr::note_launch(); kg_sketch<P_FP16><<<gridS(g.nitems), 256, 0, st>>>(g, level); } break;
+    case P_BF16: { ::mrcqr::note_launch(); kg_sketch<P_BF16><<<gridS(g.nitems), 256, 0, st>>>(g, level); } break;
+    case P_FP32: { ::mrcqr::note_launch(); kg_sketch<P_FP32><<<gridS(g.nitems), 256, 0, st>>>(g, level); } break;
+    default: { ::mrcqr::note_launch(); kg_sketch<P_FP64><<<gridS(g.nitems), 256, 0, st>>>(g, level); } break;
   }
 }
 void launch_g_sketch_reduce(const Group& g, int level, cudaStream_t st) {
-  if (g.nitems) kg_sketch_reduce<<<gridS(g.nitems), 256, 0, st>>>(g, level);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_sketch_reduce<<<gridS(g.nitems), 256, 0, st>>>(g, level); }
 }
 
 }  // namespace mrcqr

@@ -389,8 +389,8 @@ bool launch_tc(const CUtensorMap& map, int64_t m, int n, int s, const uint32_t* 
   int64_t rpc = (m + chunks - 1) / chunks;
   rpc = (rpc + 63) / 64 * 64;
   const dim3 grid((s + kM * MT - 1) / (kM * MT), (n + kN - 1) / kN, chunks);
-  k_sketch_tc<PREC, MT><<<grid, kThreads, smem, st>>>(map, m, n, s, idx, tab, tabf, seed_key(seed), rpc, Ypart, ctl,
-                                                      level);
+  { ::mrcqr::note_launch(); k_sketch_tc<PREC, MT><<<grid, kThreads, smem, st>>>(map, m, n, s, idx, tab, tabf, seed_key(seed), rpc, Ypart, ctl,
+                                                      level); }
   return true;
 }
 

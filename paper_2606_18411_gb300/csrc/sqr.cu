@@ -310,24 +310,24 @@ template <typename T>
 void launch_sqr_blocked(int n, int s, const double* Y, T* Wk, double* Rs, double* RsT, double* rinv, Ctl* ctl,
                         int level, cudaStream_t st) {
   const int64_t total = (int64_t)s * n;
-  k_sqr_copy<<<(unsigned)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024), 256, 0, st>>>(
-      total, Y, Wk, std::is_same<T, double>::value ? 1 : 0, ctl, level);
+  { ::mrcqr::note_launch(); k_sqr_copy<<<(unsigned)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024), 256, 0, st>>>(
+      total, Y, Wk, std::is_same<T, double>::value ? 1 : 0, ctl, level); }
   cudaFuncSetAttribute(k_sqr_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(sizeof(T) * (size_t)kQB * (size_t)kQMaxS));
   for (int c0 = 0; c0 < n; c0 += kQB) {
     const int c1 = c0 + kQB < n ? c0 + kQB : n;
     const size_t smem = sizeof(T) * (size_t)kQB * (size_t)(s - c0);
-    k_sqr_panel<T><<<1, kQPanelThreads, smem, st>>>(s, c0, c1, Wk, ctl, level);
+    { ::mrcqr::note_launch(); k_sqr_panel<T><<<1, kQPanelThreads, smem, st>>>(s, c0, c1, Wk, ctl, level); }
     if (c1 < n) {
       const int rows = s - c0;
       const unsigned g = (unsigned)(n - c1);
-      if (rows <= 256) k_sqr_update<T, 8><<<g, 32, 0, st>>>(s, c0, c1, Wk, ctl, level);
-      else if (rows <= 512) k_sqr_update<T, 16><<<g, 32, 0, st>>>(s, c0, c1, Wk, ctl, level);
-      else k_sqr_update<T, 32><<<g, 32, 0, st>>>(s, c0, c1, Wk, ctl, level);
+      if (rows <= 256) { ::mrcqr::note_launch(); k_sqr_update<T, 8><<<g, 32, 0, st>>>(s, c0, c1, Wk, ctl, level); }
+      else if (rows <= 512) { ::mrcqr::note_launch(); k_sqr_update<T, 16><<<g, 32, 0, st>>>(s, c0, c1, Wk, ctl, level); }
+      else { ::mrcqr::note_launch(); k_sqr_update<T, 32><<<g, 32, 0, st>>>(s, c0, c1, Wk, ctl, level); }
     }
   }
   const int64_t tot = (int64_t)padded(n) * n;
-  k_sqr_out<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, s, Wk, Rs, RsT, rinv, ctl, level);
+  { ::mrcqr::note_launch(); k_sqr_out<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, s, Wk, Rs, RsT, rinv, ctl, level); }
 }
 
 size_t sqr_workspace_bytes(int n, int s) { return (size_t)n * (size_t)s * sizeof(double); }
@@ -340,9 +340,9 @@ void launch_sketch_qr(int prec, int n, int s, const double* Y, void* work, doubl
     return;
   }
   if (prec == P_FP64)
-    k_sketch_qr<double><<<1, kSqrThreads, 0, st>>>(n, s, Y, (double*)work, Rs, RsT, rinv, ctl, level);
+    { ::mrcqr::note_launch(); k_sketch_qr<double><<<1, kSqrThreads, 0, st>>>(n, s, Y, (double*)work, Rs, RsT, rinv, ctl, level); }
   else
-    k_sketch_qr<float><<<1, kSqrThreads, 0, st>>>(n, s, Y, (float*)work, Rs, RsT, rinv, ctl, level);
+    { ::mrcqr::note_launch(); k_sketch_qr<float><<<1, kSqrThreads, 0, st>>>(n, s, Y, (float*)work, Rs, RsT, rinv, ctl, level); }
 }
 
 }  // namespace mrcqr
@@ -364,7 +364,7 @@ __global__ void k_rs_prepare(int n, const double* __restrict__ Rs, double* __res
 
 void launch_rs_prepare(int n, const double* Rs, double* RsT, double* rinv, cudaStream_t st) {
   const int64_t tot = (int64_t)n * padded(n);
-  k_rs_prepare<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, Rs, RsT, rinv);
+  { ::mrcqr::note_launch(); k_rs_prepare<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, Rs, RsT, rinv); }
 }
 
 // Grouped sketch QR: one CTA per problem.
@@ -384,8 +384,8 @@ __global__ void __launch_bounds__(kSqrThreads) kg_sketch_qr(Group g, int level) 
 void launch_g_sketch_qr(const Group& g, bool fp64, int level, cudaStream_t st) {
   if (!g.nitems) return;
   const unsigned grid = (unsigned)(g.nitems < 152 * 2 ? g.nitems : 152 * 2);
-  if (fp64) kg_sketch_qr<double><<<grid, kSqrThreads, 0, st>>>(g, level);
-  else kg_sketch_qr<float><<<grid, kSqrThreads, 0, st>>>(g, level);
+  if (fp64) { ::mrcqr::note_launch(); kg_sketch_qr<double><<<grid, kSqrThreads, 0, st>>>(g, level); }
+  else { ::mrcqr::note_launch(); kg_sketch_qr<float><<<grid, kSqrThreads, 0, st>>>(g, level); }
 }
 
 }  // namespace mrcqr

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(128) k_trsm(int64_t m, int n, const double* __
 
 void launch_trsm(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv, double* W,
                  int64_t ldw, const Ctl* ctl, int level, cudaStream_t st) {
-  k_trsm<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(m, n, A, lda, RT, rinv, W, ldw, ctl, level);
+  { ::mrcqr::note_launch(); k_trsm<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(m, n, A, lda, RT, rinv, W, ldw, ctl, level); }
 }
 
 // ---------------------------------------------------------------------------
@@ -190,9 +190,9 @@ void launch_syrk(int64_t m, int n, const double* X, int64_t ldx, int splits, dou
   int64_t rps = (m + splits - 1) / splits;
   rps = (rps + 31) / 32 * 32;
   const dim3 grid(tiles, splits);
-  if (TN == 16) k_syrk<16><<<grid, 32, 0, st>>>(m, n, X, ldx, rps, nt, Gpart, ctl, level);
-  else if (TN == 32) k_syrk<32><<<grid, 128, 0, st>>>(m, n, X, ldx, rps, nt, Gpart, ctl, level);
-  else k_syrk<64><<<grid, 512, 0, st>>>(m, n, X, ldx, rps, nt, Gpart, ctl, level);
+  if (TN == 16) { ::mrcqr::note_launch(); k_syrk<16><<<grid, 32, 0, st>>>(m, n, X, ldx, rps, nt, Gpart, ctl, level); }
+  else if (TN == 32) { ::mrcqr::note_launch(); k_syrk<32><<<grid, 128, 0, st>>>(m, n, X, ldx, rps, nt, Gpart, ctl, level); }
+  else { ::mrcqr::note_launch(); k_syrk<64><<<grid, 512, 0, st>>>(m, n, X, ldx, rps, nt, Gpart, ctl, level); }
 }
 
 // ---------------------------------------------------------------------------
@@ -218,7 +218,7 @@ __global__ void k_reduce_partials(int n, int splits, const double* __restrict__ 
 void launch_reduce_partials(int n, int splits, const double* part, double* out, const Ctl* ctl, int level,
                             cudaStream_t st) {
   const int64_t nn = (int64_t)n * n;
-  k_reduce_partials<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, splits, part, out, ctl, level);
+  { ::mrcqr::note_launch(); k_reduce_partials<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, splits, part, out, ctl, level); }
 }
 
 // ---------------------------------------------------------------------------
@@ -323,10 +323,10 @@ void launch_chol(int n, double* G, Ctl* ctl, int level, cudaStream_t st) {
     const size_t smem = sizeof(double) * (size_t)n * n;
     cudaFuncSetAttribute(k_chol_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(double) * kCholSmemN * kCholSmemN));
-    k_chol_smem<<<1, 1024, smem, st>>>(n, G, ctl, level);
+    { ::mrcqr::note_launch(); k_chol_smem<<<1, 1024, smem, st>>>(n, G, ctl, level); }
     return;
   }
-  k_chol<<<1, 1024, 0, st>>>(n, G, ctl, level);
+  { ::mrcqr::note_launch(); k_chol<<<1, 1024, 0, st>>>(n, G, ctl, level); }
 }
 
 // ---------------------------------------------------------------------------
@@ -400,10 +400,10 @@ __global__ void __launch_bounds__(128) k_trinv(int n, const double* __restrict__
 void launch_trinv(int n, const double* Rc, double* RcinvT, const Ctl* ctl, int level, cudaStream_t st) {
   const int npad = padded(n);
   const unsigned grid = (unsigned)((npad + 3) / 4);
-  if (n <= 64) k_trinv<2><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level);
-  else if (n <= 128) k_trinv<4><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level);
-  else if (n <= 256) k_trinv<8><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level);
-  else k_trinv<16><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level);
+  if (n <= 64) { ::mrcqr::note_launch(); k_trinv<2><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level); }
+  else if (n <= 128) { ::mrcqr::note_launch(); k_trinv<4><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level); }
+  else if (n <= 256) { ::mrcqr::note_launch(); k_trinv<8><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level); }
+  else { ::mrcqr::note_launch(); k_trinv<16><<<grid, 128, 0, st>>>(n, Rc, RcinvT, ctl, level); }
 }
 
 // R = R_c R_s (Algorithm 2 step 9), upper x upper; R col-major with ld ldr,
@@ -426,7 +426,7 @@ __global__ void k_rmul(int n, const double* __restrict__ Rc, const double* __res
 void launch_rmul(int n, const double* Rc, const double* Rs, double* R, int64_t ldr, const Ctl* ctl, int level,
                  cudaStream_t st) {
   const int64_t nn = (int64_t)n * n;
-  k_rmul<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, Rc, Rs, R, ldr, ctl, level);
+  { ::mrcqr::note_launch(); k_rmul<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, Rc, Rs, R, ldr, ctl, level); }
 }
 
 // ---------------------------------------------------------------------------
@@ -485,12 +485,12 @@ __global__ void k_upper_to_xt(int n, int npad, const double* __restrict__ X, int
 void launch_upper_to_xt(int n, const double* X, int64_t ldx, double* XT, cudaStream_t st) {
   const int npad = padded(n);
   const int64_t total = (int64_t)n * npad;
-  k_upper_to_xt<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, npad, X, ldx, XT);
+  { ::mrcqr::note_launch(); k_upper_to_xt<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, npad, X, ldx, XT); }
 }
 
 void launch_finalize(int64_t m, int n, double* Q, int64_t ldq, const double* XT, const Ctl* ctl, int level,
                      cudaStream_t st) {
-  k_finalize<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(m, n, Q, ldq, XT, ctl, level);
+  { ::mrcqr::note_launch(); k_finalize<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(m, n, Q, ldq, XT, ctl, level); }
 }
 
 // ---------------------------------------------------------------------------
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(1024) k_judge(int n, const double* __restrict_
 }
 
 void launch_judge(int n, const double* E, int check, Ctl* ctl, int level, cudaStream_t st) {
-  k_judge<<<1, 1024, 0, st>>>(n, E, check, ctl, level);
+  { ::mrcqr::note_launch(); k_judge<<<1, 1024, 0, st>>>(n, E, check, ctl, level); }
 }
 
 // ---------------------------------------------------------------------------
@@ -650,35 +650,35 @@ __global__ void kg_publish(Group g) {
 }  // namespace
 
 void launch_g_trsm(const Group& g, int level, cudaStream_t st) {
-  if (g.nitems) kg_trsm<<<grid_for(g.nitems), 128, 0, st>>>(g, level);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_trsm<<<grid_for(g.nitems), 128, 0, st>>>(g, level); }
 }
 void launch_g_syrk(const Group& g, int tn, bool check, int level, cudaStream_t st) {
   (void)check;
   if (!g.nitems) return;
-  if (tn == 16) kg_syrk<16><<<grid_for(g.nitems), 32, 0, st>>>(g, level);
-  else if (tn == 32) kg_syrk<32><<<grid_for(g.nitems), 128, 0, st>>>(g, level);
-  else kg_syrk<64><<<grid_for(g.nitems), 512, 0, st>>>(g, level);
+  if (tn == 16) { ::mrcqr::note_launch(); kg_syrk<16><<<grid_for(g.nitems), 32, 0, st>>>(g, level); }
+  else if (tn == 32) { ::mrcqr::note_launch(); kg_syrk<32><<<grid_for(g.nitems), 128, 0, st>>>(g, level); }
+  else { ::mrcqr::note_launch(); kg_syrk<64><<<grid_for(g.nitems), 512, 0, st>>>(g, level); }
 }
 void launch_g_reduce(const Group& g, bool check, int level, cudaStream_t st) {
-  if (g.nitems) kg_reduce<<<grid_for(g.nitems), 256, 0, st>>>(g, check ? 1 : 0, level);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_reduce<<<grid_for(g.nitems), 256, 0, st>>>(g, check ? 1 : 0, level); }
 }
 void launch_g_chol(const Group& g, int level, cudaStream_t st) {
-  if (g.nitems) kg_chol<<<grid_for(g.nitems), 1024, 0, st>>>(g, level);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_chol<<<grid_for(g.nitems), 1024, 0, st>>>(g, level); }
 }
 void launch_g_trinv(const Group& g, int level, cudaStream_t st) {
-  if (g.nitems) kg_trinv<<<grid_for(g.nitems), 64, 0, st>>>(g, level);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_trinv<<<grid_for(g.nitems), 64, 0, st>>>(g, level); }
 }
 void launch_g_rmul(const Group& g, int level, cudaStream_t st) {
-  if (g.nitems) kg_rmul<<<grid_for(g.nitems), 256, 0, st>>>(g, level);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_rmul<<<grid_for(g.nitems), 256, 0, st>>>(g, level); }
 }
 void launch_g_finalize(const Group& g, int level, cudaStream_t st) {
-  if (g.nitems) kg_finalize<<<grid_for(g.nitems), 128, 0, st>>>(g, level);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_finalize<<<grid_for(g.nitems), 128, 0, st>>>(g, level); }
 }
 void launch_g_judge(const Group& g, int level, cudaStream_t st) {
-  if (g.nitems) kg_judge<<<grid_for(g.nitems), 1024, 0, st>>>(g, level);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_judge<<<grid_for(g.nitems), 1024, 0, st>>>(g, level); }
 }
 void launch_g_publish(const Group& g, cudaStream_t st) {
-  if (g.nitems) kg_publish<<<(g.nitems + 127) / 128, 128, 0, st>>>(g);
+  if (g.nitems) { ::mrcqr::note_launch(); kg_publish<<<(g.nitems + 127) / 128, 128, 0, st>>>(g); }
 }
 
 }  // namespace mrcqr
