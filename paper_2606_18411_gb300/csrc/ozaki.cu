@@ -487,9 +487,16 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __shared__ __align__(8) uint64_t mma_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ uint32_t colE[kM];
+  __shared__ uint32_t sgn[2];   // Rademacher signs of a chunk's 32 rows (bit i: row r0 + i), by chunk parity
   OzPipe P = oz_begin(&tmem_slot, &mma_bar);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint64_t four_m = 4ull * (uint64_t)m;
+  // signs of the rows r0 .. r0 + 31 as a bit mask, one Philox draw per lane of warp 1
+  auto sign_mask = [&](int64_t r0, int64_t r_end) {
+    const int64_t j = r0 + lane;
+    const bool neg = j < r_end && row_sign((uint64_t)j, key) < 0.0;
+    return __ballot_sync(0xffffffffu, neg);
+  };
   bool abort = false;
   const int ntiles_all = SP.mblocks * SP.ntiles;
   const int nitems = ntiles_all * SP.slabs;
@@ -506,6 +513,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + kK - 1) / kK) : 0;
     __syncthreads();
     if (tid < kM) colE[tid] = c0 + tid < n ? oz::exp_field(colHi[c0 + tid]) : 0u;
+    if (warp == 1) {
+      const uint32_t mk = sign_mask(r_begin, r_end);
+      if (lane == 0) sgn[0] = mk;
+    }
     __syncthreads();
     // phase of (sample fi, row r_begin + 4 fg), its advance per chunk and per row
     const bool fval = i0 + fi < s;
@@ -535,10 +546,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     load_chunk(r_begin);
     auto produce = [&](int ch, unsigned char* a, unsigned char* b) {
       const int64_t r0 = r_begin + (int64_t)ch * kK;
-      // Rademacher signs of this lane's two rows
-      const int64_t j0 = r0 + 2 * sp;
-      const uint32_t f0 = (j0 < r_end && row_sign((uint64_t)j0, key) < 0.0) ? 1u : 0u;
-      const uint32_t f1 = (j0 + 1 < r_end && row_sign((uint64_t)(j0 + 1), key) < 0.0) ? 1u : 0u;
+      // Rademacher signs of this lane's two rows (mask of this chunk made one chunk ahead by warp 1;
+      // the pipeline's barrier between chunks publishes it)
+      const uint32_t mk = sgn[ch & 1];
+      const uint32_t f0 = (mk >> (2 * sp)) & 1u, f1 = (mk >> (2 * sp + 1)) & 1u;
+      if (warp == 1 && ch + 1 < nchunks) {
+        const uint32_t mk1 = sign_mask(r0 + kK, r_end);
+        if (lane == 0) sgn[(ch + 1) & 1] = mk1;
+      }
       oz_store_cols<kM>(va, colE, f0, f1, a, kAPanel, warp, lane);
 #pragma unroll
       for (int t2 = 0; t2 < 2; ++t2)
