@@ -423,6 +423,73 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def run_sweep(args):
+    """Stability sweep of the paper's experiment (Sec. IV-B, Fig. 1) on the
+    m = 2^22, n = 128 sweep workload: geometric, step-cliff and clustered
+    spectra, kappa_2 = 1e0 .. 1e16 in decades, MRCQR with each sketch
+    precision (FP16, BF16, FP32, FP64; no escalation, so each precision's own
+    error shows) and CholQR2.  Per run: status, ||I - Q^T Q||_F from the
+    device judge, the residual of the leading 8-column block in double-double
+    (oracle), and for MRCQR the sketch error on sampled entries against the
+    oracle's dense FP64 sketch rows.  Prints one JSON line (rank 0)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2606_18411_gb300 import build as _build
+    from paper_2606_18411_gb300 import inputs, _lib
+    from paper_2606_18411_gb300 import mrcqr as M
+
+    rank, world, local = env_rank()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    _build.build()
+    dev = torch.device("cuda", local)
+    m, n, s, seed = args.m, args.n, 2 * args.n, 0
+    idx = O.sample_rows(m, s, seed)
+    signs = O.rademacher(m, seed)
+    rng = np.random.default_rng(7)
+    rows, cols = rng.choice(s, 6, replace=False), rng.choice(n, 6, replace=False)
+    stats = torch.zeros(8, dtype=torch.float64, device=dev)
+
+    def read_stats():
+        return _lib.Stats.from_buffer_copy(stats.cpu().numpy().tobytes()).as_dict()
+
+    def residual(A, Q, R, k=8):
+        return O.residual_error(A[:, :k].cpu().numpy(), Q[:, :k].cpu().numpy(), R[:k, :k].cpu().numpy())[0]
+
+    out = []
+    t0 = time.perf_counter()
+    for kind in ("geometric", "cliff", "clustered"):
+        for e in range(0, 17):
+            kappa = 10.0 ** e
+            A = inputs.make_matrix_device(m, n, kappa, kind=kind, seed=5000 + e, device=dev)
+            Ac = A[:, cols.tolist()].cpu().numpy()
+            Yref = np.stack([O.sketch_row(int(idx[r]), m, s, signs) @ Ac for r in rows])
+            Q = M.empty_colmajor(m, n, device=dev)
+            R = M.empty_colmajor(n, n, device=dev)
+            for prec in ("fp16", "bf16", "fp32", "fp64"):
+                Y = M.sketch(A, s, prec=prec, seed=seed).cpu().numpy()[np.ix_(rows, cols)]
+                sk = float(np.linalg.norm(Y - Yref) / np.linalg.norm(Yref))
+                M.factor_ex(A, Q, R, prec=prec, seed=seed, escalate=False, stats_device=stats)
+                torch.cuda.synchronize()
+                st = read_stats()
+                out.append({"spectrum": kind, "kappa": kappa, "method": f"mrcqr-{prec}", "status": st["status"],
+                            "ortho_fro": st["ortho_fro"], "residual_lead8": residual(A, Q, R), "sketch_err": sk})
+            Q2, R2 = M.cholqr2(A)
+            torch.cuda.synchronize()
+            st = M.last_status()
+            out.append({"spectrum": kind, "kappa": kappa, "method": "cholqr2", "status": st["status"],
+                        "ortho_fro": st["ortho_fro"], "residual_lead8": residual(A, Q2, R2)})
+            del A, Q, R, Q2, R2
+            torch.cuda.empty_cache()
+    line = {"metric": "stability sweep (orthogonality, residual, sketch error) of MRCQR per sketch precision and "
+                      "CholQR2", "workload": f"MRCQR m=2^{int(math.log2(m))} n={n} s={s} spectra geometric/cliff/"
+                      "clustered kappa 1e0..1e16", "runs": len(out), "wall_s": round(time.perf_counter() - t0, 1),
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(n: int, m_full: int, m_sample: int = 1 << 18):
     """The CPU oracle, as it stands, on one matrix of the workload cut to
     m_sample rows (its cost is linear in m), scaled to factorizations/s of
@@ -479,7 +546,7 @@ def main():
     ap.add_argument("--m", type=int, default=1 << 20)
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["large", "batched"], default="large")
+    ap.add_argument("--workload", choices=["large", "batched", "sweep"], default="large")
     ap.add_argument("--count", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -488,6 +555,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

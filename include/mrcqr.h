@@ -195,6 +195,18 @@ int mrcqr_sketch_ex(int64_t m, int64_t n, const double* A, int64_t lda, int64_t 
  * written to Rs (DEVICE double n x n, ld = n). */
 int mrcqr_sketch_qr(int64_t n, int64_t s, const double* Y, int prec, double* Rs, mrcqr_stream_t stream);
 
+/* CholQR2, the comparison method of the paper's stability experiment (Sec. I-A,
+ * Sec. IV-B): Algorithm 1 run twice, R_1 = chol(A^T A), then Q, R_2 = CholQR(A R_1^{-1})
+ * (A R_1^{-1} by substitution) and R = R_2 R_1, all products in emulated FP64
+ * (as mrcqr_factor).  A (m x n, ld lda), Q (m x n, ld ldq), R (n x n, ld ldr,
+ * strict lower triangle set to 0): DEVICE doubles, column-major, caller-owned;
+ * A is read-only and may not alias Q or R.  Asynchronous on stream; status
+ * through mrcqr_get_last_status: BREAKDOWN when A^T A is not numerically
+ * positive definite (kappa_2(A) beyond about 1e8), ORTHO when ||I - Q^T Q||_F
+ * exceeds 1e-13.  INVALID on bad arguments (before any launch). */
+int mrcqr_cholqr2(int64_t m, int64_t n, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
+                  int64_t ldr, mrcqr_stream_t stream);
+
 /* Algorithm 2 steps 7-9 with a given preconditioner: Q, R_c = CholQR(A R_s^{-1})
  * (Algorithm 1) and R = R_c R_s.  With Rs = I this is Algorithm 1 on A.
  * Status (breakdown) through mrcqr_get_last_status. */

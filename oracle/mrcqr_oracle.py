@@ -317,6 +317,16 @@ def cholqr(A: np.ndarray):
     return Q, R
 
 
+def cholqr2(A: np.ndarray):
+    """CholQR2 (Sec. I-A, the comparison method of the stability experiment):
+    Algorithm 1 run twice, Q1, R1 = CholQR(A); Q, R2 = CholQR(Q1); R = R2 R1.
+    Raises CholeskyBreakdown when the first Gram matrix is not numerically
+    positive definite (kappa_2(A) beyond about u^{-1/2})."""
+    Q1, R1 = cholqr(A)
+    Q, R2 = cholqr(Q1)
+    return Q, np.triu(R2 @ R1)
+
+
 @dataclass
 class MRCQRResult:
     Q: np.ndarray

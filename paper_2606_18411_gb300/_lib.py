@@ -77,6 +77,7 @@ SIGNATURES = {
     "mrcqr_cholqr_precond": ([_i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp], _i32),
     "mrcqr_finalize_q": ([_i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp], _i32),
     "mrcqr_gram": ([_i64, _i64, _vp, _i64, _vp, _i32, _vp], _i32),
+    "mrcqr_cholqr2": ([_i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp], _i32),
     "mrcqr_trsm": ([_i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp], _i32),
     "mrcqr_sketch_qr_noalloc": ([_i64, _i64, _vp, _i32, _vp, _vp], _i32),
     "mrcqr_selector_num_params": ([], _i32),

@@ -463,6 +463,37 @@ int mrcqr_sketch_qr(int64_t n, int64_t s, const double* Y, int prec, double* Rs,
   return finish(st);
 }
 
+int mrcqr_cholqr2(int64_t m, int64_t n, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
+                  int64_t ldr, mrcqr_stream_t stream) {
+  int rc = validate(m, n, A, lda, Q, ldq, R, ldr, 1);
+  if (rc != MRCQR_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(m, (int)n, (int)n);
+  mrcqr_stats_t* slot = status_slot(st);
+  if (!slot) return MRCQR_ERR_ALLOC;
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, p.total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCQR_ERR_ALLOC;
+  }
+  Ctl* ctl = at<Ctl>(ws, p.off_ctl);
+  double* Rc = at<double>(ws, p.off_rc);
+  double* Rs = at<double>(ws, p.off_rs);
+  launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
+  // first pass, R only: R_1 = chol(A^T A) (a breakdown ends the call with that status)
+  launch(SG_SYRK, 0, st, [&] {
+    launch_syrk_oz(p.m, p.n, A, lda, p.oz, at<uint32_t>(ws, p.off_colhi), at<long long>(ws, p.off_ozpart), Rc, ctl, 0, st);
+  });
+  launch(SG_CHOL, 0, st, [&] { launch_chol(p.n, Rc, ctl, 0, st); });
+  // second pass: CholQR of A R_1^{-1} (substitution), R = R_2 R_1, with the orthogonality judge
+  cudaMemcpyAsync(Rs, Rc, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st);
+  launch(SG_PREP, 0, st, [&] { launch_rs_prepare((int)n, Rs, at<double>(ws, p.off_rst), at<double>(ws, p.off_rinv), st); });
+  enqueue_stage2(p, ws, A, lda, Q, ldq, R, ldr, 1, ctl, 0, st);
+  launch(SG_STATS, 0, st, [&] { { ::mrcqr::note_launch(); k_write_stats<<<1, 1, 0, st>>>(ctl, slot); } });
+  cudaFreeAsync(ws, st);
+  return finish(st);
+}
+
 int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, const double* Rs, double* Q,
                          int64_t ldq, double* R, int64_t ldr, mrcqr_stream_t stream) {
   int rc = validate(m, n, A, lda, Q, ldq, R, ldr, 1);

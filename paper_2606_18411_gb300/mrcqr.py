@@ -220,6 +220,16 @@ def cholqr_precond(A: torch.Tensor, Rs: torch.Tensor, stream=None):
     return Q, R
 
 
+def cholqr2(A: torch.Tensor, stream=None):
+    """Q, R = CholQR2(A) (asynchronous; status through last_status)."""
+    m, n = A.shape
+    Q = empty_colmajor(m, n, device=A.device)
+    R = empty_colmajor(n, n, device=A.device)
+    check(_lib.load().mrcqr_cholqr2(m, n, A.data_ptr(), _ld(A, "A"), Q.data_ptr(), _ld(Q, "Q"), R.data_ptr(),
+                                    _ld(R, "R"), _stream(stream)), "mrcqr_cholqr2")
+    return Q, R
+
+
 def finalize_q(W: torch.Tensor, X: torch.Tensor, fp64_products: int = 0, stream=None) -> torch.Tensor:
     """Q = W X with X upper triangular (the upper triangle of X is read); W is overwritten."""
     m, n = W.shape

@@ -202,6 +202,28 @@ def _check_factor(M, A, prec, seed=0, expect_prec=None, **kw):
     return st, o2, rf, Qh, Rh
 
 
+@pytest.mark.parametrize("kappa", [1e0, 1e4, 1e7])
+def test_cholqr2_against_oracle(M, kappa):
+    # the stability experiment's comparison method: O(u) while kappa^2 u < 1
+    A = inputs.make_matrix(8193, 48, kappa, seed=17)
+    Q, R = M.cholqr2(M.to_colmajor(A))
+    st = M.last_status()
+    Qh, Rh = _np(Q), _np(R)
+    assert st["status"] == "OK", st
+    o2 = O.orthogonality_error(Qh)[0]
+    rf = O.residual_error(A, Qh, Rh)[0]
+    assert o2 <= 1e-13 and rf <= 1e-13, (o2, rf)
+    Qo, Ro = O.cholqr2(A)
+    assert _rel(Rh, Ro) < 100 * kappa * O.U_FP64
+    np.testing.assert_array_equal(np.tril(Rh, -1), 0)
+
+
+def test_cholqr2_breaks_down_past_1e8(M):
+    A = inputs.make_matrix(8193, 48, 1e12, seed=18)
+    M.cholqr2(M.to_colmajor(A))
+    assert M.last_status()["status"] in ("BREAKDOWN", "ORTHO")
+
+
 def test_config1_fp32_sketch(M):
     # m=4096, n=32, geometric sigma 1..1e-8, FP32 sketch, s=2n, seed 0
     A = inputs.make_matrix(4096, 32, 1e8, seed=1001)

@@ -208,6 +208,24 @@ def test_cholqr_instability_and_probe_bound():
             O.cholqr(inputs.make_matrix(m, n, 1e10, seed=3))
 
 
+def test_cholqr2_orthogonal_below_1e8_and_breaks_down_beyond():
+    # CholQR2 (Sec. I-A): the second pass restores O(u) orthogonality while kappa^2 u < 1,
+    # and the first Gram matrix is not positive definite in FP64 past kappa ~ 1e8
+    m, n = 4096, 16
+    for kappa in (1e0, 1e3, 1e6, 1e7):
+        A = inputs.make_matrix(m, n, kappa, seed=5)
+        Q, R = O.cholqr2(A)
+        o2 = O.orthogonality_error(Q)[0]
+        rf = O.residual_error(A, Q, R)[0]
+        assert o2 < 1e-14 and rf < 1e-15, (kappa, o2, rf)
+        # the unique thin QR with diag(R) > 0: LAPACK's Householder R, rows sign-normalised
+        Rh = np.linalg.qr(A, mode="r")
+        Rh = Rh * np.sign(np.diag(Rh))[:, None]
+        assert np.linalg.norm(R - Rh) / np.linalg.norm(Rh) < 100 * kappa * O.U_FP64
+    with pytest.raises(O.CholeskyBreakdown):
+        O.cholqr2(inputs.make_matrix(m, n, 1e10, seed=6))
+
+
 # --- Algorithm 2 end to end ---------------------------------------------------
 
 @pytest.mark.parametrize("kappa", [1e0, 1e4, 1e8, 1e12, 1e16])
