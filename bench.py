@@ -279,6 +279,23 @@ def run_ours(args):
     baseline_value = len(As) * world * kb / t_b
     st_b = read_stats()
 
+    # the learned precision selector (AUTO): FP16 sketch, features, MLP choice, re-sketch if needed
+    auto = None
+    try:
+        from paper_2606_18411_gb300 import selector as _sel
+        _sel.load_into_library()
+        autop = ["auto"] * len(As)
+        step(autop)
+        torch.cuda.synchronize()
+        t_a, _, _ = timed(autop, kb)
+        st_a = read_stats()
+        auto = {"value": round(len(As) * world * kb / t_a, 4), "unit": UNIT,
+                "speedup_vs_fp64_sketch": round(len(As) * world * kb / t_a / baseline_value, 3),
+                "precisions_used": [s["prec_used"] for s in st_a], "retries": [s["retries"] for s in st_a],
+                "all_ok": all(s["status"] == "OK" for s in st_a)}
+    except (OSError, RuntimeError) as exc:   # no shipped weights: report why
+        auto = {"unavailable": str(exc)}
+
     # end to end through the public API with host buffers
     hA = [a.t().contiguous().cpu().pin_memory() for a in As]       # n x m row-major = column-major m x n
     hQ = [torch.empty((n, m), dtype=torch.float64).pin_memory() for _ in As]
@@ -332,6 +349,7 @@ def run_ours(args):
             "fp64_sketch_baseline": {"value": round(baseline_value, 4), "unit": UNIT,
                                      "speedup_of_rule_precision": round(value / baseline_value, 3),
                                      "all_ok": all(s["status"] == "OK" for s in st_b)},
+            "learned_selector": auto,
             "all_ok": ok, "ortho_fro": [s["ortho_fro"] for s in st_after],
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "step_ms_by_kernel": step_ms_by_kernel, "clocks": clocks, "cpu_baseline": cpu,
