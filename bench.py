@@ -421,6 +421,11 @@ def run_batched(args):
     t_once = timed(lambda: M.factor_batched(As, Qs, Rs, precs, seeds, status), 1)
     ok1 = status.cpu().tolist()
     t_loop = timed(lambda: [M.factor(As[i], prec=precs[i], seed=seeds[i]) for i in range(cnt)], 1)
+    plan_fma = M.BatchedPlan(As, Qs, Rs, precs, seeds, status, use_graph=True, fp64_products=1)
+    plan_fma.execute()
+    t_fma = timed(plan_fma.execute, 1)
+    ok_fma = status.cpu().tolist()
+    plan_fma.close()
     flops = sum(fp64eq_flops(int(m), int(n)) for m, n in zip(ms, ns))
     if rank == 0:
         line = {"metric": METRIC, "value": round(cnt * world * K / t_plan, 4), "unit": UNIT, "n_gpus": world,
@@ -434,6 +439,8 @@ def run_batched(args):
                 "all_ok": all(v == 0 for v in ok) and all(v == 0 for v in ok1),
                 "oneshot_factorizations_per_s": round(cnt * world / t_once, 4),
                 "single_call_loop_factorizations_per_s": round(cnt * world / t_loop, 4),
+                "grouped_fp64_fma_plan_factorizations_per_s": round(cnt * world / t_fma, 4),
+                "grouped_fp64_fma_all_ok": all(v == 0 for v in ok_fma),
                 "gpu_launches_per_step": info["kernels_per_execute"], "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.close()

@@ -152,6 +152,10 @@ typedef struct mrcqr_batched_opts {
   double ortho_tol;       /* default 1e-13 */
   int64_t rows_per_split; /* SYRK rows per partial (0: tuned or default 4096) */
   int64_t rows_per_chunk; /* sketch rows per partial (0: tuned or default 8192) */
+  int32_t fp64_products;  /* 0 (default): emulated FP64 products, the single-problem tensor-core kernels of the
+                             FP64 sketch and stage 2 run per problem on side streams (fork/join inside the plan);
+                             1: every phase grouped with FP64 FMA kernels */
+  int32_t reserved;
 } mrcqr_batched_opts_t;
 
 int mrcqr_batched_plan_create(int count, const int64_t* m, const int64_t* n, const double* const* A,

@@ -6,6 +6,12 @@
 // The precision ladder of every problem (Sec. II-C) runs level by level:
 // items of level L skip themselves unless their problem is active at L.
 //
+// With emulated FP64 products (the default, as in mrcqr_factor) the heavy
+// phases -- the FP64 sketch, W = A R_s^{-1}, the Gram, Q = W R_c^{-1} and the
+// check -- run the single-problem tensor-core kernels per problem, spread over
+// side streams so that problems overlap; the light phases stay grouped.
+// fp64_products = 1 runs every phase grouped with FP64 FMA kernels.
+//
 // A plan (mrcqr_batched_plan_*) keeps the workspace, the uploaded work lists
 // and optionally the whole launch sequence captured as a CUDA graph, so a
 // repeated batch replays with one graph launch.  The tuner picks the SYRK
@@ -35,7 +41,24 @@ size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 enum Kind {
   K_INIT, K_SAMPLE, K_COSTAB, K_SKETCH, K_SKREDUCE, K_SQR, K_TRSM, K_SYRK, K_GREDUCE, K_CHOL, K_TRINV, K_RMUL,
-  K_FINALIZE, K_CHECK, K_EREDUCE, K_JUDGE, K_PUBLISH
+  K_FINALIZE, K_CHECK, K_EREDUCE, K_JUDGE, K_PUBLISH,
+  // emulated-FP64 phases of one problem (param = problem) between a fork and a join of the side streams
+  K_FORK, K_JOIN, K_OZ_SKETCH, K_OZ_STAGE2A, K_OZ_STAGE2B
+};
+
+constexpr int kSideStreams = 8;
+
+// Emulated-FP64 scratch of one problem (in the batch workspace).
+struct OzWs {
+  SyrkOzPlan sp;
+  SketchOzPlan kp;
+  uint32_t* colhi;
+  long long* part;
+  uint32_t* tcole;
+  unsigned char* trd;
+  uint32_t* oze;
+  unsigned char* ozx;
+  uint64_t seed;
 };
 
 struct Launch {
@@ -66,6 +89,10 @@ struct mrcqr_batched_plan_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int kernels = 0;
+  bool emu = true;                    // emulated-FP64 heavy phases
+  std::vector<OzWs> oz;               // per problem (emu)
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
 };
 
 namespace {
@@ -173,6 +200,22 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     f[12] = take(sizeof(double) * (size_t)P.n * P.npad);
     f[13] = take(sizeof(double) * nn);
   }
+  std::vector<std::array<size_t, 6>> ozoff(pl.emu ? count : 0);
+  pl.oz.assign(pl.emu ? count : 0, OzWs{});
+  for (int i = 0; i < (pl.emu ? count : 0); ++i) {
+    const Prob& P = pl.probs[i];
+    OzWs& z = pl.oz[i];
+    z.sp = syrk_oz_plan(P.m, P.n);
+    z.kp = sketch_oz_plan(P.m, P.n, P.s);
+    z.seed = seeds[i];
+    auto& g = ozoff[i];
+    g[0] = take(syrk_oz_colhi_bytes(P.n));
+    g[1] = take(std::max(syrk_oz_part_bytes(z.sp), sketch_oz_part_bytes(z.kp)));
+    g[2] = take(trsm_oz_cole_bytes(P.n));
+    g[3] = take(trsm_oz_rd_bytes(P.n));
+    g[4] = take(sizeof(uint32_t) * (size_t)((P.n + 63) / 64 * 64));
+    g[5] = take(oz_xs_bytes(P.n));
+  }
   const size_t probs_off = take(sizeof(Prob) * (size_t)count);
   // work lists
   pl.items.clear();
@@ -183,6 +226,12 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     pl.items.insert(pl.items.end(), v.begin(), v.end());
   };
   auto blocks = [](int64_t x, int64_t b) { return (int)((x + b - 1) / b); };
+  auto per_problem = [&](int kind, int level, const std::vector<int>& which) {   // fork, one entry each, join
+    if (which.empty()) return;
+    pl.launches.push_back(Launch{K_FORK, level, 0, 0, 0});
+    for (int i : which) pl.launches.push_back(Launch{kind, level, i, 0, 0});
+    pl.launches.push_back(Launch{K_JOIN, level, 0, 0, 0});
+  };
   pl.launches.push_back(Launch{K_INIT, 0, 0, 0, count});
   {
     std::vector<int4> v, c;
@@ -197,21 +246,28 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     std::vector<int> live;
     for (int i = 0; i < count; ++i)
       if (pl.probs[i].nlevels > L) live.push_back(i);
+    std::vector<int> oz_sk;   // problems whose sketch at this level is the emulated FP64 one
     for (int pr = P_FP16; pr <= P_FP64; ++pr) {
       std::vector<int4> v;
       for (int i : live) {
         const Prob& P = pl.probs[i];
         if (P.lvl_prec[L] != pr) continue;
+        if (pl.emu && pr == P_FP64) {
+          oz_sk.push_back(i);
+          continue;
+        }
         for (int c = 0; c < P.chunks; ++c)
           for (int a = 0; a < blocks(P.s, 64); ++a)
             for (int b = 0; b < blocks(P.n, 64); ++b) v.push_back(make_int4(i, c, a, b));
       }
       add(K_SKETCH, L, pr, v);
     }
+    per_problem(K_OZ_SKETCH, L, oz_sk);
     std::vector<int4> red, q32, q64, tr, gr, one, ti, rm, fi;
     for (int i : live) {
       const Prob& P = pl.probs[i];
-      for (int b = 0; b < blocks((int64_t)P.s * P.n, 256); ++b) red.push_back(make_int4(i, b, 0, 0));
+      if (!(pl.emu && P.lvl_prec[L] == P_FP64))
+        for (int b = 0; b < blocks((int64_t)P.s * P.n, 256); ++b) red.push_back(make_int4(i, b, 0, 0));
       (P.lvl_prec[L] == P_FP64 ? q64 : q32).push_back(make_int4(i, 0, 0, 0));
       for (int b = 0; b < blocks(P.m, 128); ++b) tr.push_back(make_int4(i, b, 0, 0));
       for (int b = 0; b < blocks((int64_t)P.n * P.n, 256); ++b) gr.push_back(make_int4(i, b, 0, 0));
@@ -223,24 +279,29 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     add(K_SKREDUCE, L, 0, red);
     add(K_SQR, L, 0, q32);
     add(K_SQR, L, 1, q64);
-    add(K_TRSM, L, 0, tr);
-    for (int tn : {16, 32, 64}) {
-      std::vector<int4> v;
-      for (int i : live) {
-        const Prob& P = pl.probs[i];
-        if (syrk_tile_for(P.n) != tn) continue;
-        const int tiles = P.ntile_syrk * (P.ntile_syrk + 1) / 2;
-        for (int sp = 0; sp < P.splits; ++sp)
-          for (int t = 0; t < tiles; ++t) v.push_back(make_int4(i, t, sp, 0));
+    if (pl.emu) {
+      per_problem(K_OZ_STAGE2A, L, live);   // W = A R_s^{-1}, G = W^T W
+    } else {
+      add(K_TRSM, L, 0, tr);
+      for (int tn : {16, 32, 64}) {
+        std::vector<int4> v;
+        for (int i : live) {
+          const Prob& P = pl.probs[i];
+          if (syrk_tile_for(P.n) != tn) continue;
+          const int tiles = P.ntile_syrk * (P.ntile_syrk + 1) / 2;
+          for (int sp = 0; sp < P.splits; ++sp)
+            for (int t = 0; t < tiles; ++t) v.push_back(make_int4(i, t, sp, 0));
+        }
+        add(K_SYRK, L, tn, v);
       }
-      add(K_SYRK, L, tn, v);
+      add(K_GREDUCE, L, 0, gr);
     }
-    add(K_GREDUCE, L, 0, gr);
     add(K_CHOL, L, 0, one);
     add(K_TRINV, L, 0, ti);
     add(K_RMUL, L, 0, rm);
-    add(K_FINALIZE, L, 0, fi);
-    if (check) {
+    if (pl.emu) per_problem(K_OZ_STAGE2B, L, live);   // Q = W R_c^{-1}, E = Q^T Q
+    else add(K_FINALIZE, L, 0, fi);
+    if (check && !pl.emu) {
       for (int tn : {16, 32, 64}) {
         std::vector<int4> v;
         for (int i : live) {
@@ -279,15 +340,63 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     P.xt = reinterpret_cast<double*>(base + f[12]);
     P.e = reinterpret_cast<double*>(base + f[13]);
   }
+  for (int i = 0; i < (int)pl.oz.size(); ++i) {
+    OzWs& z = pl.oz[i];
+    auto& g = ozoff[i];
+    z.colhi = reinterpret_cast<uint32_t*>(base + g[0]);
+    z.part = reinterpret_cast<long long*>(base + g[1]);
+    z.tcole = reinterpret_cast<uint32_t*>(base + g[2]);
+    z.trd = reinterpret_cast<unsigned char*>(base + g[3]);
+    z.oze = reinterpret_cast<uint32_t*>(base + g[4]);
+    z.ozx = reinterpret_cast<unsigned char*>(base + g[5]);
+  }
   pl.d_probs = reinterpret_cast<Prob*>(base + probs_off);
   pl.d_items = reinterpret_cast<int4*>(base + items_off);
 }
 
+// The emulated-FP64 kernels of one problem's heavy phase (its control block
+// makes them return at once unless the problem is active at this level).
+void enqueue_oz(const mrcqr_batched_plan_s& pl, int kind, int level, int i, cudaStream_t st) {
+  const Prob& P = pl.probs[i];
+  const OzWs& z = pl.oz[i];
+  switch (kind) {
+    case K_OZ_SKETCH:
+      launch_sketch_oz(P.m, P.n, P.s, P.A, P.lda, P.idx, P.tab, z.seed, z.kp, z.colhi, z.part, P.y, P.ctl, level, st);
+      break;
+    case K_OZ_STAGE2A:
+      launch_trsm_oz(P.m, P.n, P.A, P.lda, P.rst, P.rinv, z.tcole, z.trd, P.Q, P.ldq, P.ctl, level, st);
+      launch_syrk_oz(P.m, P.n, P.Q, P.ldq, z.sp, z.colhi, z.part, P.rc, P.ctl, level, st);
+      break;
+    case K_OZ_STAGE2B:
+      launch_finalize_oz(P.m, P.n, P.Q, P.ldq, P.xt, z.oze, z.ozx, P.ctl, level, st);
+      if (P.check) launch_syrk_oz(P.m, P.n, P.Q, P.ldq, z.sp, z.colhi, z.part, P.e, P.ctl, level, st);
+      break;
+  }
+}
+
 void enqueue(mrcqr_batched_plan_s& pl, cudaStream_t st) {
-  pl.kernels = 0;
+  const uint64_t c0 = mrcqr_launch_count();
+  int rr = 0;   // next side stream
   for (const Launch& L : pl.launches) {
     Group g{pl.d_probs, pl.d_items + L.off, L.cnt};
     switch (L.kind) {
+      case K_FORK:
+        cudaEventRecord(pl.fork_ev, st);
+        for (int k = 0; k < kSideStreams; ++k) cudaStreamWaitEvent(pl.side[k], pl.fork_ev, 0);
+        rr = 0;
+        break;
+      case K_JOIN:
+        for (int k = 0; k < kSideStreams; ++k) {
+          cudaEventRecord(pl.join_ev[k], pl.side[k]);
+          cudaStreamWaitEvent(st, pl.join_ev[k], 0);
+        }
+        break;
+      case K_OZ_SKETCH:
+      case K_OZ_STAGE2A:
+      case K_OZ_STAGE2B:
+        enqueue_oz(pl, L.kind, L.level, L.param, pl.side[rr]);
+        rr = (rr + 1) % kSideStreams;
+        break;
       case K_INIT: launch_g_init(Group{pl.d_probs, nullptr, L.cnt}, st); break;
       case K_SAMPLE: launch_g_sample(g, pl.max_s, st); break;
       case K_COSTAB: launch_g_costab(g, st); break;
@@ -306,8 +415,44 @@ void enqueue(mrcqr_batched_plan_s& pl, cudaStream_t st) {
       case K_JUDGE: launch_g_judge(g, L.level, st); break;
       case K_PUBLISH: launch_g_publish(Group{pl.d_probs, nullptr, L.cnt}, st); break;
     }
-    ++pl.kernels;
   }
+  pl.kernels = (int)(mrcqr_launch_count() - c0);
+}
+
+// Kernels one execute launches (each emulated heavy phase of a problem is
+// several kernels: sketch 3; TRSM 3 + Gram 3; finalize 2 + check 3).
+int count_kernels(const mrcqr_batched_plan_s& pl) {
+  int k = 0;
+  for (const Launch& L : pl.launches) {
+    switch (L.kind) {
+      case K_FORK: case K_JOIN: break;
+      case K_OZ_SKETCH: k += 3; break;
+      case K_OZ_STAGE2A: k += 6; break;
+      case K_OZ_STAGE2B: k += pl.probs[L.param].check ? 5 : 2; break;
+      default: k += 1;
+    }
+  }
+  return k;
+}
+
+bool make_streams(mrcqr_batched_plan_s& pl) {
+  if (cudaEventCreateWithFlags(&pl.fork_ev, cudaEventDisableTiming) != cudaSuccess) return false;
+  for (int k = 0; k < kSideStreams; ++k)
+    if (cudaStreamCreateWithFlags(&pl.side[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl.join_ev[k], cudaEventDisableTiming) != cudaSuccess)
+      return false;
+  return true;
+}
+
+void free_streams(mrcqr_batched_plan_s& pl) {
+  for (int k = 0; k < kSideStreams; ++k) {
+    if (pl.side[k]) cudaStreamDestroy(pl.side[k]);
+    if (pl.join_ev[k]) cudaEventDestroy(pl.join_ev[k]);
+    pl.side[k] = nullptr;
+    pl.join_ev[k] = nullptr;
+  }
+  if (pl.fork_ev) cudaEventDestroy(pl.fork_ev);
+  pl.fork_ev = nullptr;
 }
 
 int validate_batch(int count, const int64_t* m, const int64_t* n, const double* const* A, const int64_t* lda,
@@ -365,6 +510,12 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
   const bool escalate = opts ? (opts->escalate != 0) : true;
   const double tol = (opts && opts->ortho_tol > 0) ? opts->ortho_tol : 1e-13;
   pl->use_graph = opts ? (opts->use_graph != 0) : false;
+  pl->emu = opts ? (opts->fp64_products == 0) : true;
+  if (!make_streams(*pl)) {
+    free_streams(*pl);
+    delete pl;
+    return MRCQR_ERR_CUDA;
+  }
   const std::string sig = signature(count, m, n);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -385,6 +536,7 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
   build(*pl, count, m, n, A, lda, Q, ldq, R, sketch_prec, seeds, status, check, escalate, tol, &bytes);
   if ((async ? cudaMallocAsync(&pl->ws, bytes, st) : cudaMalloc(&pl->ws, bytes)) != cudaSuccess) {
     cudaGetLastError();
+    free_streams(*pl);
     delete pl;
     return MRCQR_ERR_ALLOC;
   }
@@ -435,9 +587,11 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
   }
   pl->tuning = best;
   if (rc == MRCQR_OK) rc = upload();
+  if (rc == MRCQR_OK) pl->kernels = count_kernels(*pl);
   if (rc != MRCQR_OK) {
     if (async) cudaFreeAsync(pl->ws, st);
     else cudaFree(pl->ws);
+    free_streams(*pl);
     delete pl;
     return rc;
   }
@@ -466,6 +620,7 @@ int mrcqr_factor_batched(int count, const int64_t* m, const int64_t* n, const do
   enqueue(*pl, st);
   cudaFreeAsync(pl->ws, st);
   pl->ws = nullptr;
+  free_streams(*pl);   // released once their queued work completes
   delete pl;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -503,7 +658,7 @@ int mrcqr_batched_plan_info(mrcqr_batched_plan_t pl, int64_t* rows_per_split, in
   if (!pl) return MRCQR_ERR_INVALID;
   if (rows_per_split) *rows_per_split = pl->tuning.rows_per_split;
   if (rows_per_chunk) *rows_per_chunk = pl->tuning.rows_per_chunk;
-  if (kernels_per_execute) *kernels_per_execute = (int32_t)pl->launches.size();
+  if (kernels_per_execute) *kernels_per_execute = pl->kernels > 0 ? pl->kernels : (int32_t)pl->launches.size();
   if (workspace_bytes) *workspace_bytes = (int64_t)pl->ws_bytes;
   return MRCQR_OK;
 }
@@ -513,6 +668,7 @@ int mrcqr_batched_plan_destroy(mrcqr_batched_plan_t pl) {
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
   if (pl->cap) cudaStreamDestroy(pl->cap);
+  free_streams(*pl);
   if (pl->ws) {
     if (pl->async_ws) cudaFreeAsync(pl->ws, nullptr);
     else cudaFree(pl->ws);

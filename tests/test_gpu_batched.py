@@ -108,6 +108,25 @@ def test_batched_plan_graph_replay_and_autotune(env):
     plan.close()
 
 
+def test_batched_plan_grouped_fp64_fma_mode(env):
+    # fp64_products = 1: every phase grouped with FP64 FMA kernels; same bounds, same statuses
+    torch, M = env
+    mats, kappas = _batch(SHAPES[:5], seed0=1900)
+    precs = [O.precision_rule(k) for k in kappas]
+    As = [M.to_colmajor(a) for a in mats]
+    Qs = [M.empty_colmajor(*a.shape) for a in mats]
+    Rs = [M.empty_colmajor(a.shape[1], a.shape[1]) for a in mats]
+    status = torch.full((len(mats),), -1, dtype=torch.int32, device="cuda")
+    plan = M.BatchedPlan(As, Qs, Rs, precs, [5] * len(mats), status, use_graph=True, fp64_products=1)
+    plan.execute()
+    torch.cuda.synchronize()
+    assert status.cpu().tolist() == [0] * len(mats)
+    for A, Q, R in zip(mats, Qs, Rs):
+        assert O.orthogonality_error(Q.cpu().numpy())[0] <= 1e-13
+        assert O.residual_error(A, Q.cpu().numpy(), R.cpu().numpy())[0] <= 1e-13
+    plan.close()
+
+
 def test_batched_rejects_invalid(env):
     torch, M = env
     A = M.to_colmajor(inputs.gaussian(100, 60, seed=1))   # m < 2n
