@@ -69,6 +69,23 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def input_seed(rank: int, i: int) -> int:
+    """Generator seed of rank's i-th matrix: ranks factor disjoint sets of
+    problems (weak scaling, no data-path collective)."""
+    return 2000 + 17 * rank + i
+
+
+def max_over_ranks(t: float, device, world: int) -> float:
+    """The step time of the slowest rank (the only cross-rank exchange)."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def blas_threads() -> int:
     try:
         from threadpoolctl import threadpool_info
@@ -162,7 +179,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     m, n, K, W = args.m, args.n, args.steps, args.warmup
     precs = [rule(k) for k in KAPPAS]
-    As = [inputs.make_matrix_device(m, n, k, seed=2000 + 17 * rank + i, device=dev) for i, k in enumerate(KAPPAS)]
+    As = [inputs.make_matrix_device(m, n, k, seed=input_seed(rank, i), device=dev) for i, k in enumerate(KAPPAS)]
     Qs = [M.empty_colmajor(m, n, device=dev) for _ in KAPPAS]
     Rs = [M.empty_colmajor(n, n, device=dev) for _ in KAPPAS]
     stats = torch.zeros((len(KAPPAS), 8), dtype=torch.float64, device=dev)   # 64 B per mrcqr_stats_t
@@ -200,11 +217,7 @@ def run_ours(args):
             ms = (ctypes.c_float * cap)()
             lib.mrcqr_profile_end(cap, st, lv, ms, ctypes.byref(cnt))
             recs = [(st[i], lv[i], ms[i]) for i in range(min(cnt.value, cap))]
-        t = e0.elapsed_time(e1) / 1000.0
-        if world > 1:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(e0.elapsed_time(e1) / 1000.0, dev, world)
         return t, launches, recs
 
     def read_stats():
@@ -321,11 +334,7 @@ def run_ours(args):
     e1.record()
     torch.cuda.synchronize()
     barrier()
-    t_e = e0.elapsed_time(e1) / 1000.0
-    if world > 1:
-        tt = torch.tensor([t_e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e = float(tt.item())
+    t_e = max_over_ranks(e0.elapsed_time(e1) / 1000.0, dev, world)
     e2e = {"value": round(len(As) * world * ke / t_e, 4), "unit": UNIT,
            "h2d_bytes_per_step": int(len(As) * 8 * m * n),
            "d2h_bytes_per_step": int(len(As) * 8 * (m * n + n * n))}
@@ -404,12 +413,7 @@ def run_batched(args):
             fn()
         e1.record()
         torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1000.0
-        if world > 1:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return t
+        return max_over_ranks(e0.elapsed_time(e1) / 1000.0, dev, world)
 
     for _ in range(W):
         plan.execute()
