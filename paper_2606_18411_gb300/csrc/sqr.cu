@@ -144,10 +144,36 @@ __device__ __forceinline__ T wmax(T v) {
 // Householder reflector of x[jj..rows) by one warp (the column's owner):
 // beta = -sign(x0) ||x||, v = (1, x[jj+1..] / (x0 - beta)), tau = 2 / ||v||^2.
 // x[jj] <- beta, x[jj+1..] <- v[1..]; returns tau (0 for a zero column).
-// The norm is scaled by the column maximum, so FP32 neither overflows nor
-// underflows.
+// FP32 scales the norm by the column maximum so it neither overflows nor
+// underflows; FP64 does so only when the plain sum of squares leaves
+// [1e-250, 1e250] (each FP64 operation is a long-latency step on this GPU).
 template <typename T>
 __device__ __forceinline__ T house_warp(T* x, int jj, int rows, int lane) {
+  if constexpr (sizeof(T) == 8) {   // FP64: unscaled sums of squares unless they leave the normal range
+    T t0 = T(0), t1 = T(0);
+    int i = jj + 1 + lane;
+    for (; i + 32 < rows; i += 64) {
+      t0 = fma(x[i], x[i], t0);
+      t1 = fma(x[i + 32], x[i + 32], t1);
+    }
+    if (i < rows) t0 = fma(x[i], x[i], t0);
+    const T tail = wsum(t0 + t1);
+    const T x0 = x[jj];
+    const T ss = fma(x0, x0, tail);
+    if (ss > T(1e-250) && ss < T(1e250)) {
+      const T nrm = sqrt(ss);
+      const T beta = x0 >= T(0) ? -nrm : nrm;
+      const T d = x0 - beta;
+      const T scale = T(1) / d;
+      const T tau = T(2) / fma(tail * scale, scale, T(1));
+      __syncwarp();
+      for (int k = jj + 1 + lane; k < rows; k += 32) x[k] *= scale;
+      if (lane == 0) x[jj] = beta;
+      __syncwarp();
+      return tau;
+    }
+    if (!(ss > T(0))) return T(0);   // zero column (or NaN: left as it is)
+  }
   T amax = T(0);
   for (int i = jj + lane; i < rows; i += 32) amax = max(amax, (T)fabs(x[i]));
   amax = wmax(amax);
