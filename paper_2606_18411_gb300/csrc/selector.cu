@@ -52,47 +52,49 @@ __device__ double block_max_d(double v, double* red) {
   return red[32];
 }
 
+// The reciprocals of the diagonal (rd = 1 / |R_jj|, rdg = 1 / R_jj) are formed
+// once: FP64 division is a long sequence on this GPU's 1/64-rate pipe, and the
+// sweeps below would otherwise divide at every step in every thread.
+
 // y = M x (M = R or R diag(R)^-1), x and y in shared memory
-__device__ void mat_vec(const double* R, const double* d, bool unit, int n, const double* x, double* y) {
+__device__ void mat_vec(const double* R, const double* rd, bool unit, int n, const double* x, double* y) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double acc = 0.0;
-    for (int j = i; j < n; ++j) acc = fma(R[(int64_t)j * n + i] * (unit ? 1.0 / d[j] : 1.0), x[j], acc);
+    for (int j = i; j < n; ++j) acc = fma(R[(int64_t)j * n + i] * (unit ? rd[j] : 1.0), x[j], acc);
     y[i] = acc;
   }
   __syncthreads();
 }
 
 // y = M^T x
-__device__ void mat_t_vec(const double* R, const double* d, bool unit, int n, const double* x, double* y) {
+__device__ void mat_t_vec(const double* R, const double* rd, bool unit, int n, const double* x, double* y) {
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     double acc = 0.0;
     for (int i = 0; i <= j; ++i) acc = fma(R[(int64_t)j * n + i], x[i], acc);
-    y[j] = unit ? acc / d[j] : acc;
+    y[j] = unit ? acc * rd[j] : acc;
   }
   __syncthreads();
 }
 
 // x <- M^{-1} x (column sweep from the last column)
-__device__ void solve(const double* R, const double* d, bool unit, int n, double* x) {
+__device__ void solve(const double* R, const double* rd, const double* rdg, bool unit, int n, double* x) {
   for (int j = n - 1; j >= 0; --j) {
-    const double djj = unit ? 1.0 : R[(int64_t)j * n + j];
-    const double xj = x[j] / djj;
+    const double xj = unit ? x[j] : x[j] * rdg[j];
     __syncthreads();
     for (int i = threadIdx.x; i < j; i += blockDim.x)
-      x[i] = fma(-R[(int64_t)j * n + i] * (unit ? 1.0 / d[j] : 1.0), xj, x[i]);
+      x[i] = fma(-R[(int64_t)j * n + i] * (unit ? rd[j] : 1.0), xj, x[i]);
     if (threadIdx.x == 0) x[j] = xj;
     __syncthreads();
   }
 }
 
 // x <- M^{-T} x (forward sweep)
-__device__ void solve_t(const double* R, const double* d, bool unit, int n, double* x) {
+__device__ void solve_t(const double* R, const double* rd, const double* rdg, bool unit, int n, double* x) {
   for (int j = 0; j < n; ++j) {
-    const double djj = unit ? 1.0 : R[(int64_t)j * n + j];
-    const double xj = x[j] / djj;
+    const double xj = unit ? x[j] : x[j] * rdg[j];
     __syncthreads();
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
-      x[i] = fma(-R[(int64_t)i * n + j] * (unit ? 1.0 / d[i] : 1.0), xj, x[i]);
+      x[i] = fma(-R[(int64_t)i * n + j] * (unit ? rd[i] : 1.0), xj, x[i]);
     if (threadIdx.x == 0) x[j] = xj;
     __syncthreads();
   }
@@ -105,18 +107,18 @@ __device__ double vec_norm(const double* x, int n, double* red) {
 }
 
 // 3-step power iteration for ||M|| (inverse = false) or ||M^{-1}|| (true).
-__device__ double power_norm(const double* R, const double* d, bool unit, bool inverse, int n, double* x, double* y,
-                             double* red) {
+__device__ double power_norm(const double* R, const double* rd, const double* rdg, bool unit, bool inverse, int n,
+                             double* x, double* y, double* red) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = 1.0 / sqrt((double)n);
   __syncthreads();
   double nrm = 0.0;
   for (int it = 0; it < 3; ++it) {
     if (!inverse) {
-      mat_vec(R, d, unit, n, x, y);
-      mat_t_vec(R, d, unit, n, y, x);
+      mat_vec(R, rd, unit, n, x, y);
+      mat_t_vec(R, rd, unit, n, y, x);
     } else {
-      solve(R, d, unit, n, x);
-      solve_t(R, d, unit, n, x);
+      solve(R, rd, rdg, unit, n, x);
+      solve_t(R, rd, rdg, unit, n, x);
     }
     nrm = vec_norm(x, n, red);
     if (!(nrm > 0.0) || !isfinite(nrm)) return nrm;
@@ -129,13 +131,15 @@ __device__ double power_norm(const double* R, const double* d, bool unit, bool i
 __global__ void __launch_bounds__(kFeatThreads) k_features(const double* __restrict__ R, int n, int64_t m,
                                                           float* __restrict__ out, const Ctl* ctl, int level) {
   if (ctl && (ctl->active != level || ctl->lvl_status != 0)) return;
-  __shared__ double d[kMaxN], L[kMaxN], Ls[kMaxN], x[kMaxN], y[kMaxN];
+  __shared__ double d[kMaxN], L[kMaxN], Ls[kMaxN], x[kMaxN], y[kMaxN], rd[kMaxN], rdg[kMaxN];
   __shared__ double red[33];
   const double tiny = 2.2250738585072014e-308;
   const int tid = threadIdx.x;
   for (int i = tid; i < kMaxN; i += blockDim.x) {
     if (i < n) {
       d[i] = fabs(R[(int64_t)i * n + i]);
+      rd[i] = 1.0 / d[i];
+      rdg[i] = 1.0 / R[(int64_t)i * n + i];
       L[i] = log10(fmax(d[i], tiny));
       Ls[i] = L[i];
     } else {
@@ -169,10 +173,10 @@ __global__ void __launch_bounds__(kFeatThreads) k_features(const double* __restr
   const double gapm = block_sum_d(gap, red) / n;
   const double dmax = pow(10.0, lmax);
   // condition estimates of R and of R diag(R)^-1
-  const double nr = power_norm(R, d, false, false, n, x, y, red);
-  const double ni = power_norm(R, d, false, true, n, x, y, red);
-  const double ur = power_norm(R, d, true, false, n, x, y, red);
-  const double ui = power_norm(R, d, true, true, n, x, y, red);
+  const double nr = power_norm(R, rd, rdg, false, false, n, x, y, red);
+  const double ni = power_norm(R, rd, rdg, false, true, n, x, y, red);
+  const double ur = power_norm(R, rd, rdg, true, false, n, x, y, red);
+  const double ui = power_norm(R, rd, rdg, true, true, n, x, y, red);
   // column norms, off-diagonal mass, noise-floor fractions
   double cmax = 0.0, cmin = INFINITY, off = 0.0, dsq = 0.0, f16 = 0.0, f32 = 0.0;
   for (int j = tid; j < n; j += blockDim.x) {

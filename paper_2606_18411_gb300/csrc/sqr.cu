@@ -26,6 +26,7 @@ __device__ __forceinline__ void sketch_qr_block(int n, int s, const double* __re
                                                 double* __restrict__ rinv) {
   __shared__ T red[33];
   __shared__ T diag[512];
+  __shared__ T sh_inv, sh_tau;   // per-column scalars, formed once (FP64 division and sqrt are long sequences)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int64_t total = (int64_t)s * n;
   for (int64_t e = tid; e < total; e += blockDim.x) W[e] = (T)Y[e];
@@ -42,31 +43,33 @@ __device__ __forceinline__ void sketch_qr_block(int n, int s, const double* __re
     if (warp == 0) {
       T t = lane < nwarps ? red[lane] : T(0);
       t = warp_max(t);
-      if (lane == 0) red[32] = t;
+      if (lane == 0) {
+        red[32] = t;
+        sh_inv = t > T(0) ? T(1) / t : T(0);
+      }
     }
     __syncthreads();
     amax = red[32];
     T part = T(0);
     if (amax > T(0)) {
-      const T inv = T(1) / amax;
+      const T inv = sh_inv;
       for (int i = j + tid; i < s; i += blockDim.x) {
         const T v = col[i] * inv;
         part = fma(v, v, part);
       }
     }
     const T ss = block_sum(part, red);
-    const T nrm = amax * sqrt(ss);
-    const T x0 = col[j];
-    const T alpha = (x0 >= T(0)) ? -nrm : nrm;
-    const T v0 = x0 - alpha;
-    // ||v||^2 = 2 nrm (nrm + |x0|), so tau = 2/||v||^2 = 1/(nrm (nrm + |x0|))
-    const T tau = (nrm > T(0)) ? T(1) / (nrm * (nrm + (T)fabs(x0))) : T(0);
-    __syncthreads();
     if (tid == 0) {
-      col[j] = v0;
+      const T nrm = amax * sqrt(ss);
+      const T x0 = col[j];
+      const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+      // ||v||^2 = 2 nrm (nrm + |x0|), so tau = 2/||v||^2 = 1/(nrm (nrm + |x0|))
+      sh_tau = (nrm > T(0)) ? T(1) / (nrm * (nrm + (T)fabs(x0))) : T(0);
+      col[j] = x0 - alpha;
       diag[j] = alpha;
     }
     __syncthreads();
+    const T tau = sh_tau;
     for (int c = j + 1 + warp; c < n; c += nwarps) {
       T* cc = W + (int64_t)c * s;
       T d = T(0);

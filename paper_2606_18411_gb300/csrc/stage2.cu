@@ -230,11 +230,12 @@ void launch_reduce_partials(int n, int splits, const double* part, double* out, 
 __device__ __forceinline__ bool chol_block(int n, double* __restrict__ G) {
   const int tid = threadIdx.x;
   const int64_t nn = (int64_t)n * n;
-  __shared__ double piv;
+  __shared__ double piv, ipiv;
   for (int k = 0; k < n; ++k) {
     if (tid == 0) {
       const double d = G[(int64_t)k * n + k];
       piv = (d > 0.0 && isfinite(d)) ? sqrt(d) : -1.0;
+      ipiv = piv > 0.0 ? 1.0 / piv : 0.0;
       if (piv > 0.0) G[(int64_t)k * n + k] = piv;
     }
     __syncthreads();
@@ -243,7 +244,7 @@ __device__ __forceinline__ bool chol_block(int n, double* __restrict__ G) {
       __syncthreads();
       return false;
     }
-    const double ip = 1.0 / p;
+    const double ip = ipiv;
     for (int j = k + 1 + tid; j < n; j += blockDim.x) G[(int64_t)j * n + k] *= ip;   // row k
     __syncthreads();
     // trailing update G[i][j] -= R[k][i] R[k][j], k < i <= j: lanes over
@@ -276,16 +277,19 @@ constexpr int kCholSmemN = 160;
 __global__ void __launch_bounds__(1024) k_chol_smem(int n, double* __restrict__ G, Ctl* ctl, int level) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ double S[];   // S[j n + i] = G[i][j], i <= j
-  __shared__ double piv;
+  __shared__ double piv, ipiv;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int64_t nn = (int64_t)n * n;
   for (int64_t e = tid; e < nn; e += blockDim.x) S[e] = G[e];
   __syncthreads();
   bool ok = true;
   for (int k = 0; k < n; ++k) {
+    // one thread forms the pivot and its reciprocal: the FP64 sqrt and division are
+    // long sequences on a 1/64-rate pipe, not to be repeated by every warp
     if (tid == 0) {
       const double d = S[(int64_t)k * n + k];
       piv = (d > 0.0 && isfinite(d)) ? sqrt(d) : -1.0;
+      ipiv = piv > 0.0 ? 1.0 / piv : 0.0;
     }
     __syncthreads();
     const double p = piv;
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(1024) k_chol_smem(int n, double* __restrict__ 
       ok = false;
       break;
     }
-    const double ip = 1.0 / p;
+    const double ip = ipiv;
     for (int j = k + 1 + tid; j < n; j += blockDim.x) {
       const double r = S[(int64_t)j * n + k] * ip;
       S[(int64_t)j * n + k] = r;
