@@ -257,13 +257,13 @@ void enqueue_stage2(const Plan& p, void* ws, const double* A, int64_t lda, doubl
   if (emu)
     launch(SG_TRSM, lvl, st, [&] {
       launch_trsm_oz(p.m, p.n, A, lda, RsT, rinv, at<uint32_t>(ws, p.off_tcole), at<unsigned char>(ws, p.off_trd), Q,
-                     ldq, ctl, lvl, st);
+                     ldq, ctl, lvl, st, colhi);
     });
   else
     launch(SG_TRSM, lvl, st, [&] { launch_trsm(p.m, p.n, A, lda, RsT, rinv, Q, ldq, ctl, lvl, st); });
   double* E = at<double>(ws, p.off_e);
   if (emu) {
-    launch(SG_SYRK, lvl, st, [&] { launch_syrk_oz(p.m, p.n, Q, ldq, p.oz, colhi, ozpart, Rc, ctl, lvl, st); });
+    launch(SG_SYRK, lvl, st, [&] { launch_syrk_oz(p.m, p.n, Q, ldq, p.oz, colhi, ozpart, Rc, ctl, lvl, st, true); });
   } else {
     launch(SG_SYRK, lvl, st, [&] { launch_syrk(p.m, p.n, Q, ldq, p.splits, Gpart, ctl, lvl, st); });
     launch(SG_GREDUCE, lvl, st, [&] { launch_reduce_partials(p.n, p.splits, Gpart, Rc, ctl, lvl, st); });
@@ -276,10 +276,10 @@ void enqueue_stage2(const Plan& p, void* ws, const double* A, int64_t lda, doubl
   else
     launch(SG_FINALIZE, lvl, st, [&] {
       launch_finalize_oz(p.m, p.n, Q, ldq, XT, at<uint32_t>(ws, p.off_oze), at<unsigned char>(ws, p.off_ozx), ctl,
-                         lvl, st);
+                         lvl, st, check ? colhi : nullptr);
     });
   if (check && emu) {
-    launch(SG_CHECK, lvl, st, [&] { launch_syrk_oz(p.m, p.n, Q, ldq, p.oz, colhi, ozpart, E, ctl, lvl, st); });
+    launch(SG_CHECK, lvl, st, [&] { launch_syrk_oz(p.m, p.n, Q, ldq, p.oz, colhi, ozpart, E, ctl, lvl, st, true); });
   } else if (check) {
     launch(SG_CHECK, lvl, st, [&] { launch_syrk(p.m, p.n, Q, ldq, p.splits, Gpart, ctl, lvl, st); });
     launch(SG_EREDUCE, lvl, st, [&] { launch_reduce_partials(p.n, p.splits, Gpart, E, ctl, lvl, st); });

@@ -364,12 +364,12 @@ void enqueue_oz(const mrcqr_batched_plan_s& pl, int kind, int level, int i, cuda
       launch_sketch_oz(P.m, P.n, P.s, P.A, P.lda, P.idx, P.tab, z.seed, z.kp, z.colhi, z.part, P.y, P.ctl, level, st);
       break;
     case K_OZ_STAGE2A:
-      launch_trsm_oz(P.m, P.n, P.A, P.lda, P.rst, P.rinv, z.tcole, z.trd, P.Q, P.ldq, P.ctl, level, st);
-      launch_syrk_oz(P.m, P.n, P.Q, P.ldq, z.sp, z.colhi, z.part, P.rc, P.ctl, level, st);
+      launch_trsm_oz(P.m, P.n, P.A, P.lda, P.rst, P.rinv, z.tcole, z.trd, P.Q, P.ldq, P.ctl, level, st, z.colhi);
+      launch_syrk_oz(P.m, P.n, P.Q, P.ldq, z.sp, z.colhi, z.part, P.rc, P.ctl, level, st, true);
       break;
     case K_OZ_STAGE2B:
-      launch_finalize_oz(P.m, P.n, P.Q, P.ldq, P.xt, z.oze, z.ozx, P.ctl, level, st);
-      if (P.check) launch_syrk_oz(P.m, P.n, P.Q, P.ldq, z.sp, z.colhi, z.part, P.e, P.ctl, level, st);
+      launch_finalize_oz(P.m, P.n, P.Q, P.ldq, P.xt, z.oze, z.ozx, P.ctl, level, st, P.check ? z.colhi : nullptr);
+      if (P.check) launch_syrk_oz(P.m, P.n, P.Q, P.ldq, z.sp, z.colhi, z.part, P.e, P.ctl, level, st, true);
       break;
   }
 }

@@ -121,8 +121,10 @@ struct SyrkOzPlan {     // emulated-FP64 Gram: output tiles (128 x 64) and row s
 SyrkOzPlan syrk_oz_plan(int64_t m, int n);
 size_t syrk_oz_part_bytes(const SyrkOzPlan& P);
 size_t syrk_oz_colhi_bytes(int n);
+// colHi holds the column maxima of |W| (high words); colhi_ready: the producer of W
+// (launch_trsm_oz / launch_finalize_oz given colHiOut = colHi) already wrote them.
 void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOzPlan& P, uint32_t* colHi,
-                    long long* part, double* out, Ctl* ctl, int level, cudaStream_t st);
+                    long long* part, double* out, Ctl* ctl, int level, cudaStream_t st, bool colhi_ready = false);
 struct SketchOzPlan {   // emulated-FP64 sketch: 128-column blocks of A x 64-row sample tiles x row slabs
   int mblocks, ntiles, slabs;
   int64_t rows_per_slab;
@@ -131,13 +133,14 @@ SketchOzPlan sketch_oz_plan(int64_t m, int n, int s);
 size_t trsm_oz_rd_bytes(int n);
 size_t trsm_oz_cole_bytes(int n);
 void launch_trsm_oz(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv,
-                    uint32_t* colE, unsigned char* Rd, double* W, int64_t ldw, Ctl* ctl, int level, cudaStream_t st);
+                    uint32_t* colE, unsigned char* Rd, double* W, int64_t ldw, Ctl* ctl, int level, cudaStream_t st,
+                    uint32_t* colHiOut = nullptr);
 size_t sketch_oz_part_bytes(const SketchOzPlan& P);
 void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, const uint32_t* idx, const double* tab,
                       uint64_t seed, const SketchOzPlan& P, uint32_t* colHi, long long* part, double* Y, Ctl* ctl,
                       int level, cudaStream_t st);
 void launch_finalize_oz(int64_t m, int n, double* Q, int64_t ldq, const double* XT, uint32_t* colE,
-                        unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st);
+                        unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st, uint32_t* colHiOut = nullptr);
 
 // --- learned selector (selector.cu) --------------------------------------------
 int selector_num_params();

@@ -243,9 +243,12 @@ __device__ __forceinline__ double nan64() { return __longlong_as_double(0x7FF800
 // [32kc, 32kc+32) of digit b.  XT[k][j] = X[k][j], row stride npad.
 __global__ void __launch_bounds__(512) k_oz_prep_x(int n, int npad, int n64, const double* __restrict__ XT,
                                                    uint32_t* __restrict__ colE, unsigned char* __restrict__ Xs,
-                                                   const Ctl* ctl, int level) {
+                                                   uint32_t* __restrict__ colHiOut, int nhi, const Ctl* ctl,
+                                                   int level) {
   if (ctl && (level_inactive(ctl, level) || ctl->lvl_status != 0)) return;
   const int j = blockIdx.x;   // column, < n64
+  if (colHiOut && j == 0)     // the finalize folds the column maxima of Q into these
+    for (int i = threadIdx.x; i < nhi; i += blockDim.x) colHiOut[i] = 0u;
   __shared__ uint32_t red[32];
   uint32_t mx = 0u;
   for (int k = threadIdx.x; k < n64; k += blockDim.x)
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(512) k_oz_prep_x(int n, int npad, int n64, con
 // X upper triangular: tile t needs K chunks 0 .. 2t + 1.
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_finalize_oz(int64_t m, int n, int n64, double* __restrict__ Q, int64_t ldq, const uint32_t* __restrict__ colE,
-                  const unsigned char* __restrict__ Xs, Ctl* ctl, int level) {
+                  const unsigned char* __restrict__ Xs, uint32_t* __restrict__ colHiOut, Ctl* ctl, int level) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = oz_smem(smem_raw);
@@ -289,9 +292,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ uint32_t rowE[kM];
   __shared__ uint32_t redE[4][kM];
+  __shared__ uint32_t cmax[512];   // column maxima of |Q| (high words) over this CTA's rows
   OzPipe P = oz_begin(&tmem_slot, &mma_bar);
   const int tid = threadIdx.x, lane = tid & 31;
   const int ntiles = n64 / kN, nkc = n64 / kK;
+  for (int j = tid; j < n64; j += kOzThreads) cmax[j] = 0u;
   bool abort = false;
   const int64_t nblocks = (m + kM - 1) / kM;
 
@@ -344,24 +349,36 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         abort = true;
         break;
       }
-      // write Q[:, 64t + 16g + c] for this thread's row
+      // write Q[:, 64t + 16g + c] for this thread's row (lane c keeps the warp's maximum of column c)
       const int rr = P.q * 32 + lane;
-      if (r0 + rr < m) {
-        const int scale_r = (int)rowE[rr] - oz::kScaleBias;
+      const bool rlive = r0 + rr < m;
+      const int scale_r = (int)rowE[rr] - oz::kScaleBias;
+      uint32_t mine = 0u;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int j = t * kN + P.g * 16 + c;
-          if (j < n) {
-            const uint32_t ce = colE[j];
-            Q[r0 + rr + (int64_t)j * ldq] = (rowE[rr] == 2047u || ce == 2047u)   // non-finite operands
-                                                ? nan64()
-                                                : oz::i128_to_double(hi[c], lo[c], scale_r + (int)ce);
-          }
+      for (int c = 0; c < 16; ++c) {
+        const int j = t * kN + P.g * 16 + c;
+        uint32_t h = 0u;
+        if (rlive && j < n) {
+          const uint32_t ce = colE[j];
+          const double qv = (rowE[rr] == 2047u || ce == 2047u)   // non-finite operands
+                                ? nan64()
+                                : oz::i128_to_double(hi[c], lo[c], scale_r + (int)ce);
+          Q[r0 + rr + (int64_t)j * ldq] = qv;
+          h = (uint32_t)__double2hiint(qv) & 0x7FFFFFFFu;
+        }
+        if (colHiOut) {
+          h = __reduce_max_sync(0xffffffffu, h);
+          if (lane == c) mine = h;
         }
       }
+      if (mine) atomicMax(&cmax[t * kN + P.g * 16 + lane], mine);
       __syncthreads();
     }
   }
+  __syncthreads();
+  if (colHiOut && !abort)
+    for (int j = tid; j < n; j += kOzThreads)
+      if (cmax[j]) atomicMax(colHiOut + j, cmax[j]);
   oz_end(P, abort, ctl);
 }
 
@@ -637,9 +654,12 @@ __global__ void __launch_bounds__(256) k_oz_row_scale(int n, int npad, const dou
 // entry is not finite).  RT[k][c] = R[k][c], row stride npad.
 __global__ void __launch_bounds__(256) k_oz_prep_r(int n, int npad, int nkc, const double* __restrict__ RT,
                                                    const int* __restrict__ eR, int* __restrict__ colE,
-                                                   unsigned char* __restrict__ Rd, const Ctl* ctl, int level) {
+                                                   unsigned char* __restrict__ Rd, uint32_t* __restrict__ colHiOut,
+                                                   int nhi, const Ctl* ctl, int level) {
   if (ctl && (level_inactive(ctl, level) || ctl->lvl_status != 0)) return;
   const int c = blockIdx.x;   // column, < 16 ceil(n / 16)
+  if (colHiOut && c == 0)     // the TRSM folds the column maxima of W into these
+    for (int i = threadIdx.x; i < nhi; i += blockDim.x) colHiOut[i] = 0u;
   const int J = c / kTB, kend = kTB * J;
   __shared__ int red[8];
   __shared__ int bad[8];
@@ -680,7 +700,8 @@ __global__ void __launch_bounds__(256) k_oz_prep_r(int n, int npad, int nkc, con
 __global__ void __launch_bounds__(kTThreads, 2)
     k_trsm_oz(int64_t m, int n, const double* __restrict__ A, int64_t lda, const double* __restrict__ RT,
               const double* __restrict__ rinv, const int* __restrict__ eR, const int* __restrict__ colE,
-              const unsigned char* __restrict__ Rd, int nkc, double* W, int64_t ldw, Ctl* ctl, int level) {
+              const unsigned char* __restrict__ Rd, int nkc, double* W, int64_t ldw, uint32_t* __restrict__ colHiOut,
+              Ctl* ctl, int level) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = oz_smem(smem_raw);
@@ -693,6 +714,7 @@ __global__ void __launch_bounds__(kTThreads, 2)
   __shared__ int eRs[512];             // e_k
   __shared__ double Rd16[kTB][kTB + 1];   // diagonal block R_JJ
   __shared__ double rinv16[kTB];
+  __shared__ uint32_t cmax[512];          // column maxima of |W| (high words) over this CTA's rows
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tc::tmem_alloc(&tmem_slot, 128);
   if (tid == 0) {
@@ -711,7 +733,10 @@ __global__ void __launch_bounds__(kTThreads, 2)
   const int64_t nblocks = (m + kM - 1) / kM;
   const int pr = tid & (kM - 1), ph = tid >> 7;   // producer role: row pr, column pairs ph + 2 i
   constexpr int kNoEntry = -100000, kNonfinite = 100000;
-  for (int k = tid; k < n; k += kTThreads) eRs[k] = eR[k];
+  for (int k = tid; k < n; k += kTThreads) {
+    eRs[k] = eR[k];
+    cmax[k] = 0u;
+  }
 
   for (int64_t rb = blockIdx.x; rb < nblocks && !abort; rb += gridDim.x) {
     const int64_t r0 = rb * kM;
@@ -839,6 +864,16 @@ __global__ void __launch_bounds__(kTThreads, 2)
             }
         }
         rowX[tid] = mx;
+        if (colHiOut) {   // lane c keeps the warp's maximum of column c0 + c
+          uint32_t mine = 0u;
+#pragma unroll
+          for (int c = 0; c < kTB; ++c) {
+            const uint32_t h = (r0 + tid < m && c0 + c < n) ? ((uint32_t)__double2hiint(t[c]) & 0x7FFFFFFFu) : 0u;
+            const uint32_t wm = __reduce_max_sync(0xffffffffu, h);
+            if (lane == c) mine = wm;
+          }
+          if (mine) atomicMax(&cmax[c0 + lane], mine);
+        }
       }
       __syncthreads();
     }
@@ -846,6 +881,9 @@ __global__ void __launch_bounds__(kTThreads, 2)
   if (abort && tid == 0) raise_level_status(ctl, ST_TIMEOUT);
   tc::fence_before();
   __syncthreads();
+  if (colHiOut && !abort)
+    for (int k = tid; k < n; k += kTThreads)
+      if (cmax[k]) atomicMax(colHiOut + k, cmax[k]);
   if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
 
@@ -909,14 +947,15 @@ void launch_col_hi(int64_t m, int n, const double* X, int64_t ldx, uint32_t* col
 }  // namespace
 
 void launch_finalize_oz(int64_t m, int n, double* Q, int64_t ldq, const double* XT, uint32_t* colE,
-                        unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st) {
+                        unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st, uint32_t* colHiOut) {
   const int npad = (n + 31) / 32 * 32;
   const int n64 = (n + kN - 1) / kN * kN;
-  { ::mrcqr::note_launch(); k_oz_prep_x<<<n64, 512, 0, st>>>(n, npad, n64, XT, colE, Xs, ctl, level); }
+  const int nhi = (int)(syrk_oz_colhi_bytes(n) / sizeof(uint32_t));
+  { ::mrcqr::note_launch(); k_oz_prep_x<<<n64, 512, 0, st>>>(n, npad, n64, XT, colE, Xs, colHiOut, nhi, ctl, level); }
   set_smem(k_finalize_oz);
   const int64_t nblocks = (m + kM - 1) / kM;
   const unsigned grid = (unsigned)(nblocks < num_sms() ? nblocks : num_sms());
-  { ::mrcqr::note_launch(); k_finalize_oz<<<grid, kOzThreads, kSmem, st>>>(m, n, n64, Q, ldq, colE, Xs, ctl, level); }
+  { ::mrcqr::note_launch(); k_finalize_oz<<<grid, kOzThreads, kSmem, st>>>(m, n, n64, Q, ldq, colE, Xs, colHiOut, ctl, level); }
 }
 
 SyrkOzPlan syrk_oz_plan(int64_t m, int n) {
@@ -939,8 +978,8 @@ SyrkOzPlan syrk_oz_plan(int64_t m, int n) {
 size_t syrk_oz_part_bytes(const SyrkOzPlan& P) { return sizeof(long long) * kPartElems * (size_t)P.ntiles * P.slabs; }
 
 void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOzPlan& P, uint32_t* colHi,
-                    long long* part, double* out, Ctl* ctl, int level, cudaStream_t st) {
-  launch_col_hi(m, n, W, ldw, colHi, ctl, level, st);
+                    long long* part, double* out, Ctl* ctl, int level, cudaStream_t st, bool colhi_ready) {
+  if (!colhi_ready) launch_col_hi(m, n, W, ldw, colHi, ctl, level, st);
   set_smem(k_syrk_oz);
   const int nitems = P.ntiles * P.slabs;
   { ::mrcqr::note_launch(); k_syrk_oz<<<nitems < num_sms() ? nitems : num_sms(), kOzThreads, kSmem, st>>>(m, n, W, ldw, colHi, P, part, ctl,
@@ -981,19 +1020,21 @@ size_t trsm_oz_rd_bytes(int n) {
 size_t trsm_oz_cole_bytes(int n) { return 2 * sizeof(int) * (size_t)((n + kTB - 1) / kTB * kTB); }
 
 void launch_trsm_oz(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv,
-                    uint32_t* colE_ws, unsigned char* Rd, double* W, int64_t ldw, Ctl* ctl, int level, cudaStream_t st) {
+                    uint32_t* colE_ws, unsigned char* Rd, double* W, int64_t ldw, Ctl* ctl, int level, cudaStream_t st,
+                    uint32_t* colHiOut) {
   const int npad = (n + 31) / 32 * 32;
   const int nkc = (n + kK - 1) / kK;
   const int n16 = (n + kTB - 1) / kTB * kTB;
   int* colE = reinterpret_cast<int*>(colE_ws);
   int* eR = colE + n16;
   { ::mrcqr::note_launch(); k_oz_row_scale<<<(n + 7) / 8, 256, 0, st>>>(n, npad, RT, eR, ctl, level); }
-  { ::mrcqr::note_launch(); k_oz_prep_r<<<n16, 256, 0, st>>>(n, npad, nkc, RT, eR, colE, Rd, ctl, level); }
+  const int nhi = (int)(syrk_oz_colhi_bytes(n) / sizeof(uint32_t));
+  { ::mrcqr::note_launch(); k_oz_prep_r<<<n16, 256, 0, st>>>(n, npad, nkc, RT, eR, colE, Rd, colHiOut, nhi, ctl, level); }
   cudaFuncSetAttribute(k_trsm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
   const int64_t nblocks = (m + kM - 1) / kM;
   const int64_t slots = 2 * (int64_t)num_sms();
   { ::mrcqr::note_launch(); k_trsm_oz<<<(unsigned)(nblocks < slots ? nblocks : slots), kTThreads, kTSmem, st>>>(m, n, A, lda, RT, rinv, eR,
-                                                                                       colE, Rd, nkc, W, ldw, ctl, level); }
+                                                                                       colE, Rd, nkc, W, ldw, colHiOut, ctl, level); }
 }
 
 }  // namespace mrcqr
