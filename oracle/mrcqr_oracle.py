@@ -22,10 +22,12 @@ Steps, in the paper's order and notation:
     F_kj = sqrt(2/m) * c_k * cos(pi * k * (2j + 1) / (2m)),
     c_0 = 1/sqrt(2), c_k = 1 otherwise,
   built here as an explicit dense matrix, row by row, with the phase reduced
-  exactly as an integer r = k (2j + 1) mod 4m.  (The paper's transform is the
-  real part of a column-wise real FFT with scale sqrt(c/m); the orthonormal
-  DCT-II with scale sqrt(m/c) is the reading used by this project.  A scalar
-  scale of the sketch cancels in R_s^{-1} ... R, see ``mrcqr``.)
+  exactly as an integer r = k (2j + 1) mod 4m.  The paper's own transform,
+  the real part of a column-wise real FFT over c of the floor(m/2) + 1 bins
+  with scale sqrt(c/m) (and the variant that also keeps the imaginary parts),
+  is here too (``rfft_sketch``, ``sample_bins``); the orthonormal DCT-II with
+  scale sqrt(m/c) is the library's default.  A scalar scale of the sketch
+  cancels in R_s^{-1} ... R, see ``mrcqr``.
 * Algorithm 2 step 5 (SketchQR): Householder QR of Y, normalised to
   diag(R_s) > 0.
 * Algorithm 2 steps 6-8 (Stage 2, Algorithm 1 on A R_s^{-1}, Sec. II-A):
@@ -210,6 +212,88 @@ def sketch_emulated(A: np.ndarray, idx: np.ndarray, signs: np.ndarray, prec: str
 
 
 # ---------------------------------------------------------------------------
+# The paper's own transform (Algorithm 2 as printed, Sec. II-A): the real FFT
+# of each sign-flipped column, c of its floor(m/2) + 1 distinct bins (a real
+# column's spectrum is Hermitian), the real parts scaled by sqrt(c/m); the
+# variant of Sec. II-A that keeps the imaginary parts as well stacks them
+# below, a 2c x n sketch.  Bins are 0-based here (the paper's bin k + 1).
+
+TRANSFORMS = ("dct", "rfft", "rfft_reim")
+
+
+def sample_bins(m: int, c: int, seed: int) -> np.ndarray:
+    """The sampled bins of the real-FFT sketch (Algorithm 2 step 1): c
+    distinct values of {0..floor(m/2)}, uniform without replacement, by the
+    Floyd draw of ``sample_rows`` over that population, sorted ascending."""
+    return sample_rows(m // 2 + 1, c, seed)
+
+
+def dft_phase(k: int, m: int) -> np.ndarray:
+    """k j mod m for j < m, exact in integers: row k of the DFT is
+    exp(-2 pi i (k j mod m) / m)."""
+    j = np.arange(m, dtype=np.int64)
+    return (np.int64(k) * j) % m
+
+
+def rfft_re_row(k: int, m: int) -> np.ndarray:
+    """Real part of row k of the unnormalised DFT: cos(2 pi k j / m)."""
+    return np.cos(2.0 * np.pi * dft_phase(k, m).astype(np.float64) / m)
+
+
+def rfft_im_row(k: int, m: int) -> np.ndarray:
+    """Imaginary part of row k of the unnormalised DFT: -sin(2 pi k j / m)."""
+    return -np.sin(2.0 * np.pi * dft_phase(k, m).astype(np.float64) / m)
+
+
+def rfft_rows(bins: np.ndarray, imag: bool = False):
+    """The sketch's rows in order: (part, bin) for the Re rows of the bins,
+    then, with ``imag``, their Im rows."""
+    rows = [("re", int(k)) for k in bins]
+    if imag:
+        rows += [("im", int(k)) for k in bins]
+    return rows
+
+
+def rfft_sketch_row(part: str, k: int, m: int, c: int, signs: np.ndarray) -> np.ndarray:
+    """One row of S = sqrt(c/m) P [Re F; Im F] D (F the unnormalised DFT)."""
+    row = rfft_re_row(k, m) if part == "re" else rfft_im_row(k, m)
+    return math.sqrt(c / m) * row * signs
+
+
+def rfft_sketch(A: np.ndarray, bins: np.ndarray, signs: np.ndarray, imag: bool = False,
+                rows_per_block: int = 16) -> np.ndarray:
+    """Y = S A in FP64 (Algorithm 2 steps 2-4 with the real FFT), S built
+    explicitly row by row as ``sketch`` does for the DCT."""
+    m, n = A.shape
+    c = len(bins)
+    rows = rfft_rows(bins, imag)
+    Y = np.empty((len(rows), n))
+    for b in range(0, len(rows), rows_per_block):
+        blk = rows[b:b + rows_per_block]
+        Sb = np.stack([rfft_sketch_row(part, k, m, c, signs) for part, k in blk])
+        Y[b:b + len(blk)] = Sb @ A
+    return Y
+
+
+def rfft_sketch_emulated(A: np.ndarray, bins: np.ndarray, signs: np.ndarray, prec: str,
+                         imag: bool = False) -> np.ndarray:
+    """Error model of the precision-p real-FFT sketch, as ``sketch_emulated``:
+    fl_p(D A 2^e) and fl_p(cos / sin entries), products in FP64, the scale
+    sqrt(c/m) 2^-e applied last."""
+    bits = SIGNIFICAND_BITS[prec]
+    m, n = A.shape
+    c = len(bins)
+    e = column_scale_exponents(A)
+    X = round_significand(signs[:, None] * np.ldexp(A, e[None, :]), bits).reshape(m, n)
+    rows = rfft_rows(bins, imag)
+    Y = np.empty((len(rows), n))
+    for i, (part, k) in enumerate(rows):
+        row = round_significand(rfft_re_row(k, m) if part == "re" else rfft_im_row(k, m), bits)
+        Y[i] = row @ X
+    return np.ldexp(Y * math.sqrt(c / m), -e[None, :])
+
+
+# ---------------------------------------------------------------------------
 # Small dense factorizations (Algorithm 1 and Algorithm 2 steps 5-9)
 
 def householder_qr(Y: np.ndarray, want_q: bool = False, dtype=np.float64):
@@ -344,20 +428,32 @@ def sketch_rows_for(n: int, s_factor: int = 2) -> int:
 
 
 def mrcqr(A: np.ndarray, seed: int = 0, prec: str = "fp64", s: int | None = None,
-          sketch_scale: float = 1.0) -> MRCQRResult:
+          sketch_scale: float = 1.0, transform: str = "dct") -> MRCQRResult:
     """Algorithm 2 with sketch precision ``prec`` (fp64: the exact FP64 sketch;
     otherwise the fl_p error model of ``sketch_emulated`` and a sketch QR in
-    FP32 as the paper does for half precision, Sec. II-A)."""
+    FP32 as the paper does for half precision, Sec. II-A).  ``transform``:
+    "dct" (s sampled DCT-II rows), "rfft" (Re of s sampled real-FFT bins) or
+    "rfft_reim" (Re and Im of s bins, a 2s x n sketch)."""
     m, n = A.shape
     if s is None:
         s = sketch_rows_for(n)
     signs = rademacher(m, seed)
-    idx = sample_rows(m, s, seed)
+    if transform == "dct":
+        idx = sample_rows(m, s, seed)
+        exact = lambda: sketch(A, idx, signs)
+        emulated = lambda: sketch_emulated(A, idx, signs, prec)
+    elif transform in ("rfft", "rfft_reim"):
+        idx = sample_bins(m, s, seed)
+        imag = transform == "rfft_reim"
+        exact = lambda: rfft_sketch(A, idx, signs, imag)
+        emulated = lambda: rfft_sketch_emulated(A, idx, signs, prec, imag)
+    else:
+        raise ValueError(f"unknown transform {transform!r}")
     if prec == "fp64":
-        Y = sketch(A, idx, signs)
+        Y = exact()
         Rs = householder_qr(Y * sketch_scale)
     else:
-        Y = sketch_emulated(A, idx, signs, prec)
+        Y = emulated()
         Rs = householder_qr((Y * sketch_scale).astype(np.float32), dtype=np.float32)
     W = trsm_right_upper(A, Rs)
     G = W.T @ W

@@ -107,6 +107,93 @@ def test_sketch_full_sample_preserves_gram():
     np.testing.assert_allclose(Y.T @ Y, A.T @ A, atol=1e-12)
 
 
+# --- The paper's real-FFT sketch (Algorithm 2 as printed, Sec. II-A) ----------
+
+@pytest.mark.parametrize("m", [1, 2, 7, 64, 1000, 1025])
+def test_rfft_rows_match_library(m):
+    # Re and Im of every row of the unnormalised DFT against numpy's real FFT
+    x = inputs.gaussian(m, 3, seed=m)
+    ref = np.fft.rfft(x, axis=0)
+    assert ref.shape[0] == m // 2 + 1
+    Re = np.stack([O.rfft_re_row(k, m) for k in range(m // 2 + 1)])
+    Im = np.stack([O.rfft_im_row(k, m) for k in range(m // 2 + 1)])
+    tol = 1e-13 * np.abs(x).sum(axis=0).max()
+    np.testing.assert_allclose(Re @ x, ref.real, rtol=0, atol=tol)
+    np.testing.assert_allclose(Im @ x, ref.imag, rtol=0, atol=tol)
+
+
+@pytest.mark.parametrize("m,c", [(1, 1), (2, 2), (7, 4), (64, 33), (4096, 150), (1 << 17, 150), (3001, 1501)])
+def test_sample_bins_valid(m, c):
+    # c distinct bins of the floor(m/2) + 1 that a real column has (Hermitian symmetry)
+    b = O.sample_bins(m, c, seed=5)
+    assert b.shape == (c,)
+    assert np.all(np.diff(b) > 0) and b[0] >= 0 and b[-1] <= m // 2
+    if c == m // 2 + 1:
+        assert np.array_equal(b, np.arange(m // 2 + 1))
+
+
+def test_sample_bins_uniform_subsets():
+    # m = 8 has 5 distinct bins; each 2-subset of them is drawn with probability 1/10
+    m, c, trials = 8, 2, 5000
+    counts = {}
+    for seed in range(trials):
+        key = tuple(O.sample_bins(m, c, seed).tolist())
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == math.comb(5, 2) and all(max(k) <= 4 for k in counts)
+    exp = trials / math.comb(5, 2)
+    chi2 = sum((v - exp) ** 2 / exp for v in counts.values())
+    assert chi2 < 30.0          # 9 dof; p ~ 4e-4
+
+
+@pytest.mark.parametrize("m,n", [(256, 8), (301, 5), (1024, 16)])
+def test_rfft_sketch_equals_fast_transform(m, n):
+    # Y = sqrt(c/m) Re(FFT(D A))[bins] (and the Im rows below), independently with numpy's real FFT
+    c = 3 * n
+    A = inputs.gaussian(m, n, seed=1)
+    d = O.rademacher(m, 9)
+    bins = O.sample_bins(m, c, 9)
+    F = np.fft.rfft(d[:, None] * A, axis=0)[bins]
+    ref = math.sqrt(c / m) * np.concatenate([F.real, F.imag])
+    tol = 1e-13 * np.abs(ref).max()
+    np.testing.assert_allclose(O.rfft_sketch(A, bins, d, imag=True), ref, rtol=0, atol=tol)
+    np.testing.assert_allclose(O.rfft_sketch(A, bins, d), ref[:c], rtol=0, atol=tol)
+
+
+@pytest.mark.parametrize("m", [64, 65])
+def test_rfft_all_bins_parseval(m):
+    # Parseval for real columns a, b with spectra X, Y: sum_k w_k (Re X_k Re Y_k + Im X_k Im Y_k) = m a^T b
+    # over the floor(m/2) + 1 bins, w_k = 2 except w_0 = 1 and (m even) w_{m/2} = 1.  With every bin
+    # sampled (c of them), the scale sqrt(c/m) and D^2 = I: Y^T W Y = c A^T A.
+    n = 5
+    c = m // 2 + 1
+    A = inputs.gaussian(m, n, seed=3)
+    d = O.rademacher(m, 4)
+    bins = O.sample_bins(m, c, 4)
+    Y = O.rfft_sketch(A, bins, d, imag=True)
+    w = np.full(c, 2.0)
+    w[0] = 1.0
+    if m % 2 == 0:
+        w[-1] = 1.0
+    Wt = np.concatenate([w, w])
+    G = c * (A.T @ A)
+    np.testing.assert_allclose(Y.T @ (Wt[:, None] * Y), G, rtol=0, atol=1e-12 * np.abs(G).max())
+    # the Im rows of bin 0 (and bin m/2 for even m) vanish
+    assert np.all(Y[c] == 0)
+    if m % 2 == 0:
+        assert np.abs(Y[2 * c - 1]).max() <= 1e-12 * np.abs(Y).max()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16", 5e-3), ("bf16", 5e-3), ("fp32", 1e-5)])
+def test_emulated_rfft_sketch_within_precision_tolerance(prec, tol):
+    m, n = 4096, 32
+    A = inputs.make_matrix(m, n, 1e8, seed=4)
+    d, bins = O.rademacher(m, 0), O.sample_bins(m, 3 * n, 0)
+    Y = O.rfft_sketch(A, bins, d, imag=True)
+    Yp = O.rfft_sketch_emulated(A, bins, d, prec, imag=True)
+    err = np.linalg.norm(Yp - Y) / np.linalg.norm(Y)
+    assert O.UNIT_ROUNDOFF[prec] / 100 < err < tol
+
+
 # --- fl_p: rounding to the sketch precision (Algorithm 2 step 2) --------------
 
 def test_round_significand_fp16_fp32_match_casts():
@@ -280,6 +367,23 @@ def test_mrcqr_invariant_to_sketch_scale():
     tol = 100 * 1e6 * O.U_FP64
     assert np.abs(r2.Q - r1.Q).max() < tol
     assert np.linalg.norm(r2.R - r1.R) / np.linalg.norm(r1.R) < tol
+
+
+@pytest.mark.parametrize("transform,prec,kappa", [("rfft", "fp64", 1e0), ("rfft", "fp64", 1e16), ("rfft", "fp32", 1e8),
+                                                  ("rfft_reim", "fp64", 1e8), ("rfft_reim", "fp16", 1e4)])
+def test_mrcqr_paper_transform_stability_experiment_shape(transform, prec, kappa):
+    # Sec. IV-B's shape (m = 2^17, n = 50) with the paper's sketch: c = 3n real-FFT bins (Sec. II-A)
+    m, n = 1 << 17, 50
+    A, U, sig, V = inputs.make_matrix(m, n, kappa, seed=21, return_factors=True)
+    res = O.mrcqr(A, seed=0, prec=prec, s=3 * n, transform=transform)
+    assert res.Y.shape == ((6 if transform == "rfft_reim" else 3) * n, n)
+    assert O.orthogonality_error(res.Q)[0] <= 1e-13
+    assert O.residual_error(A, res.Q, res.R)[0] <= 1e-13
+    assert np.all(np.diag(res.R) > 0)
+    if kappa <= 1e8:   # R against the exact R of A = U (Sigma V^T)
+        _, R0 = np.linalg.qr(sig[:, None] * V.T)
+        R0 = R0 * np.sign(np.diag(R0))[:, None]
+        assert np.linalg.norm(res.R - R0) / np.linalg.norm(R0) < 100 * kappa * O.U_FP64 * n
 
 
 @pytest.mark.parametrize("prec,kappa", [("fp16", 1e2), ("fp16", 1e4), ("bf16", 1e2), ("fp32", 1e4),
