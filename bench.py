@@ -493,7 +493,10 @@ def run_sweep(args):
     error shows) and CholQR2.  Per run: status, ||I - Q^T Q||_F from the
     device judge, the residual of the leading 8-column block in double-double
     (oracle), and for MRCQR the sketch error on sampled entries against the
-    oracle's dense FP64 sketch rows.  Prints one JSON line (rank 0)."""
+    oracle's dense FP64 sketch rows.  --transform rfft (or rfft_reim) with
+    --s-factor 3 --m 131072 --n 50 runs the experiment's own configuration:
+    the paper's real-FFT sketch of c = 3n bins on m = 2^17, n = 50.  Prints one
+    JSON line (rank 0)."""
     import numpy as np
     import torch
     import oracle as O
@@ -507,9 +510,16 @@ def run_sweep(args):
     torch.cuda.set_device(local)
     _build.build()
     dev = torch.device("cuda", local)
-    m, n, s, seed = args.m, args.n, 2 * args.n, 0
-    idx = O.sample_rows(m, s, seed)
+    m, n, seed, tf = args.m, args.n, 0, args.transform
+    c = args.s_factor * n                   # sampled rows (DCT) or bins (real FFT)
     signs = O.rademacher(m, seed)
+    if tf == "dct":
+        row_defs = [("dct", int(k)) for k in O.sample_rows(m, c, seed)]
+        row_of = lambda part, k: O.sketch_row(k, m, c, signs)
+    else:
+        row_defs = O.rfft_rows(O.sample_bins(m, c, seed), imag=tf == "rfft_reim")
+        row_of = lambda part, k: O.rfft_sketch_row(part, k, m, c, signs)
+    s = len(row_defs)                       # rows of Y
     rng = np.random.default_rng(7)
     rows, cols = rng.choice(s, 6, replace=False), rng.choice(n, 6, replace=False)
     stats = torch.zeros(8, dtype=torch.float64, device=dev)
@@ -527,13 +537,14 @@ def run_sweep(args):
             kappa = 10.0 ** e
             A = inputs.make_matrix_device(m, n, kappa, kind=kind, seed=5000 + e, device=dev)
             Ac = A[:, cols.tolist()].cpu().numpy()
-            Yref = np.stack([O.sketch_row(int(idx[r]), m, s, signs) @ Ac for r in rows])
+            Yref = np.stack([row_of(*row_defs[r]) @ Ac for r in rows])
             Q = M.empty_colmajor(m, n, device=dev)
             R = M.empty_colmajor(n, n, device=dev)
             for prec in ("fp16", "bf16", "fp32", "fp64"):
-                Y = M.sketch(A, s, prec=prec, seed=seed).cpu().numpy()[np.ix_(rows, cols)]
+                Y = M.sketch_transform(A, c, tf, prec=prec, seed=seed).cpu().numpy()[np.ix_(rows, cols)]
                 sk = float(np.linalg.norm(Y - Yref) / np.linalg.norm(Yref))
-                M.factor_ex(A, Q, R, prec=prec, seed=seed, escalate=False, stats_device=stats)
+                M.factor_ex(A, Q, R, prec=prec, seed=seed, escalate=False, stats_device=stats, s_factor=args.s_factor,
+                            transform=tf)
                 torch.cuda.synchronize()
                 st = read_stats()
                 out.append({"spectrum": kind, "kappa": kappa, "method": f"mrcqr-{prec}", "status": st["status"],
@@ -546,8 +557,8 @@ def run_sweep(args):
             del A, Q, R, Q2, R2
             torch.cuda.empty_cache()
     line = {"metric": "stability sweep (orthogonality, residual, sketch error) of MRCQR per sketch precision and "
-                      "CholQR2", "workload": f"MRCQR m=2^{int(math.log2(m))} n={n} s={s} spectra geometric/cliff/"
-                      "clustered kappa 1e0..1e16", "runs": len(out), "wall_s": round(time.perf_counter() - t0, 1),
+                      "CholQR2", "workload": f"MRCQR m=2^{int(math.log2(m))} n={n} transform={tf} c={c} rows={s} "
+                      "spectra geometric/cliff/clustered kappa 1e0..1e16", "runs": len(out), "wall_s": round(time.perf_counter() - t0, 1),
             "results": out}
     print(json.dumps(line), flush=True)
 
@@ -609,6 +620,9 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["large", "batched", "sweep"], default="large")
+    ap.add_argument("--transform", choices=["dct", "rfft", "rfft_reim"], default="dct",
+                    help="sketch transform of the sweep workload")
+    ap.add_argument("--s-factor", type=int, default=2, help="sampled rows or bins per column (sweep workload)")
     ap.add_argument("--count", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -59,8 +59,26 @@ typedef enum {
   MRCQR_ERR_TIMEOUT = 7    /* a bounded device wait gave up (batched persistent kernels) */
 } mrcqr_status_t;
 
+/* Sketch transform F of Algorithm 2 (Sec. II-A).
+ *  DCT:       c rows k of the orthonormal DCT-II, sampled from {0..m-1}, scale sqrt(m/c):
+ *             Y_i = sqrt(2/c) c_k sum_j cos(pi k (2j+1) / (2m)) d_j A_j, c_0 = 1/sqrt(2), else 1.
+ *  RFFT:      the paper's transform: c bins k of the real FFT, sampled from the
+ *             floor(m/2) + 1 distinct bins of a real column, real parts, scale sqrt(c/m):
+ *             Y_i = sqrt(c/m) sum_j cos(2 pi k j / m) d_j A_j (unnormalised DFT).
+ *  RFFT_REIM: as RFFT, with the imaginary parts -sqrt(c/m) sum_j sin(2 pi k j / m) d_j A_j
+ *             of the same c bins stacked below: a 2c x n sketch.
+ * Bins and rows are 0-based (the paper's bin k + 1); a scalar scale of Y cancels in
+ * Q and R. */
+typedef enum {
+  MRCQR_TRANSFORM_DCT = 0,
+  MRCQR_TRANSFORM_RFFT = 1,
+  MRCQR_TRANSFORM_RFFT_REIM = 2
+} mrcqr_transform_t;
+
 typedef struct mrcqr_opts {
-  int32_t s_factor;   /* sketch rows s = s_factor * n (default 2; the paper uses 3, Sec. II-A) */
+  int32_t s_factor;   /* sampled rows or bins c = s_factor * n (default 2; the paper uses 3, Sec. II-A);
+                         Y has c rows, 2c for MRCQR_TRANSFORM_RFFT_REIM (at most 8192), and c is at
+                         most m (DCT) or floor(m/2) + 1 (real FFT) */
   int32_t check;      /* 1 (default): measure ||I - Q^T Q||_F on device and judge the result */
   int32_t escalate;   /* 1 (default): on failure re-run at the next precision (Sec. II-C),
                          FP16/BF16 -> FP32 -> FP64 */
@@ -75,7 +93,7 @@ typedef struct mrcqr_opts {
                             as emulated FP64 on the FP16 tensor cores (exact 8-bit digit slicing,
                             integer recombination, one final rounding; see mrcqr_trsm, mrcqr_gram
                             and mrcqr_finalize_q); 1: FP64 FMA kernels throughout */
-  int32_t reserved1;
+  int32_t transform;  /* mrcqr_transform_t, default MRCQR_TRANSFORM_DCT (0) */
 } mrcqr_opts_t;
 
 typedef struct mrcqr_stats {
@@ -178,6 +196,15 @@ int mrcqr_signs(int64_t m, uint64_t seed, double* d, mrcqr_stream_t stream);
  * ascending (DEVICE uint32[s]); 1 <= s <= min(m, 8192). */
 int mrcqr_sample_rows(int64_t m, int64_t s, uint64_t seed, uint32_t* idx, mrcqr_stream_t stream);
 
+/* Algorithm 2 step 1 for a given transform: c distinct rows (DCT, of {0..m-1})
+ * or bins (real FFT, of {0..floor(m/2)}), uniform without replacement (Floyd,
+ * the same Philox stream as mrcqr_sample_rows over that population), sorted
+ * ascending, written to idx[0..c) (DEVICE uint32).  MRCQR_TRANSFORM_RFFT_REIM
+ * also writes the Im rows of the same bins to idx[c..2c) as bin | 0x80000000.
+ * INVALID when c exceeds the population or the rows of Y exceed 8192. */
+int mrcqr_sample_transform_rows(int64_t m, int64_t c, int transform, uint64_t seed, uint32_t* idx,
+                                mrcqr_stream_t stream);
+
 /* fl_p of Algorithm 2 step 2 exactly as the tensor-core sketch applies it:
  * one round-to-nearest-even from FP64 to FP16, BF16 or FP32 (subnormal
  * targets included), y[i] = fl_p(x[i]) widened back to FP64 (DEVICE arrays
@@ -193,6 +220,16 @@ int mrcqr_sketch(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, 
 /* As mrcqr_sketch with an explicit kernel variant (see mrcqr_opts_t.sketch_variant). */
 int mrcqr_sketch_ex(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, int sketch_prec, uint64_t seed,
                     int variant, double* Y, mrcqr_stream_t stream);
+
+/* Algorithm 2 steps 1-4 with the transform of mrcqr_transform_t: c sampled
+ * rows or bins (mrcqr_sample_transform_rows with the same seed), Y = the
+ * scaled transform rows times D A in precision sketch_prec, widened to FP64
+ * (DEVICE double, ld = rows of Y: c, or 2c for MRCQR_TRANSFORM_RFFT_REIM with
+ * the Re rows first).  variant as mrcqr_opts_t.sketch_variant.  A: DEVICE
+ * double m x n, ld lda >= m, read-only.  Allocates its workspace with
+ * cudaMallocAsync on `stream`; INVALID before any launch on bad arguments. */
+int mrcqr_sketch_transform(int64_t m, int64_t n, const double* A, int64_t lda, int64_t c, int transform,
+                           int sketch_prec, uint64_t seed, int variant, double* Y, mrcqr_stream_t stream);
 
 /* Algorithm 2 steps 5-6: R_s of Y (DEVICE double s x n, ld = s) by
  * Householder QR in FP32 (prec FP16/BF16/FP32) or FP64, diag(R_s) > 0,

@@ -24,7 +24,7 @@ class MrcqrError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("s_factor", ctypes.c_int32), ("check", ctypes.c_int32), ("escalate", ctypes.c_int32),
                 ("sketch_variant", ctypes.c_int32), ("ortho_tol", ctypes.c_double), ("stats_device", ctypes.c_void_p),
-                ("fp64_products", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("fp64_products", ctypes.c_int32), ("transform", ctypes.c_int32)]
 
 
 class BatchedOpts(ctypes.Structure):
@@ -69,9 +69,11 @@ SIGNATURES = {
     "mrcqr_batched_plan_destroy": ([_vp], _i32),
     "mrcqr_signs": ([_i64, _u64, _vp, _vp], _i32),
     "mrcqr_sample_rows": ([_i64, _i64, _u64, _vp, _vp], _i32),
+    "mrcqr_sample_transform_rows": ([_i64, _i64, _i32, _u64, _vp, _vp], _i32),
     "mrcqr_round": ([_i32, _i64, _vp, _vp, _vp], _i32),
     "mrcqr_sketch": ([_i64, _i64, _vp, _i64, _i64, _i32, _u64, _vp, _vp], _i32),
     "mrcqr_sketch_ex": ([_i64, _i64, _vp, _i64, _i64, _i32, _u64, _i32, _vp, _vp], _i32),
+    "mrcqr_sketch_transform": ([_i64, _i64, _vp, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp], _i32),
     "mrcqr_sketch_qr": ([_i64, _i64, _vp, _i32, _vp, _vp], _i32),
     "mrcqr_last_sketch_variant": ([], _i32),
     "mrcqr_cholqr_precond": ([_i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp], _i32),

@@ -26,6 +26,7 @@ size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 struct Plan {
   int64_t m = 0;
   int n = 0, s = 0, npad = 0, chunks = 0, splits = 0;
+  int tf = T_DCT;   // sketch transform; s counts the rows of Y (2 x bins for T_RFFT_REIM)
   size_t off_ctl = 0, off_idx = 0, off_tab = 0, off_tabf = 0, off_ypart = 0, off_y = 0, off_sqr = 0, off_rs = 0, off_rst = 0,
          off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, off_feat = 0, off_oze = 0, off_ozx = 0,
          off_colhi = 0, off_ozpart = 0, off_tcole = 0, off_trd = 0, total = 0;
@@ -33,8 +34,9 @@ struct Plan {
   SketchOzPlan sk{};
 };
 
-Plan make_plan(int64_t m, int n, int s) {
+Plan make_plan(int64_t m, int n, int s, int tf = T_DCT) {
   Plan p;
+  p.tf = tf;
   p.m = m;
   p.n = n;
   p.s = s;
@@ -189,13 +191,22 @@ bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
   return pa < pb + bbytes && pb < pa + abytes;
 }
 
+// Rows of Y for c sampled rows or bins; INVALID (-1) when c does not fit the
+// transform: at most m rows of the DCT, floor(m/2) + 1 bins of the real FFT,
+// at most 8192 rows of Y.
+int64_t sketch_rows(int64_t m, int64_t c, int tf) {
+  if (tf < T_DCT || tf > T_RFFT_REIM || c < 1) return -1;
+  if (c > (tf == T_DCT ? m : m / 2 + 1)) return -1;
+  const int64_t rows = tf == T_RFFT_REIM ? 2 * c : c;
+  return rows > 8192 ? -1 : rows;
+}
+
 int validate(int64_t m, int64_t n, const double* A, int64_t lda, const double* Q, int64_t ldq, const double* R,
-             int64_t ldr, int s_factor) {
+             int64_t ldr, int s_factor, int tf = T_DCT) {
   if (!A || !Q || !R) return MRCQR_ERR_INVALID;
   if (n < 1 || n > kMaxN || m < 1 || m >= (int64_t(1) << 31)) return MRCQR_ERR_INVALID;
   if (s_factor < 1 || s_factor > 16) return MRCQR_ERR_INVALID;
-  const int64_t s = (int64_t)s_factor * n;
-  if (s > m || s > 8192) return MRCQR_ERR_INVALID;
+  if (sketch_rows(m, (int64_t)s_factor * n, tf) < 0) return MRCQR_ERR_INVALID;
   if (lda < m || ldq < m || ldr < n) return MRCQR_ERR_INVALID;
   const size_t abytes = sizeof(double) * (size_t)((n - 1) * lda + m);
   const size_t qbytes = sizeof(double) * (size_t)((n - 1) * ldq + m);
@@ -230,16 +241,18 @@ int enqueue_sketch(const Plan& p, void* ws, int prec, int variant, int fp64_prod
   if (prec == P_FP64 && variant != 1 && fp64_products == 0) {
     launch(SG_SKETCH, lvl, st, [&] {
       launch_sketch_oz(p.m, p.n, p.s, A, lda, idx, tab, seed, p.sk, at<uint32_t>(ws, p.off_colhi),
-                       at<long long>(ws, p.off_ozpart), Y, ctl, lvl, st);
+                       at<long long>(ws, p.off_ozpart), Y, ctl, lvl, st, p.tf);
     });
     return 3;
   }
   double* ypart = at<double>(ws, p.off_ypart);
   launch(SG_SKETCH, lvl, st, [&] {
     used = launch_sketch(prec, variant, A, lda, p.m, p.n, p.s, idx, tab, at<float>(ws, p.off_tabf), seed, p.chunks,
-                         ypart, ctl, lvl, st);
+                         ypart, ctl, lvl, st, p.tf);
   });
-  launch(SG_SKREDUCE, lvl, st, [&] { launch_sketch_reduce(p.m, p.n, p.s, p.chunks, ypart, idx, Y, ctl, lvl, st); });
+  launch(SG_SKREDUCE, lvl, st, [&] {
+    launch_sketch_reduce(p.m, p.n, p.s, p.chunks, ypart, idx, Y, ctl, lvl, st, p.tf);
+  });
   return used;
 }
 
@@ -327,7 +340,8 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
   const double tol = (opts && opts->ortho_tol > 0) ? opts->ortho_tol : kDefaultTol;
   const int variant = opts ? opts->sketch_variant : 0;
   const int fp64p = opts ? opts->fp64_products : 0;
-  int rc = validate(m, n, A, lda, Q, ldq, R, ldr, s_factor);
+  const int tf = opts ? opts->transform : T_DCT;
+  int rc = validate(m, n, A, lda, Q, ldq, R, ldr, s_factor, tf);
   if (rc != MRCQR_OK) return rc;
   if (sketch_prec < P_FP16 || sketch_prec > P_AUTO) return MRCQR_ERR_INVALID;
   const bool autosel = sketch_prec == P_AUTO;
@@ -336,8 +350,9 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
     return MRCQR_ERR_INVALID;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int s = s_factor * (int)n;
-  const Plan p = make_plan(m, (int)n, s);
+  const int bins = s_factor * (int)n;                 // sampled rows (DCT) or bins (real FFT)
+  const int s = (int)sketch_rows(m, bins, tf);        // rows of Y
+  const Plan p = make_plan(m, (int)n, s, tf);
   int lv[kMaxLevels] = {P_FP64, P_FP64, P_FP64, P_FP64};
   // AUTO: the ladder fp16 -> fp32 -> fp64 always; the selector picks where it starts
   const int nlevels = make_ladder(autosel ? (int)P_FP16 : sketch_prec, autosel || escalate, lv);
@@ -352,7 +367,7 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
   uint32_t* idx = at<uint32_t>(ws, p.off_idx);
   double* tab = at<double>(ws, p.off_tab);
   launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, nlevels, lv[0], lv[1], lv[2], lv[3], tol); } });
-  launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, s, seed, idx, ctl, st); });
+  launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, bins, seed, idx, ctl, st, tf); });
   launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, at<float>(ws, p.off_tabf), st); });
   for (int L = 0; L < nlevels; ++L) {
     double* y = at<double>(ws, p.off_y);
@@ -412,6 +427,14 @@ int mrcqr_sample_rows(int64_t m, int64_t s, uint64_t seed, uint32_t* idx, mrcqr_
   return finish(st);
 }
 
+int mrcqr_sample_transform_rows(int64_t m, int64_t c, int transform, uint64_t seed, uint32_t* idx,
+                                mrcqr_stream_t stream) {
+  if (!idx || m < 1 || m >= (int64_t(1) << 31) || sketch_rows(m, c, transform) < 0) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, (int)c, seed, idx, nullptr, st, transform); });
+  return finish(st);
+}
+
 int mrcqr_sketch(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, int sketch_prec, uint64_t seed,
                  double* Y, mrcqr_stream_t stream) {
   return mrcqr_sketch_ex(m, n, A, lda, s, sketch_prec, seed, 0, Y, stream);
@@ -419,12 +442,17 @@ int mrcqr_sketch(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, 
 
 int mrcqr_sketch_ex(int64_t m, int64_t n, const double* A, int64_t lda, int64_t s, int sketch_prec, uint64_t seed,
                     int variant, double* Y, mrcqr_stream_t stream) {
-  if (!A || !Y || n < 1 || n > kMaxN || m < 1 || m >= (int64_t(1) << 31) || lda < m || s < 1 || s > m ||
-      s > 8192)
-    return MRCQR_ERR_INVALID;
+  return mrcqr_sketch_transform(m, n, A, lda, s, MRCQR_TRANSFORM_DCT, sketch_prec, seed, variant, Y, stream);
+}
+
+int mrcqr_sketch_transform(int64_t m, int64_t n, const double* A, int64_t lda, int64_t c, int transform,
+                           int sketch_prec, uint64_t seed, int variant, double* Y, mrcqr_stream_t stream) {
+  if (!A || !Y || n < 1 || n > kMaxN || m < 1 || m >= (int64_t(1) << 31) || lda < m) return MRCQR_ERR_INVALID;
+  const int64_t s = sketch_rows(m, c, transform);
+  if (s < 0) return MRCQR_ERR_INVALID;
   if (sketch_prec < P_FP16 || sketch_prec > P_FP64) return MRCQR_ERR_INVALID;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const Plan p = make_plan(m, (int)n, (int)s);
+  const Plan p = make_plan(m, (int)n, (int)s, transform);
   void* ws = nullptr;
   if (cudaMallocAsync(&ws, p.total, st) != cudaSuccess) {
     cudaGetLastError();
@@ -434,7 +462,7 @@ int mrcqr_sketch_ex(int64_t m, int64_t n, const double* A, int64_t lda, int64_t 
   uint32_t* idx = at<uint32_t>(ws, p.off_idx);
   double* tab = at<double>(ws, p.off_tab);
   launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, sketch_prec, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
-  launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, (int)s, seed, idx, ctl, st); });
+  launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, (int)c, seed, idx, ctl, st, transform); });
   launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, at<float>(ws, p.off_tabf), st); });
   g_sketch_variant_last = enqueue_sketch(p, ws, sketch_prec, variant, 0, A, lda, seed, Y, ctl, 0, st);
   cudaFreeAsync(ws, st);

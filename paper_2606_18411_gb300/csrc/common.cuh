@@ -115,6 +115,31 @@ __device__ __forceinline__ int scale_exponent(double amax) {
   return 14 - ex;
 }
 
+// Sketch transforms (Sec. II-A).  Every entry of a transform row is
+// cos(pi r / (2m)) for the integer phase r = (dk j + beta) mod 4m of column j:
+//   T_DCT      DCT-II row k:             dk = 2k, beta = k  (cos(pi k (2j+1) / (2m)))
+//   T_RFFT     Re of real-FFT bin k:     dk = 4k, beta = 0  (cos(2 pi k j / m))
+//   T_RFFT_REIM Im rows of those bins:   dk = 4k, beta = m  (cos(2 pi k j / m + pi / 2)
+//                                                           = -sin(2 pi k j / m))
+// A row word holds k in bits 0..30 and, for the Im rows, kImRow.
+enum Transform : int { T_DCT = 0, T_RFFT = 1, T_RFFT_REIM = 2 };
+constexpr uint32_t kImRow = 0x80000000u;
+
+struct RowPhase {
+  uint64_t dk, beta;   // phase of column j: (dk j + beta) mod 4m, dk < 4m
+};
+
+__device__ __forceinline__ RowPhase row_phase(int tf, uint32_t word, uint64_t m) {
+  const uint64_t k = word & ~kImRow, fm = 4ull * m;
+  if (tf == T_DCT) return RowPhase{(2ull * k) % fm, k % fm};
+  return RowPhase{(4ull * k) % fm, (word & kImRow) ? m : 0ull};
+}
+
+// (dk j + beta) mod 4m without overflow: dk < 4m <= 2^33, j < 2^31.
+__device__ __forceinline__ uint64_t phase_at(const RowPhase& p, uint64_t j, uint64_t fm) {
+  return (p.dk * j + p.beta) % fm;
+}
+
 // cos(pi r / (2m)) for an integer phase r in [0, 4m), from a table of
 // cos(pi q / (2m)), q = 0..m (quarter-wave symmetry).
 __device__ __forceinline__ double cos_phase(const double* __restrict__ tab, int64_t r, int64_t m) {

@@ -67,21 +67,23 @@ void launch_g_judge(const Group& g, int level, cudaStream_t st);
 void launch_g_publish(const Group& g, cudaStream_t st);
 
 // --- sketch (sketch.cu) ------------------------------------------------------
-void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ctl, cudaStream_t st);
+// tf: the sketch transform (T_DCT, T_RFFT, T_RFFT_REIM of common.cuh); s rows (DCT) or bins (real FFT), written
+// to idx[0..s) and, for T_RFFT_REIM, their Im rows to idx[s..2s).
+void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ctl, cudaStream_t st, int tf = 0);
 void launch_costab(int64_t m, double* tab, float* tabf, cudaStream_t st);
 int sketch_chunks(int64_t m, int n, int s);
 // variant: 0 = auto (tensor cores when eligible), 1 = SIMT, 2 = tensor cores (falls back to SIMT when
 // the TMA preconditions fail).  Returns the variant launched (1 or 2).
 int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m, int n, int s,
                   const uint32_t* idx, const double* tab, const float* tabf, uint64_t seed, int chunks,
-                  double* Ypart, Ctl* ctl, int level, cudaStream_t st);
+                  double* Ypart, Ctl* ctl, int level, cudaStream_t st, int tf = 0);
 // tensor-core sketch (sketch_tc.cu): FP16/BF16/FP32, A 16-byte aligned, lda even
 bool sketch_tc_eligible(int prec, const double* A, int64_t lda);
 bool launch_sketch_tc(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,
                       const double* tab, const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl,
-                      int level, cudaStream_t st);
+                      int level, cudaStream_t st, int tf = 0);
 void launch_sketch_reduce(int64_t m, int n, int s, int chunks, const double* Ypart, const uint32_t* idx,
-                          double* Y, Ctl* ctl, int level, cudaStream_t st);
+                          double* Y, Ctl* ctl, int level, cudaStream_t st, int tf = 0);
 void launch_round(int prec, int64_t count, const double* x, double* y, cudaStream_t st);
 // Signs of rows [0, m) as +-1 doubles (test entry point).
 void launch_signs(int64_t m, uint64_t seed, double* out, cudaStream_t st);
@@ -138,7 +140,7 @@ void launch_trsm_oz(int64_t m, int n, const double* A, int64_t lda, const double
 size_t sketch_oz_part_bytes(const SketchOzPlan& P);
 void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, const uint32_t* idx, const double* tab,
                       uint64_t seed, const SketchOzPlan& P, uint32_t* colHi, long long* part, double* Y, Ctl* ctl,
-                      int level, cudaStream_t st);
+                      int level, cudaStream_t st, int tf = 0);
 void launch_finalize_oz(int64_t m, int n, double* Q, int64_t ldq, const double* XT, uint32_t* colE,
                         unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st, uint32_t* colHiOut = nullptr);
 

@@ -497,7 +497,7 @@ __global__ void k_syrk_oz_reduce(int n, const uint32_t* __restrict__ colHi, Syrk
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_sketch_oz(int64_t m, int n, int s, const double* __restrict__ A, int64_t lda, const uint32_t* __restrict__ colHi,
                 const uint32_t* __restrict__ idx, const double* __restrict__ tab, uint2 key, SketchOzPlan SP,
-                long long* __restrict__ part, Ctl* ctl, int level) {
+                long long* __restrict__ part, Ctl* ctl, int level, int tf) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = oz_smem(smem_raw);
@@ -537,10 +537,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     __syncthreads();
     // phase of (sample fi, row r_begin + 4 fg), its advance per chunk and per row
     const bool fval = i0 + fi < s;
-    const uint64_t k = fval ? (uint64_t)idx[i0 + fi] : 0ull;
-    uint64_t r = fval ? (k * (uint64_t)(2 * (r_begin + 4 * fg) + 1)) % four_m : 0ull;
-    const uint64_t step_chunk = (k * (uint64_t)(2 * kK)) % four_m;
-    const uint64_t step_row = 2ull * k;   // < 4m
+    const RowPhase rp = row_phase(tf, fval ? idx[i0 + fi] : 0u, (uint64_t)m);
+    uint64_t r = fval ? phase_at(rp, (uint64_t)(r_begin + 4 * fg), four_m) : 0ull;
+    const uint64_t step_chunk = (rp.dk * (uint64_t)kK) % four_m;
+    const uint64_t step_row = rp.dk;   // < 4m
     long long hi[16], lo[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
@@ -589,11 +589,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 }
 
 // Y (s x n, column-major) from the items' partials: exact sums over the
-// slabs, one rounding, times sqrt(2/s) c_k.  A non-finite column of A gives a
-// NaN column and raises NONFINITE.
+// slabs, one rounding, times the row's scale (DCT: sqrt(2/s) c_k; real FFT:
+// sqrt(c/m) for c bins).  A non-finite column of A gives a NaN column and
+// raises NONFINITE.
 __global__ void k_sketch_oz_reduce(int n, int s, const uint32_t* __restrict__ colHi, const uint32_t* __restrict__ idx,
                                    SketchOzPlan SP, const long long* __restrict__ part, double* __restrict__ Y,
-                                   Ctl* ctl, int level) {
+                                   Ctl* ctl, int level, int tf, int64_t m) {
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)s * n) return;
@@ -602,7 +603,8 @@ __global__ void k_sketch_oz_reduce(int n, int s, const uint32_t* __restrict__ co
   const oz::I128 acc = oz_sum_partials(part + (size_t)tile * kPartElems, SP.slabs,
                                        (size_t)SP.mblocks * SP.ntiles * kPartElems, c % kM, i % kN);
   const uint32_t Ec = oz::exp_field(colHi[c]);
-  const double coef = sqrt(2.0 / (double)s) * (idx[i] == 0 ? 0.70710678118654752440 : 1.0);
+  const double coef = tf == T_DCT ? sqrt(2.0 / (double)s) * (idx[i] == 0 ? 0.70710678118654752440 : 1.0)
+                                  : sqrt((double)(tf == T_RFFT_REIM ? s / 2 : s) / (double)m);
   const double y = Ec == 2047u ? nan64() : oz::i128_to_double(acc, (int)Ec + 1023 - oz::kScaleBias) * coef;
   Y[e] = y;
   if (!isfinite(y)) {
@@ -1002,14 +1004,14 @@ size_t sketch_oz_part_bytes(const SketchOzPlan& P) {
 
 void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, const uint32_t* idx, const double* tab,
                       uint64_t seed, const SketchOzPlan& P, uint32_t* colHi, long long* part, double* Y, Ctl* ctl,
-                      int level, cudaStream_t st) {
+                      int level, cudaStream_t st, int tf) {
   launch_col_hi(m, n, A, lda, colHi, ctl, level, st);
   set_smem(k_sketch_oz);
   const int nitems = P.mblocks * P.ntiles * P.slabs;
   { ::mrcqr::note_launch(); k_sketch_oz<<<nitems < num_sms() ? nitems : num_sms(), kOzThreads, kSmem, st>>>(m, n, s, A, lda, colHi, idx, tab,
-                                                                                 seed_key(seed), P, part, ctl, level); }
+                                                                                 seed_key(seed), P, part, ctl, level, tf); }
   const int64_t total = (int64_t)s * n;
-  { ::mrcqr::note_launch(); k_sketch_oz_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, colHi, idx, P, part, Y, ctl, level); }
+  { ::mrcqr::note_launch(); k_sketch_oz_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, colHi, idx, P, part, Y, ctl, level, tf, m); }
 }
 
 size_t trsm_oz_rd_bytes(int n) {

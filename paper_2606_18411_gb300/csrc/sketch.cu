@@ -18,7 +18,10 @@ namespace mrcqr {
 // keeps j (never chosen before, since all earlier values are < j).
 constexpr uint32_t kEmpty = 0xffffffffu;
 
-__device__ __forceinline__ void sample_block(int64_t m, int s, uint2 key, uint32_t* __restrict__ idx) {
+// m is the population: the rows of the transform (DCT) or its floor(m/2) + 1
+// bins (real FFT).  reim: idx[s + t] = idx[t] | kImRow, the Im rows of the
+// same bins.
+__device__ __forceinline__ void sample_block(int64_t m, int s, uint2 key, uint32_t* __restrict__ idx, int reim = 0) {
   extern __shared__ uint32_t sm[];
   int H = 1;
   while (H < 2 * s) H <<= 1;
@@ -72,24 +75,30 @@ __device__ __forceinline__ void sample_block(int64_t m, int s, uint2 key, uint32
       __syncthreads();
     }
   }
-  for (int t = threadIdx.x; t < s; t += blockDim.x) idx[t] = keys[t];
+  for (int t = threadIdx.x; t < s; t += blockDim.x) {
+    idx[t] = keys[t];
+    if (reim) idx[s + t] = keys[t] | kImRow;
+  }
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(1024) k_sample(int64_t m, int s, uint2 key, uint32_t* __restrict__ idx,
-                                                  const Ctl* ctl) {
+                                                  const Ctl* ctl, int reim) {
   (void)ctl;
-  sample_block(m, s, key, idx);
+  sample_block(m, s, key, idx, reim);
 }
 
-void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ctl, cudaStream_t st) {
+// s = the number of sampled rows (DCT) or bins (real FFT); the real-FFT
+// transforms draw from the floor(m/2) + 1 bins of a real column.
+void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ctl, cudaStream_t st, int tf) {
+  if (tf != T_DCT) m = m / 2 + 1;
   int H = 1;
   while (H < 2 * s) H <<= 1;
   int P = 1;
   while (P < s) P <<= 1;
   const size_t smem = sizeof(uint32_t) * (size_t)(s + H + P);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  { ::mrcqr::note_launch(); k_sample<<<1, 1024, smem, st>>>(m, s, seed_key(seed), idx, ctl); }
+  { ::mrcqr::note_launch(); k_sample<<<1, 1024, smem, st>>>(m, s, seed_key(seed), idx, ctl, tf == T_RFFT_REIM); }
 }
 
 // ---------------------------------------------------------------------------
@@ -151,7 +160,7 @@ template <int PREC>
 __device__ __forceinline__ void sketch_simt_block(const double* __restrict__ A, int64_t lda, int64_t m, int n, int s,
                                                   const uint32_t* __restrict__ idx, const double* __restrict__ tab,
                                                   uint2 key, int64_t rows_per_chunk, double* __restrict__ Ypart,
-                                                  int bx, int by, int bz) {
+                                                  int bx, int by, int bz, int tf) {
   using Acc = std::conditional_t<PREC == P_FP64, double, float>;
   constexpr int ST = kSkST, NT = kSkNT, T = kSkT;
   __shared__ double Xd[T][NT + 1];
@@ -161,7 +170,7 @@ __device__ __forceinline__ void sketch_simt_block(const double* __restrict__ A, 
   __shared__ Acc colscale[NT];
   __shared__ double sg[T];
   __shared__ uint32_t ks[ST];
-  __shared__ uint64_t r0[ST];
+  __shared__ uint64_t r0[ST], dks[ST];
 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
@@ -169,7 +178,10 @@ __device__ __forceinline__ void sketch_simt_block(const double* __restrict__ A, 
   const int64_t j_begin = (int64_t)bx * rows_per_chunk;
   const int64_t j_end = min(m, j_begin + rows_per_chunk);
   const uint64_t four_m = 4ull * (uint64_t)m;
-  if (tid < ST) ks[tid] = (s0 + tid < s) ? idx[s0 + tid] : kEmpty;
+  if (tid < ST) {
+    ks[tid] = (s0 + tid < s) ? idx[s0 + tid] : kEmpty;
+    dks[tid] = ks[tid] == kEmpty ? 0ull : row_phase(tf, ks[tid], (uint64_t)m).dk;
+  }
 
   Acc acc[4][4];
 #pragma unroll
@@ -182,7 +194,7 @@ __device__ __forceinline__ void sketch_simt_block(const double* __restrict__ A, 
     if (tid < T) sg[tid] = (j0 + tid < j_end) ? row_sign((uint64_t)(j0 + tid), key) : 0.0;
     if (tid >= 64 && tid < 64 + ST) {
       const int i = tid - 64;
-      r0[i] = ks[i] == kEmpty ? 0 : ((uint64_t)ks[i] * (uint64_t)(2 * j0 + 1)) % four_m;
+      r0[i] = ks[i] == kEmpty ? 0 : phase_at(row_phase(tf, ks[i], (uint64_t)m), (uint64_t)j0, four_m);
     }
     __syncthreads();
     for (int e = tid; e < T * NT; e += 256) {
@@ -198,7 +210,7 @@ __device__ __forceinline__ void sketch_simt_block(const double* __restrict__ A, 
       const uint32_t k = ks[i];
       double v = 0.0;
       if (k != kEmpty && j0 + t < j_end) {
-        const uint64_t r = (r0[i] + 2ull * (uint64_t)k * (uint64_t)t) % four_m;
+        const uint64_t r = (r0[i] + dks[i] * (uint64_t)t) % four_m;
         v = cos_phase(tab, (int64_t)r, m);
       }
       if constexpr (PREC == P_FP64) Ss[t][i] = v;
@@ -262,9 +274,10 @@ __global__ void __launch_bounds__(256) k_sketch_simt(const double* __restrict__ 
                                                       int s, const uint32_t* __restrict__ idx,
                                                       const double* __restrict__ tab, uint2 key,
                                                       int64_t rows_per_chunk, double* __restrict__ Ypart,
-                                                      const Ctl* ctl, int level) {
+                                                      const Ctl* ctl, int level, int tf) {
   if (level_inactive(ctl, level)) return;
-  sketch_simt_block<PREC>(A, lda, m, n, s, idx, tab, key, rows_per_chunk, Ypart, blockIdx.x, blockIdx.y, blockIdx.z);
+  sketch_simt_block<PREC>(A, lda, m, n, s, idx, tab, key, rows_per_chunk, Ypart, blockIdx.x, blockIdx.y, blockIdx.z,
+                          tf);
 }
 
 int sketch_chunks(int64_t m, int n, int s) {
@@ -283,32 +296,35 @@ static int64_t rows_per_chunk(int64_t m, int chunks) {
 
 int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m, int n, int s,
                   const uint32_t* idx, const double* tab, const float* tabf, uint64_t seed, int chunks,
-                  double* Ypart, Ctl* ctl, int level, cudaStream_t st) {
+                  double* Ypart, Ctl* ctl, int level, cudaStream_t st, int tf) {
   if (variant != 1 && sketch_tc_eligible(prec, A, lda) &&
-      launch_sketch_tc(prec, A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st))
+      launch_sketch_tc(prec, A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf))
     return 2;
   const dim3 grid(chunks, (s + kSkST - 1) / kSkST, (n + kSkNT - 1) / kSkNT);
   const int64_t rpc = rows_per_chunk(m, chunks);
   const uint2 key = seed_key(seed);
   switch (prec) {
-    case P_FP16: { ::mrcqr::note_launch(); k_sketch_simt<P_FP16><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); } break;
-    case P_BF16: { ::mrcqr::note_launch(); k_sketch_simt<P_BF16><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); } break;
-    case P_FP32: { ::mrcqr::note_launch(); k_sketch_simt<P_FP32><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); } break;
-    default: { ::mrcqr::note_launch(); k_sketch_simt<P_FP64><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level); } break;
+    case P_FP16: { ::mrcqr::note_launch(); k_sketch_simt<P_FP16><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level, tf); } break;
+    case P_BF16: { ::mrcqr::note_launch(); k_sketch_simt<P_BF16><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level, tf); } break;
+    case P_FP32: { ::mrcqr::note_launch(); k_sketch_simt<P_FP32><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level, tf); } break;
+    default: { ::mrcqr::note_launch(); k_sketch_simt<P_FP64><<<grid, 256, 0, st>>>(A, lda, m, n, s, idx, tab, key, rpc, Ypart, ctl, level, tf); } break;
   }
   return 1;
 }
 
-// Y = sqrt(2/s) c_k * sum over chunks (fixed order), with c_0 = 1/sqrt(2):
-// the sqrt(m/s) sketch scale times the sqrt(2/m) c_k of the orthonormal DCT.
+// Y = coef_i * sum over chunks (fixed order).  DCT: coef = sqrt(2/s) c_k with
+// c_0 = 1/sqrt(2), the sqrt(m/s) sketch scale times the sqrt(2/m) c_k of the
+// orthonormal DCT-II.  Real FFT: coef = sqrt(c/m) for c sampled bins (the
+// unnormalised transform, Algorithm 2 as printed).
 __device__ __forceinline__ void sketch_reduce_entry(int n, int s, int chunks, const double* __restrict__ Ypart,
                                                     const uint32_t* __restrict__ idx, double* __restrict__ Y,
-                                                    Ctl* ctl, int64_t e) {
+                                                    Ctl* ctl, int64_t e, int tf = T_DCT, int64_t m = 0) {
   const int64_t total = (int64_t)s * n;
   const int i = (int)(e % s);
   double acc = 0.0;
   for (int c = 0; c < chunks; ++c) acc += Ypart[(size_t)c * total + e];
-  const double coef = sqrt(2.0 / (double)s) * (idx[i] == 0 ? 0.70710678118654752440 : 1.0);
+  const double coef = tf == T_DCT ? sqrt(2.0 / (double)s) * (idx[i] == 0 ? 0.70710678118654752440 : 1.0)
+                                  : sqrt((double)(tf == T_RFFT_REIM ? s / 2 : s) / (double)m);
   const double y = acc * coef;
   Y[e] = y;
   if (!isfinite(y)) {
@@ -318,17 +334,17 @@ __device__ __forceinline__ void sketch_reduce_entry(int n, int s, int chunks, co
 }
 
 __global__ void k_sketch_reduce(int n, int s, int chunks, const double* __restrict__ Ypart,
-                                const uint32_t* __restrict__ idx, double* __restrict__ Y, Ctl* ctl, int level) {
+                                const uint32_t* __restrict__ idx, double* __restrict__ Y, Ctl* ctl, int level, int tf,
+                                int64_t m) {
   if (level_inactive(ctl, level)) return;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < (int64_t)s * n) sketch_reduce_entry(n, s, chunks, Ypart, idx, Y, ctl, e);
+  if (e < (int64_t)s * n) sketch_reduce_entry(n, s, chunks, Ypart, idx, Y, ctl, e, tf, m);
 }
 
 void launch_sketch_reduce(int64_t m, int n, int s, int chunks, const double* Ypart, const uint32_t* idx, double* Y,
-                          Ctl* ctl, int level, cudaStream_t st) {
-  (void)m;
+                          Ctl* ctl, int level, cudaStream_t st, int tf) {
   const int64_t total = (int64_t)s * n;
-  { ::mrcqr::note_launch(); k_sketch_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, chunks, Ypart, idx, Y, ctl, level); }
+  { ::mrcqr::note_launch(); k_sketch_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, chunks, Ypart, idx, Y, ctl, level, tf, m); }
 }
 
 // ---------------------------------------------------------------------------
@@ -386,7 +402,7 @@ __global__ void __launch_bounds__(256) kg_sketch(Group g, int level) {
     const Prob& P = g.probs[w.x];
     if (P.ctl->active != level) continue;
     sketch_simt_block<PREC>(P.A, P.lda, P.m, P.n, P.s, P.idx, P.tab, P.key, P.rows_per_chunk, P.ypart, w.y, w.z,
-                            w.w);
+                            w.w, T_DCT);
   }
 }
 

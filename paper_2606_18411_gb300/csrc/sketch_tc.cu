@@ -6,7 +6,11 @@
 // theta_i = pi k_i (2 j0 + 1) / (2m) and beta_it = pi k_i t / m, so
 //   sum_t cos(theta_i + beta_it) x_t = cos(theta_i) (C x)_i - sin(theta_i) (S x)_i
 // with C_it = cos(pi k_i t/m), S_it = sin(pi k_i t/m) independent of the
-// slab.  A CTA keeps C and S (rounded to the sketch precision) in shared
+// slab.  The real-FFT transforms of Algorithm 2 as printed take the same
+// path with the phase 2 pi k j / m (plus pi / 2 on the Im rows, which turns
+// the cosine into -sin), i.e. C_it = cos(2 pi k_i t / m) and theta_i the phase
+// of j0 (the row words and phases of common.cuh).
+// A CTA keeps C and S (rounded to the sketch precision) in shared
 // memory for up to 256 sampled rows (one or two MMA tiles of 128) and 64
 // columns of A, and per slab:
 //   1. TMA brings the FP64 tile A[j0 : j0+T, n0 : n0+64] (3-4 stages);
@@ -100,13 +104,14 @@ __device__ __forceinline__ uint32_t pack2(uint32_t h0, uint32_t l0, uint32_t h1,
   else return f64bits_to_bf16(h0, l0) | (f64bits_to_bf16(h1, l1) << 16);
 }
 
-// Phase k (2 j0 + 1) mod 4m advanced by slabs of T rows: adds 2 k T mod 4m.
+// Phase (dk j0 + beta) mod 4m of a row at slab start j0, advanced by slabs of
+// T rows: adds dk T mod 4m.
 struct Phase {
   uint64_t r, step, four_m;
-  __device__ void init(uint64_t k, int64_t j0, int T, uint64_t fm) {
+  __device__ void init(const RowPhase& p, int64_t j0, int T, uint64_t fm) {
     four_m = fm;
-    r = (k * (uint64_t)(2 * j0 + 1)) % fm;
-    step = (2ull * k * (uint64_t)T) % fm;
+    r = phase_at(p, (uint64_t)j0, fm);
+    step = (p.dk * (uint64_t)T) % fm;
   }
   __device__ void advance() {
     r += step;
@@ -118,7 +123,7 @@ template <int PREC, int MT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sketch_tc(const __grid_constant__ CUtensorMap tmapA, int64_t m, int n, int s, const uint32_t* __restrict__ idx,
                 const double* __restrict__ tab, const float* __restrict__ tabf, uint2 key, int64_t rows_per_chunk,
-                double* __restrict__ Ypart, Ctl* ctl, int level) {
+                double* __restrict__ Ypart, Ctl* ctl, int level, int tf) {
   using C = Cfg<PREC, MT>;
   constexpr int T = C::T;
   if (level_inactive(ctl, level)) return;
@@ -149,15 +154,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::mbar_fence_init();
   }
   // slab-invariant transform tables: two threads per sampled row (halves of
-  // t), phases 2 k t mod 4m advanced by additions along t
+  // t), phases dk t mod 4m advanced by additions along t
   for (int w = tid; w < 2 * kM * MT; w += kThreads) {
     const int ri = w >> 1, half = w & 1;
     const int mt = ri / kM, i = ri % kM;
     unsigned char* cb = tabs + (mt * 2 + 0) * C::PARTS * C::PANEL;
     unsigned char* sb = tabs + (mt * 2 + 1) * C::PARTS * C::PANEL;
     const bool ok = s0 + ri < s;
-    const uint64_t k = ok ? idx[s0 + ri] : 0;
-    const uint64_t d = (2ull * k) % four_m;
+    const uint64_t d = row_phase(tf, ok ? idx[s0 + ri] : 0u, (uint64_t)m).dk;
     const int t0 = half * (T / 2);
     uint64_t rc = (d * (uint64_t)t0) % four_m;
 #pragma unroll 8
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int erow = mt_e * kM + q * 32 + lane;
   const bool row_ok = s0 + erow < s;
   Phase ph;
-  ph.init(row_ok ? (uint64_t)idx[s0 + erow] : 0ull, j_begin, T, four_m);
+  ph.init(row_phase(tf, row_ok ? idx[s0 + erow] : 0u, (uint64_t)m), j_begin, T, four_m);
   const uint32_t idesc = tc::idesc(C::FMT, kM, kN);
   float acc[C::ACC];
 #pragma unroll
@@ -380,7 +384,8 @@ EncodeFn encode_fn() {
 
 template <int PREC, int MT>
 bool launch_tc(const CUtensorMap& map, int64_t m, int n, int s, const uint32_t* idx, const double* tab,
-               const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level, cudaStream_t st) {
+               const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level, cudaStream_t st,
+               int tf) {
   using C = Cfg<PREC, MT>;
   const size_t smem = C::SMEM + 1024;
   if (cudaFuncSetAttribute(k_sketch_tc<PREC, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -390,13 +395,14 @@ bool launch_tc(const CUtensorMap& map, int64_t m, int n, int s, const uint32_t* 
   rpc = (rpc + 63) / 64 * 64;
   const dim3 grid((s + kM * MT - 1) / (kM * MT), (n + kN - 1) / kN, chunks);
   { ::mrcqr::note_launch(); k_sketch_tc<PREC, MT><<<grid, kThreads, smem, st>>>(map, m, n, s, idx, tab, tabf, seed_key(seed), rpc, Ypart, ctl,
-                                                      level); }
+                                                      level, tf); }
   return true;
 }
 
 template <int PREC>
 bool launch_prec(const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx, const double* tab,
-                 const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level, cudaStream_t st) {
+                 const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level, cudaStream_t st,
+                 int tf) {
   EncodeFn enc = encode_fn();
   if (!enc) return false;
   CUtensorMap map;
@@ -408,8 +414,8 @@ bool launch_prec(const double* A, int64_t lda, int64_t m, int n, int s, const ui
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
-  if (s > kM) return launch_tc<PREC, 2>(map, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st);
-  return launch_tc<PREC, 1>(map, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st);
+  if (s > kM) return launch_tc<PREC, 2>(map, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf);
+  return launch_tc<PREC, 1>(map, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf);
 }
 
 }  // namespace
@@ -422,11 +428,11 @@ bool sketch_tc_eligible(int prec, const double* A, int64_t lda) {
 
 bool launch_sketch_tc(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,
                       const double* tab, const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl,
-                      int level, cudaStream_t st) {
+                      int level, cudaStream_t st, int tf) {
   switch (prec) {
-    case P_FP16: return launch_prec<P_FP16>(A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st);
-    case P_BF16: return launch_prec<P_BF16>(A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st);
-    case P_FP32: return launch_prec<P_FP32>(A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st);
+    case P_FP16: return launch_prec<P_FP16>(A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf);
+    case P_BF16: return launch_prec<P_BF16>(A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf);
+    case P_FP32: return launch_prec<P_FP32>(A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf);
     default: return false;
   }
 }

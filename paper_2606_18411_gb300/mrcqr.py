@@ -67,12 +67,13 @@ def version() -> int:
 
 def factor_ex(A: torch.Tensor, Q: torch.Tensor, R: torch.Tensor, prec="fp64", seed: int = 0, s_factor: int = 2,
               check_ortho: bool = True, escalate: bool = True, tol: float = 1e-13, stats_device=None,
-              sketch_variant: int = 0, fp64_products: int = 0, stream=None) -> None:
-    """Enqueue MRCQR of A into Q (m x n) and R (n x n); asynchronous."""
+              sketch_variant: int = 0, fp64_products: int = 0, transform="dct", stream=None) -> None:
+    """Enqueue MRCQR of A into Q (m x n) and R (n x n); asynchronous.  transform: "dct" (default),
+    "rfft" (the paper's real-FFT sketch) or "rfft_reim" (real and imaginary parts)."""
     m, n = A.shape
     o = Opts(s_factor=s_factor, check=int(check_ortho), escalate=int(escalate), sketch_variant=sketch_variant,
              ortho_tol=tol, stats_device=stats_device.data_ptr() if stats_device is not None else None,
-             fp64_products=fp64_products, reserved1=0)
+             fp64_products=fp64_products, transform=_transform(transform))
     rc = _lib.load().mrcqr_factor_ex(m, n, A.data_ptr(), _ld(A, "A"), Q.data_ptr(), _ld(Q, "Q"), R.data_ptr(),
                                      _ld(R, "R"), _prec(prec), seed, ctypes.byref(o), _stream(stream))
     check(rc, "mrcqr_factor_ex")
@@ -183,6 +184,38 @@ def sample_rows(m: int, s: int, seed: int, device="cuda", stream=None) -> torch.
     idx = torch.empty(s, dtype=torch.int32, device=device)
     check(_lib.load().mrcqr_sample_rows(m, s, seed, idx.data_ptr(), _stream(stream)), "mrcqr_sample_rows")
     return idx
+
+
+TRANSFORMS = {"dct": 0, "rfft": 1, "rfft_reim": 2}
+
+
+def _transform(t) -> int:
+    if isinstance(t, str):
+        if t not in TRANSFORMS:
+            raise ValueError(f"unknown transform {t!r}")
+        return TRANSFORMS[t]
+    return int(t)
+
+
+def sample_transform_rows(m: int, c: int, transform="rfft", seed: int = 0, device="cuda",
+                          stream=None) -> torch.Tensor:
+    """c sampled rows (DCT) or bins (real FFT); rfft_reim returns 2c words, the Im rows with bit 31 set."""
+    tf = _transform(transform)
+    idx = torch.empty(2 * c if tf == 2 else c, dtype=torch.int32, device=device)
+    check(_lib.load().mrcqr_sample_transform_rows(m, c, tf, seed, idx.data_ptr(), _stream(stream)),
+          "mrcqr_sample_transform_rows")
+    return idx
+
+
+def sketch_transform(A: torch.Tensor, c: int, transform="rfft", prec="fp64", seed: int = 0, variant: int = 0,
+                     stream=None) -> torch.Tensor:
+    """Y of the given transform: c x n (2c x n for rfft_reim, Re rows first)."""
+    m, n = A.shape
+    tf = _transform(transform)
+    Y = empty_colmajor(2 * c if tf == 2 else c, n, device=A.device)
+    check(_lib.load().mrcqr_sketch_transform(m, n, A.data_ptr(), _ld(A, "A"), c, tf, _prec(prec), seed, variant,
+                                             Y.data_ptr(), _stream(stream)), "mrcqr_sketch_transform")
+    return Y
 
 
 def sketch(A: torch.Tensor, s: int, prec="fp64", seed: int = 0, variant: int = 0, stream=None) -> torch.Tensor:
