@@ -51,6 +51,7 @@ import os
 from dataclasses import dataclass, field
 
 import numpy as np
+from scipy.linalg import solve_triangular as scipy_solve_triangular
 
 U_FP64 = 2.0 ** -53
 # unit roundoff of the sketch precisions (round to nearest)
@@ -486,6 +487,142 @@ def probe_kappa_lower(q: float, u: float = U_FP64) -> float:
     """CholQR probe (Sec. II-C): kappa_2(A) >= sqrt(q / (u (1 + q))) with
     q = ||I - Q^T Q||_2 of a CholQR run."""
     return math.sqrt(q / (u * (1.0 + q)))
+
+
+# ---------------------------------------------------------------------------
+# Regime classification without learning (Sec. II-C): the CholQR probe and the
+# block 1-norm estimate on A^T A.  Regime 0 = half, 1 = single, 2 = double,
+# from an estimate of kappa_2(A) by ``precision_rule``'s thresholds.
+
+REGIME_PRECISIONS = ("fp16", "fp32", "fp64")
+
+
+def regime_of(kappa: float) -> int:
+    """Regime index of a kappa_2 estimate (``precision_rule``; inf -> 2)."""
+    return REGIME_PRECISIONS.index(precision_rule(kappa))
+
+
+def cholqr_probe(A: np.ndarray, u: float = U_FP64):
+    """(kappa estimate, q): Algorithm 1 on A, q = ||I - Q^T Q||_2 (sums in
+    double-double), and the bound kappa_2(A) >= sqrt(q / (u (1 + q))) of
+    Sec. II-C.  A Cholesky breakdown (A^T A not numerically positive
+    definite, kappa_2(A) beyond about u^-1/2) gives (inf, inf)."""
+    try:
+        Q, _ = cholqr(A)
+    except CholeskyBreakdown:
+        return math.inf, math.inf
+    q = orthogonality_error(Q)[0]
+    return probe_kappa_lower(q, u), q
+
+
+def random_sign_column(n: int, seed: int, draw: int) -> np.ndarray:
+    """The ``draw``-th random +-1 column of the block 1-norm estimator:
+    entry i = 1 - 2 (Philox(key=seed, ctr=(i, 2, draw, 0)).word0 & 1)."""
+    k0, k1 = seed_key(seed)
+    w0, _, _, _ = philox4x32_10(np.arange(n, dtype=np.uint64), 2, draw, 0, k0, k1)
+    return 1.0 - 2.0 * (w0 & 1).astype(np.float64)
+
+
+def _parallel(x: np.ndarray, y: np.ndarray) -> bool:
+    """Two +-1 columns are parallel when they are equal or opposite."""
+    return abs(float(x @ y)) == len(x)
+
+
+def onenorm_estimate(apply_B, apply_Bt, n: int, t: int = 2, itmax: int = 5, seed: int = 0,
+                     max_resample: int = 100) -> float:
+    """Block 1-norm estimator of Higham and Tisseur (SIAM J. Matrix Anal.
+    Appl. 21 (2000), Algorithm 2.4), a lower bound est <= ||B||_1 of a matrix
+    seen only through products B X and B^T X (n x t blocks).  Its random +-1
+    columns come from ``random_sign_column``; a column parallel to an
+    earlier one is redrawn (at most ``max_resample`` times).  For n <= 4 the
+    norm is computed exactly from B I (as MATLAB's normest1 does)."""
+    if n <= 4:
+        return float(np.abs(apply_B(np.eye(n))).sum(axis=0).max())
+    draw = 0
+
+    def fresh():
+        nonlocal draw
+        x = random_sign_column(n, seed, draw)
+        draw += 1
+        return x
+
+    # starting block: e/n, then random +-1 columns, none parallel to an earlier one
+    X = np.empty((n, t))
+    X[:, 0] = 1.0
+    for j in range(1, t):
+        x = fresh()
+        for _ in range(max_resample):
+            if not any(_parallel(x, X[:, i]) for i in range(j)):
+                break
+            x = fresh()
+        X[:, j] = x
+    X /= n
+    ind_hist: list[int] = []
+    est_old = 0.0
+    ind = np.zeros(n, dtype=np.int64)
+    S = np.zeros((n, t))
+    ind_best = 0
+    est = 0.0
+    for k in range(1, itmax + 2):
+        Y = apply_B(X)
+        norms = np.abs(Y).sum(axis=0)
+        jbest = int(np.argmax(norms))
+        est = float(norms[jbest])
+        if est > est_old or k == 2:
+            ind_best = int(ind[jbest])
+        if k >= 2 and est <= est_old:          # (1) no increase: stop with the previous estimate
+            est = est_old
+            break
+        est_old = est
+        S_old = S
+        if k > itmax:
+            break
+        S = np.where(Y >= 0, 1.0, -1.0)
+        if all(any(_parallel(S[:, j], S_old[:, i]) for i in range(t)) for j in range(t)):   # (2)
+            break
+        if t > 1:                              # (3) no column parallel to an earlier one or to S_old
+            for j in range(t):
+                for _ in range(max_resample):
+                    if not (any(_parallel(S[:, j], S[:, i]) for i in range(j)) or
+                            any(_parallel(S[:, j], S_old[:, i]) for i in range(t))):
+                        break
+                    S[:, j] = fresh()
+        Z = apply_Bt(S)
+        h = np.abs(Z).max(axis=1)
+        if k >= 2 and h.max() == h[ind_best]:  # (4)
+            break
+        order = np.argsort(-h, kind="stable")  # h descending, ties by index
+        if t > 1:
+            if all(int(i) in ind_hist for i in order[:t]):
+                break
+            fresh_idx = [int(i) for i in order if int(i) not in ind_hist][:t]
+            if len(fresh_idx) < t:
+                break
+            order = np.array(fresh_idx)
+        ind = np.zeros(n, dtype=np.int64)
+        X = np.zeros((n, t))
+        for j in range(t):
+            X[order[j], j] = 1.0
+            ind[j] = order[j]
+        ind_hist += [int(i) for i in order[:t]]
+    return est
+
+
+def onenorm_regime_estimate(A: np.ndarray, seed: int = 0):
+    """(kappa estimate, ||G||_1, est ||G^-1||_1) with G = A^T A: the bound
+    kappa_2(A)^2 <= n ||G||_1 ||G^-1||_1 of Sec. II-C, ||G^-1||_1 from the
+    block estimator with G^-1 applied through the Cholesky factor
+    (G = R^T R: two substitutions).  A Cholesky breakdown gives inf."""
+    n = A.shape[1]
+    G = A.T @ A
+    try:
+        R = cholesky_upper(G)
+    except CholeskyBreakdown:
+        return math.inf, float(np.abs(G).sum(axis=0).max()), math.inf
+    solve = lambda X: scipy_solve_triangular(R, scipy_solve_triangular(R, X, trans="T"))
+    g1 = float(np.abs(G).sum(axis=0).max())
+    est = onenorm_estimate(solve, solve, n, seed=seed)
+    return math.sqrt(n * g1 * est), g1, est
 
 
 def cond2(A: np.ndarray) -> float:

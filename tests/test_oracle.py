@@ -502,3 +502,78 @@ def test_product_rounded_cancellation_and_integers():
     Wi = rng.integers(-1000, 1000, (20, 12)).astype(float)
     Xi = np.triu(rng.integers(-1000, 1000, (12, 12))).astype(float)
     np.testing.assert_array_equal(O.product_rounded(Wi, Xi), Wi @ Xi)
+
+
+# --- Regime classification without learning (Sec. II-C) -------------------------
+
+def test_regime_thresholds():
+    # half below 1e4, single below 1e8, double beyond (boundaries as precision_rule)
+    assert [O.regime_of(k) for k in (1.0, 1e4, 1.0001e4, 1e8, 1.0001e8, math.inf)] == [0, 0, 1, 1, 2, 2]
+
+
+@pytest.mark.parametrize("n", [1, 3, 4])
+def test_onenorm_estimate_exact_for_tiny_n(n):
+    B = inputs.gaussian(n, n, seed=n)
+    est = O.onenorm_estimate(lambda X: B @ X, lambda X: B.T @ X, n)
+    assert est == pytest.approx(np.abs(B).sum(axis=0).max(), rel=1e-15)
+
+
+def test_onenorm_estimate_exact_on_diagonal_and_dominant_column():
+    # the estimator's second step lands on the unit vector of the largest column
+    n = 50
+    d = np.linspace(1.0, 3.0, n)[::-1].copy()
+    np.random.default_rng(1).shuffle(d)
+    B = np.diag(d)
+    assert O.onenorm_estimate(lambda X: B @ X, lambda X: B.T @ X, n) == pytest.approx(d.max(), rel=1e-15)
+    C = 0.01 * inputs.gaussian(n, n, seed=2)
+    C[:, 17] += 5.0
+    exact = np.abs(C).sum(axis=0).max()
+    assert O.onenorm_estimate(lambda X: C @ X, lambda X: C.T @ X, n) == pytest.approx(exact, rel=1e-14)
+
+
+def test_onenorm_estimate_lower_bound_and_close():
+    # est = ||B x||_1 for some ||x||_1 = 1, so est <= ||B||_1; Higham and Tisseur report it within a
+    # small factor, usually exact; scipy's implementation of the same algorithm (its own random
+    # columns) is the library cross-check
+    import scipy.sparse.linalg as sl
+    rng = np.random.default_rng(0)
+    ratios, scipy_ratios = [], []
+    for trial in range(40):
+        n = int(rng.integers(5, 80))
+        B = rng.standard_normal((n, n))
+        exact = np.abs(B).sum(axis=0).max()
+        est = O.onenorm_estimate(lambda X: B @ X, lambda X: B.T @ X, n, seed=trial)
+        assert est <= exact * (1 + 1e-12)
+        ratios.append(est / exact)
+        scipy_ratios.append(sl.onenormest(B) / exact)
+    assert min(ratios) > 0.5 and np.mean(ratios) > 0.85
+    assert abs(np.mean(ratios) - np.mean(scipy_ratios)) < 0.1
+
+
+@pytest.mark.parametrize("kappa", [1e0, 1e2, 1e4, 1e6, 1e7])
+def test_cholqr_probe_is_a_lower_bound(kappa):
+    # Sec. II-C: kappa_2(A) >= sqrt(q / (u (1 + q))), q = ||I - Q^T Q||_2 of CholQR
+    A = inputs.make_matrix(4096, 32, kappa, seed=3)
+    est, q = O.cholqr_probe(A)
+    k2 = O.cond2(A)
+    if kappa >= 1e2:   # once CholQR's loss of orthogonality exceeds the rounding floor
+        assert k2 / 100 <= est <= k2
+    else:              # at kappa ~ 1, q sits on the floor of a few u: the value is O(1)
+        assert q < 32 * O.U_FP64 and est < 8
+    assert O.cholqr_probe(inputs.make_matrix(4096, 32, 1e10, seed=3))[0] == math.inf   # breakdown
+
+
+@pytest.mark.parametrize("kappa", [1e0, 1e3, 1e6])
+def test_onenorm_regime_estimate_brackets_kappa(kappa):
+    # kappa_2^2 <= n ||G||_1 ||G^-1||_1 <= n^2 kappa_2^2 with the exact norm; the estimate of
+    # ||G^-1||_1 is a lower bound within a small factor of it
+    m, n = 4096, 24
+    A = inputs.make_matrix(m, n, kappa, seed=5)
+    est, g1, ginv1 = O.onenorm_regime_estimate(A)
+    G = A.T @ A
+    exact = np.abs(np.linalg.inv(G)).sum(axis=0).max()
+    assert g1 == pytest.approx(np.abs(G).sum(axis=0).max(), rel=1e-15)
+    assert ginv1 <= exact * (1 + 1e-8) and ginv1 >= exact / 3
+    k2 = O.cond2(A)
+    assert est >= k2 / 2 and est <= n * k2 * (1 + 1e-8)
+    assert O.onenorm_regime_estimate(inputs.make_matrix(m, n, 1e10, seed=5))[0] == math.inf
