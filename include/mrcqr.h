@@ -248,6 +248,26 @@ int mrcqr_sketch_qr(int64_t n, int64_t s, const double* Y, int prec, double* Rs,
 int mrcqr_cholqr2(int64_t m, int64_t n, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
                   int64_t ldr, mrcqr_stream_t stream);
 
+/* Regime estimates without learning (Sec. II-C): an estimate of kappa_2(A)
+ * and the sketch precision it calls for (0 half: kappa <= 1e4, 1 single:
+ * kappa <= 1e8, 2 double), before any factorization.
+ *  CHOLQR_PROBE: Algorithm 1 on A (Gram, Cholesky, Q = A R^{-1}, all products
+ *    emulated FP64 as in mrcqr_factor), q = ||I - Q^T Q||_2 by power iteration
+ *    on the n x n Gram of Q, kappa = sqrt(q / (u (1 + q))) with u = 2^-53 (the
+ *    probe's lower bound).  out = {kappa, regime, q, 0}.
+ *  ONENORM: G = A^T A, kappa = sqrt(n ||G||_1 est), est <= ||G^-1||_1 from the
+ *    block 1-norm estimator of Higham and Tisseur (t = 2, at most 5 iterations,
+ *    random +-1 columns from Philox with key `seed`, G^-1 applied through the
+ *    Cholesky factor; exact for n <= 4).  out = {kappa, regime, ||G||_1, est}.
+ * A Cholesky breakdown (kappa_2(A) beyond about 1e8) gives kappa = inf and
+ * regime 2.  A: DEVICE double m x n, column-major, ld lda >= m, read-only,
+ * 1 <= n <= 512, n <= m < 2^31; out: DEVICE double[4], written on `stream`.
+ * Allocates its workspace (m x n doubles more for the probe) with
+ * cudaMallocAsync on `stream`.  INVALID before any launch on bad arguments. */
+typedef enum { MRCQR_REGIME_CHOLQR_PROBE = 0, MRCQR_REGIME_ONENORM = 1 } mrcqr_regime_method_t;
+int mrcqr_regime_estimate(int64_t m, int64_t n, const double* A, int64_t lda, int method, uint64_t seed,
+                          double* out, mrcqr_stream_t stream);
+
 /* Algorithm 2 steps 7-9 with a given preconditioner: Q, R_c = CholQR(A R_s^{-1})
  * (Algorithm 1) and R = R_c R_s.  With Rs = I this is Algorithm 1 on A.
  * Status (breakdown) through mrcqr_get_last_status. */

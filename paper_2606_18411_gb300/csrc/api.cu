@@ -522,6 +522,51 @@ int mrcqr_cholqr2(int64_t m, int64_t n, const double* A, int64_t lda, double* Q,
   return finish(st);
 }
 
+int mrcqr_regime_estimate(int64_t m, int64_t n, const double* A, int64_t lda, int method, uint64_t seed,
+                          double* out, mrcqr_stream_t stream) {
+  if (!A || !out || n < 1 || n > kMaxN || m < n || m >= (int64_t(1) << 31) || lda < m) return MRCQR_ERR_INVALID;
+  if (method != MRCQR_REGIME_CHOLQR_PROBE && method != MRCQR_REGIME_ONENORM) return MRCQR_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(m, (int)n, (int)n);
+  const bool probe = method == MRCQR_REGIME_CHOLQR_PROBE;
+  const size_t off_w = p.total;   // Q = A R^{-1} of the probe
+  const size_t total = off_w + (probe ? align_up(sizeof(double) * (size_t)m * n) : 0);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCQR_ERR_ALLOC;
+  }
+  Ctl* ctl = at<Ctl>(ws, p.off_ctl);
+  double* Rc = at<double>(ws, p.off_rc);
+  double* E = at<double>(ws, p.off_e);
+  double* Rs = at<double>(ws, p.off_rs);
+  double* RsT = at<double>(ws, p.off_rst);
+  double* rinv = at<double>(ws, p.off_rinv);
+  uint32_t* colhi = at<uint32_t>(ws, p.off_colhi);
+  long long* part = at<long long>(ws, p.off_ozpart);
+  launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, P_FP64, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
+  // G = A^T A (emulated FP64) and its Cholesky factor (a breakdown raises the level status)
+  launch(SG_SYRK, 0, st, [&] { launch_syrk_oz(p.m, p.n, A, lda, p.oz, colhi, part, Rc, ctl, 0, st); });
+  if (!probe) cudaMemcpyAsync(E, Rc, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st);
+  launch(SG_CHOL, 0, st, [&] { launch_chol(p.n, Rc, ctl, 0, st); });
+  cudaMemcpyAsync(Rs, Rc, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st);
+  launch(SG_PREP, 0, st, [&] { launch_rs_prepare((int)n, Rs, RsT, rinv, st); });
+  if (probe) {
+    // Q = A R^{-1} and E = Q^T Q: the CholQR run whose loss of orthogonality bounds kappa
+    double* W = at<double>(ws, off_w);
+    launch(SG_TRSM, 0, st, [&] {
+      launch_trsm_oz(p.m, p.n, A, lda, RsT, rinv, at<uint32_t>(ws, p.off_tcole), at<unsigned char>(ws, p.off_trd), W,
+                     m, ctl, 0, st, colhi);
+    });
+    launch(SG_CHECK, 0, st, [&] { launch_syrk_oz(p.m, p.n, W, m, p.oz, colhi, part, E, ctl, 0, st, true); });
+    launch(SG_JUDGE, 0, st, [&] { launch_probe(p.n, E, ctl, out, st); });
+  } else {
+    launch(SG_JUDGE, 0, st, [&] { launch_onenorm(p.n, E, Rc, RsT, rinv, seed, ctl, out, st); });
+  }
+  cudaFreeAsync(ws, st);
+  return finish(st);
+}
+
 int mrcqr_cholqr_precond(int64_t m, int64_t n, const double* A, int64_t lda, const double* Rs, double* Q,
                          int64_t ldq, double* R, int64_t ldr, mrcqr_stream_t stream) {
   int rc = validate(m, n, A, lda, Q, ldq, R, ldr, 1);

@@ -144,6 +144,14 @@ void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, con
 void launch_finalize_oz(int64_t m, int n, double* Q, int64_t ldq, const double* XT, uint32_t* colE,
                         unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st, uint32_t* colHiOut = nullptr);
 
+// --- regime estimates without learning (regime.cu) -------------------------------
+// out (DEVICE double[4]) = {kappa estimate, regime 0/1/2, q, 0} from the Gram E = Q^T Q of a CholQR run,
+// or {kappa estimate, regime, ||G||_1, est ||G^-1||_1} from G = A^T A and its Cholesky factor R
+// (RT, rinv as launch_rs_prepare writes them).  A raised level status (Cholesky breakdown) gives inf.
+void launch_probe(int n, const double* E, const Ctl* ctl, double* out, cudaStream_t st);
+void launch_onenorm(int n, const double* G, const double* R, const double* RT, const double* rinv, uint64_t seed,
+                    const Ctl* ctl, double* out, cudaStream_t st);
+
 // --- learned selector (selector.cu) --------------------------------------------
 int selector_num_params();
 bool selector_ready();

@@ -218,6 +218,20 @@ def sketch_transform(A: torch.Tensor, c: int, transform="rfft", prec="fp64", see
     return Y
 
 
+REGIME_METHODS = {"probe": 0, "onenorm": 1}
+
+
+def regime_estimate(A: torch.Tensor, method="probe", seed: int = 0, out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """Device tensor [kappa estimate, regime (0 fp16, 1 fp32, 2 fp64), q or ||A^T A||_1, 0 or est
+    ||(A^T A)^-1||_1] from the CholQR probe or the block 1-norm estimate (Sec. II-C)."""
+    m, n = A.shape
+    o = out if out is not None else torch.empty(4, dtype=torch.float64, device=A.device)
+    check(_lib.load().mrcqr_regime_estimate(m, n, A.data_ptr(), _ld(A, "A"), REGIME_METHODS[method], seed,
+                                            o.data_ptr(), _stream(stream)), "mrcqr_regime_estimate")
+    return o
+
+
 def sketch(A: torch.Tensor, s: int, prec="fp64", seed: int = 0, variant: int = 0, stream=None) -> torch.Tensor:
     """Y = sqrt(m/s) P F D A in precision prec (variant 0 auto, 1 SIMT, 2 tensor cores)."""
     m, n = A.shape

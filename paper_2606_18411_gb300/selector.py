@@ -204,6 +204,83 @@ def ladder_cost(start: int, label: int, costs) -> float:
     return costs[start] if start >= label else float(sum(costs[start:label + 1]))
 
 
+def heldout_matrices(count: int, m: int, seed0: int = 2, n_range=(32, 256), device="cuda"):
+    """The matrices of ``make_dataset(count, m, seed0)`` in order (the same draws), with (n, kappa, kind)."""
+    rng = np.random.default_rng(seed0)
+    for i in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        kind = SPECTRA[int(rng.integers(len(SPECTRA)))]
+        kappa = float(10.0 ** rng.uniform(0.0, 16.0))
+        yield i, inputs.make_matrix_torch(m, n, kappa, kind=kind, seed=seed0 * 1000003 + i, device=device), \
+            (n, kappa, kind)
+
+
+def evaluate_baselines(count: int, m: int, weights: str = DEFAULT_WEIGHTS, log_every: int = 0) -> dict:
+    """The learned selector against the two estimators of Sec. II-C (the CholQR probe and the block
+    1-norm estimate on A^T A) on the held-out set of ``train``: accuracy against the cheapest passing
+    precision, under-predictions (each costs an escalation), and the cost of the precision ladder
+    plus each estimator's own time, relative to the ideal choice (estimator time in units of one
+    FP16-sketch run of the cost measurement)."""
+    costs, times = measure_costs(m=m)
+    load_into_library(weights)
+    dev = "cuda"
+    methods = ("learned", "probe", "onenorm")
+    chosen = {k: [] for k in methods}
+    est_ms = {k: 0.0 for k in methods}
+    labels = []
+    out = torch.empty(4, dtype=torch.float64, device=dev)
+    stats = torch.zeros(8, dtype=torch.float64, device=dev)
+    feat = torch.empty(NF, dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    for i, A, _ in heldout_matrices(count, m):
+        mm, n = A.shape
+        p16 = passes(A, "fp16", seed=i)
+        p32 = True if p16 else passes(A, "fp32", seed=i)
+        labels.append(0 if p16 else (1 if p32 else 2))
+        # learned: the choice AUTO makes; its own cost is the FP16 sketch, its QR and the features
+        e0.record()
+        features_of(A, seed=i, out=feat)
+        e1.record()
+        torch.cuda.synchronize()
+        est_ms["learned"] += e0.elapsed_time(e1)
+        Q = M.empty_colmajor(mm, n, device=dev)
+        R = M.empty_colmajor(n, n, device=dev)
+        M.factor_ex(A, Q, R, prec="auto", seed=i, stats_device=stats)
+        torch.cuda.synchronize()
+        chosen["learned"].append(int(_lib.Stats.from_buffer_copy(stats.cpu().numpy().tobytes()).selector_choice))
+        del Q, R
+        for meth in ("probe", "onenorm"):
+            e0.record()
+            M.regime_estimate(A, meth, seed=i, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            est_ms[meth] += e0.elapsed_time(e1)
+            chosen[meth].append(int(out[1].item()))
+        if log_every and (i + 1) % log_every == 0:
+            print(f"  {i + 1}/{count} matrices, {time.time() - t0:.0f} s", flush=True)
+    y = np.array(labels)
+    ideal = sum(ladder_cost(int(l), int(l), costs) for l in y)
+    rep = {"heldout_count": count, "m": m, "label_counts": np.bincount(y, minlength=3).tolist(),
+           "relative_costs": costs, "run_ms": times,
+           "always_fp32_relative_cost": sum(ladder_cost(1, int(l), costs) for l in y) / ideal,
+           "always_fp64_relative_cost": sum(ladder_cost(2, int(l), costs) for l in y) / ideal, "methods": {}}
+    for k in methods:
+        c = np.array(chosen[k])
+        conf = np.zeros((3, 3), dtype=int)
+        for a, b in zip(y, c):
+            conf[a, b] += 1
+        ladder = sum(ladder_cost(int(ci), int(li), costs) for ci, li in zip(c, y))
+        est_units = est_ms[k] / times[0]
+        rep["methods"][k] = {"accuracy": float(np.mean(c == y)), "under_predictions": int(np.sum(c < y)),
+                             "confusion_true_by_chosen": conf.tolist(),
+                             "estimator_ms_mean": est_ms[k] / count,
+                             "relative_cost_ladder": ladder / ideal,
+                             "relative_cost_with_estimator": (ladder + est_units) / ideal}
+    rep["seconds"] = time.time() - t0
+    return rep
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -214,10 +291,22 @@ def main():
     t.add_argument("--epochs", type=int, default=40)
     t.add_argument("--out", default=DEFAULT_WEIGHTS)
     t.add_argument("--report", default=None)
+    b = sub.add_parser("baselines")
+    b.add_argument("--heldout", type=int, default=2000)
+    b.add_argument("--m", type=int, default=1 << 16)
+    b.add_argument("--weights", default=DEFAULT_WEIGHTS)
+    b.add_argument("--report", default=None)
     args = ap.parse_args()
     from . import build
     build.build()
     torch.cuda.set_device(0)
+    if args.cmd == "baselines":
+        rep = evaluate_baselines(args.heldout, args.m, args.weights, log_every=500)
+        print(json.dumps(rep), flush=True)
+        if args.report:
+            with open(args.report, "w") as f:
+                json.dump(rep, f, indent=1)
+        return
     t0 = time.time()
     costs, times = measure_costs(m=args.m)
     print(f"relative run costs fp16/fp32/fp64: {costs} ({times} ms)", flush=True)
