@@ -313,6 +313,13 @@ int mrcqr_gram(int64_t m, int64_t n, const double* W, int64_t ldw, double* G, in
 int mrcqr_finalize_q(int64_t m, int64_t n, double* Q, int64_t ldq, const double* X, int64_t ldx, int fp64_products,
                      mrcqr_stream_t stream);
 
+/* Test hook for the bounded device waits: one CTA waits on a barrier that
+ * nothing completes, with the bounded wait of the tensor-core pipelines
+ * (each poll blocks for a hardware time slice), and writes MRCQR_ERR_TIMEOUT
+ * to *status (DEVICE int32) when `polls` polls (1 .. 2^20) run out; the
+ * context stays usable.  INVALID on bad arguments. */
+int mrcqr_debug_wait_timeout(uint32_t polls, int32_t* status, mrcqr_stream_t stream);
+
 /* Allocation-free variant of mrcqr_sketch_qr.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * when they need R_s -- code running under another framework's memory

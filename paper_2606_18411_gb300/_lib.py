@@ -75,6 +75,7 @@ SIGNATURES = {
     "mrcqr_sketch_ex": ([_i64, _i64, _vp, _i64, _i64, _i32, _u64, _i32, _vp, _vp], _i32),
     "mrcqr_sketch_transform": ([_i64, _i64, _vp, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp], _i32),
     "mrcqr_regime_estimate": ([_i64, _i64, _vp, _i64, _i32, _u64, _vp, _vp], _i32),
+    "mrcqr_debug_wait_timeout": ([ctypes.c_uint32, _vp, _vp], _i32),
     "mrcqr_sketch_qr": ([_i64, _i64, _vp, _i32, _vp, _vp], _i32),
     "mrcqr_last_sketch_variant": ([], _i32),
     "mrcqr_cholqr_precond": ([_i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp], _i32),

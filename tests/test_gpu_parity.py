@@ -308,3 +308,19 @@ def test_leading_dimensions(M):
     assert M.last_status()["status"] == "OK"
     Qh, Rh = _np(Q), _np(Rbig)
     assert O.orthogonality_error(Qh)[0] <= 1e-13 and O.residual_error(A, Qh, Rh)[0] <= 1e-13
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(M):
+    # a wait on a barrier that nothing completes gives up after its bound and reports TIMEOUT
+    # (no fault, trap or endless loop); the context then still runs a factorization
+    import torch
+    from paper_2606_18411_gb300 import _lib
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    assert _lib.load().mrcqr_debug_wait_timeout(4096, status.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 7                       # MRCQR_ERR_TIMEOUT
+    A = inputs.make_matrix(4096, 16, 1e3, seed=1)
+    Q, R = M.factor(M.to_colmajor(A), prec="fp16")
+    torch.cuda.synchronize()
+    assert M.last_status()["status"] == "OK"
+    assert O.orthogonality_error(Q.cpu().numpy())[0] <= 1e-13
