@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Bit-exact: signs and sample indices.  Floating point: the spec limits
+Bit-exact: signs and sample indices.  Floating point: the parity bounds
 -- sketch within 5e-3 (FP16/BF16), 1e-5 (FP32) relative Frobenius of the FP64
 oracle sketch (1e-13 for the FP64 sketch: same arithmetic, different
 summation order); ||I - Q^T Q||_2 <= 1e-13 and ||A - QR||_F / ||A||_F <= 1e-13
