@@ -173,7 +173,9 @@ typedef struct mrcqr_batched_opts {
   int32_t fp64_products;  /* 0 (default): emulated FP64 products, the single-problem tensor-core kernels of the
                              FP64 sketch and stage 2 run per problem on side streams (fork/join inside the plan);
                              1: every phase grouped with FP64 FMA kernels */
-  int32_t reserved;
+  int32_t transform;      /* mrcqr_transform_t of every problem's sketch (default DCT): 2n sampled rows, or 2n
+                             bins of the real FFT (then 2n <= floor(m/2) + 1 for every problem, and 4n <= 8192
+                             for MRCQR_TRANSFORM_RFFT_REIM; INVALID otherwise) */
 } mrcqr_batched_opts_t;
 
 int mrcqr_batched_plan_create(int count, const int64_t* m, const int64_t* n, const double* const* A,

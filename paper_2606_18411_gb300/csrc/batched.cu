@@ -146,7 +146,7 @@ int ladder(int p, bool escalate, int* lv) {
 // Per-problem workspace layout and work lists for the given tuning.
 void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t* n, const double* const* A,
            const int64_t* lda, double* const* Q, const int64_t* ldq, double* const* R, const int* prec,
-           const uint64_t* seeds, int32_t* status, int check, bool escalate, double tol, size_t* ws_bytes) {
+           const uint64_t* seeds, int32_t* status, int check, bool escalate, double tol, int tf, size_t* ws_bytes) {
   pl.count = count;
   pl.probs.assign(count, Prob{});
   size_t o = 0;
@@ -168,7 +168,9 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     P.ldr = n[i];
     P.m = m[i];
     P.n = (int)n[i];
-    P.s = 2 * P.n;
+    P.tf = tf;
+    P.bins = 2 * P.n;
+    P.s = tf == T_RFFT_REIM ? 2 * P.bins : P.bins;
     P.npad = (P.n + 31) / 32 * 32;
     P.rows_per_chunk = pl.tuning.rows_per_chunk;
     P.chunks = (int)((P.m + P.rows_per_chunk - 1) / P.rows_per_chunk);
@@ -361,7 +363,8 @@ void enqueue_oz(const mrcqr_batched_plan_s& pl, int kind, int level, int i, cuda
   const OzWs& z = pl.oz[i];
   switch (kind) {
     case K_OZ_SKETCH:
-      launch_sketch_oz(P.m, P.n, P.s, P.A, P.lda, P.idx, P.tab, z.seed, z.kp, z.colhi, z.part, P.y, P.ctl, level, st);
+      launch_sketch_oz(P.m, P.n, P.s, P.A, P.lda, P.idx, P.tab, z.seed, z.kp, z.colhi, z.part, P.y, P.ctl, level, st,
+                       P.tf);
       break;
     case K_OZ_STAGE2A:
       launch_trsm_oz(P.m, P.n, P.A, P.lda, P.rst, P.rinv, z.tcole, z.trd, P.Q, P.ldq, P.ctl, level, st, z.colhi);
@@ -505,6 +508,11 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
   *out = nullptr;
   int rc = validate_batch(count, m, n, A, lda, Q, ldq, R, sketch_prec, seeds, status);
   if (rc != MRCQR_OK) return rc;
+  // sketch transform: 2n sampled rows (DCT) or bins (real FFT: at most floor(m/2) + 1; Re + Im rows <= 8192)
+  const int tf = opts ? opts->transform : T_DCT;
+  if (tf < T_DCT || tf > T_RFFT_REIM) return MRCQR_ERR_INVALID;
+  for (int i = 0; i < count; ++i)
+    if (tf != T_DCT && (2 * n[i] > m[i] / 2 + 1 || (tf == T_RFFT_REIM && 4 * n[i] > 8192))) return MRCQR_ERR_INVALID;
   auto* pl = new mrcqr_batched_plan_s();
   const int check = opts ? (opts->check != 0) : 1;
   const bool escalate = opts ? (opts->escalate != 0) : true;
@@ -533,7 +541,7 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
     // size the workspace for the smallest candidates (most partials)
     pl->tuning = Tuning{1024, 2048};
   }
-  build(*pl, count, m, n, A, lda, Q, ldq, R, sketch_prec, seeds, status, check, escalate, tol, &bytes);
+  build(*pl, count, m, n, A, lda, Q, ldq, R, sketch_prec, seeds, status, check, escalate, tol, tf, &bytes);
   if ((async ? cudaMallocAsync(&pl->ws, bytes, st) : cudaMalloc(&pl->ws, bytes)) != cudaSuccess) {
     cudaGetLastError();
     free_streams(*pl);
@@ -543,7 +551,7 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
   pl->ws_bytes = bytes;
   auto upload = [&]() -> int {
     size_t dummy = 0;
-    build(*pl, count, m, n, A, lda, Q, ldq, R, sketch_prec, seeds, status, check, escalate, tol, &dummy);
+    build(*pl, count, m, n, A, lda, Q, ldq, R, sketch_prec, seeds, status, check, escalate, tol, tf, &dummy);
     if (dummy > pl->ws_bytes) return MRCQR_ERR_ALLOC;
     if (async) {   // pageable sources: the copies are staged before these calls return
       if (cudaMemcpyAsync(pl->d_probs, pl->probs.data(), sizeof(Prob) * pl->probs.size(), cudaMemcpyHostToDevice,

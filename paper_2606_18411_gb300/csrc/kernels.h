@@ -19,6 +19,7 @@ struct Prob {
   int64_t lda, ldq, ldr;
   int64_t m;
   int n, s, npad, chunks, splits, ntile_syrk, check, nlevels;
+  int tf, bins;      // sketch transform (T_DCT, T_RFFT, T_RFFT_REIM) and sampled rows or bins; s = rows of Y
   int lvl_prec[kMaxLevels];
   int64_t rows_per_chunk, rows_per_split;
   uint2 key;

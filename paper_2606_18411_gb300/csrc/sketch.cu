@@ -378,7 +378,7 @@ __global__ void kg_init(Group g) {
 __global__ void __launch_bounds__(1024) kg_sample(Group g) {
   for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
     const Prob& P = g.probs[g.items[it].x];
-    sample_block(P.m, P.s, P.key, P.idx);
+    sample_block(P.tf == T_DCT ? P.m : P.m / 2 + 1, P.bins, P.key, P.idx, P.tf == T_RFFT_REIM);
   }
 }
 
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(256) kg_sketch(Group g, int level) {
     const Prob& P = g.probs[w.x];
     if (P.ctl->active != level) continue;
     sketch_simt_block<PREC>(P.A, P.lda, P.m, P.n, P.s, P.idx, P.tab, P.key, P.rows_per_chunk, P.ypart, w.y, w.z,
-                            w.w, T_DCT);
+                            w.w, P.tf);
   }
 }
 
@@ -412,7 +412,7 @@ __global__ void kg_sketch_reduce(Group g, int level) {
     const Prob& P = g.probs[w.x];
     if (P.ctl->active != level) continue;
     const int64_t e = (int64_t)w.y * 256 + threadIdx.x;
-    if (e < (int64_t)P.s * P.n) sketch_reduce_entry(P.n, P.s, P.chunks, P.ypart, P.idx, P.y, P.ctl, e);
+    if (e < (int64_t)P.s * P.n) sketch_reduce_entry(P.n, P.s, P.chunks, P.ypart, P.idx, P.y, P.ctl, e, P.tf, P.m);
   }
 }
 

@@ -135,3 +135,47 @@ def test_batched_rejects_invalid(env):
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     with pytest.raises(M.MrcqrError):
         M.factor_batched([A], [Q], [R], ["fp64"], [0], status)
+
+
+@pytest.mark.parametrize("fp64_products", [0, 1])
+@pytest.mark.parametrize("transform", ["rfft", "rfft_reim"])
+def test_batched_plan_paper_transform(env, transform, fp64_products):
+    # the paper's real-FFT sketch (2n bins per problem) in a batched plan
+    torch, M = env
+    mats, kappas = _batch(SHAPES[:6], seed0=2100)
+    precs = [O.precision_rule(k) for k in kappas]
+    As = [M.to_colmajor(a) for a in mats]
+    Qs = [M.empty_colmajor(*a.shape) for a in mats]
+    Rs = [M.empty_colmajor(a.shape[1], a.shape[1]) for a in mats]
+    status = torch.full((len(mats),), -1, dtype=torch.int32, device="cuda")
+    plan = M.BatchedPlan(As, Qs, Rs, precs, [3] * len(mats), status, use_graph=True, fp64_products=fp64_products,
+                         transform=transform)
+    plan.execute()
+    torch.cuda.synchronize()
+    assert status.cpu().tolist() == [0] * len(mats)
+    for A, Q, R, p in zip(mats, Qs, Rs, precs):
+        Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
+        assert O.orthogonality_error(Qh)[0] <= 1e-13
+        assert O.residual_error(A, Qh, Rh)[0] <= 1e-13
+        if fp64_products == 0:
+            # the same bins, signs and kernels as a single call with that transform: summation order only
+            _, R1 = M.factor(M.to_colmajor(A), prec=p, seed=3, transform=transform, s_factor=2)
+            R1h = R1.cpu().numpy()
+            assert np.linalg.norm(Rh - R1h) <= 1e-9 * np.linalg.norm(R1h)
+    plan.close()
+
+
+def test_batched_plan_rejects_too_few_bins(env):
+    # 2n = 60 bins of a real column with m = 100 (51 distinct bins) do not exist; the DCT plan is fine
+    torch, M = env
+    A = M.to_colmajor(inputs.gaussian(100, 30, seed=2))
+    Q = M.empty_colmajor(100, 30)
+    R = M.empty_colmajor(30, 30)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(M.MrcqrError):
+        M.BatchedPlan([A], [Q], [R], ["fp64"], [0], status, transform="rfft")
+    plan = M.BatchedPlan([A], [Q], [R], ["fp64"], [0], status)
+    plan.execute()
+    torch.cuda.synchronize()
+    assert status.cpu().tolist() == [0]
+    plan.close()
