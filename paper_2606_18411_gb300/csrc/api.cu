@@ -27,7 +27,7 @@ struct Plan {
   int64_t m = 0;
   int n = 0, s = 0, npad = 0, chunks = 0, splits = 0;
   int tf = T_DCT;   // sketch transform; s counts the rows of Y (2 x bins for T_RFFT_REIM)
-  size_t off_ctl = 0, off_idx = 0, off_tab = 0, off_tabf = 0, off_ypart = 0, off_y = 0, off_sqr = 0, off_rs = 0, off_rst = 0,
+  size_t off_ctl = 0, off_idx = 0, off_tab = 0, off_ypart = 0, off_y = 0, off_sqr = 0, off_rs = 0, off_rst = 0,
          off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, off_feat = 0, off_oze = 0, off_ozx = 0,
          off_colhi = 0, off_ozpart = 0, off_tcole = 0, off_trd = 0, total = 0;
   SyrkOzPlan oz{};
@@ -52,7 +52,6 @@ Plan make_plan(int64_t m, int n, int s, int tf = T_DCT) {
   p.off_ctl = take(sizeof(Ctl));
   p.off_idx = take(sizeof(uint32_t) * (size_t)s);
   p.off_tab = take(sizeof(double) * (size_t)(m + 1));
-  p.off_tabf = take(sizeof(float) * (size_t)(m + 1));
   p.off_ypart = take(sizeof(double) * (size_t)p.chunks * s * n);
   p.off_y = take(sizeof(double) * (size_t)s * n);
   p.off_sqr = take(sqr_workspace_bytes(n, s));
@@ -247,7 +246,7 @@ int enqueue_sketch(const Plan& p, void* ws, int prec, int variant, int fp64_prod
   }
   double* ypart = at<double>(ws, p.off_ypart);
   launch(SG_SKETCH, lvl, st, [&] {
-    used = launch_sketch(prec, variant, A, lda, p.m, p.n, p.s, idx, tab, at<float>(ws, p.off_tabf), seed, p.chunks,
+    used = launch_sketch(prec, variant, A, lda, p.m, p.n, p.s, idx, tab, seed, p.chunks,
                          ypart, ctl, lvl, st, p.tf);
   });
   launch(SG_SKREDUCE, lvl, st, [&] {
@@ -368,7 +367,7 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
   double* tab = at<double>(ws, p.off_tab);
   launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, nlevels, lv[0], lv[1], lv[2], lv[3], tol); } });
   launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, bins, seed, idx, ctl, st, tf); });
-  launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, at<float>(ws, p.off_tabf), st); });
+  launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, st); });
   for (int L = 0; L < nlevels; ++L) {
     double* y = at<double>(ws, p.off_y);
     g_sketch_variant_last = enqueue_sketch(p, ws, lv[L], variant, fp64p, A, lda, seed, y, ctl, L, st);
@@ -463,7 +462,7 @@ int mrcqr_sketch_transform(int64_t m, int64_t n, const double* A, int64_t lda, i
   double* tab = at<double>(ws, p.off_tab);
   launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, sketch_prec, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
   launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, (int)c, seed, idx, ctl, st, transform); });
-  launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, at<float>(ws, p.off_tabf), st); });
+  launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, st); });
   g_sketch_variant_last = enqueue_sketch(p, ws, sketch_prec, variant, 0, A, lda, seed, Y, ctl, 0, st);
   cudaFreeAsync(ws, st);
   return finish(st);

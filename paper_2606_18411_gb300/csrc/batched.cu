@@ -190,7 +190,7 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     f[0] = take(sizeof(Ctl));
     f[1] = take(sizeof(uint32_t) * P.s);
     f[2] = take(sizeof(double) * (size_t)(P.m + 1));
-    f[3] = take(sizeof(float) * (size_t)(P.m + 1));
+    f[3] = take(0);   // (unused slot)
     f[4] = take(sizeof(double) * (size_t)P.chunks * P.s * P.n);
     f[5] = take(sizeof(double) * (size_t)P.s * P.n);
     f[6] = take(sizeof(double) * (size_t)P.s * P.n);
@@ -330,7 +330,6 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     P.ctl = reinterpret_cast<Ctl*>(base + f[0]);
     P.idx = reinterpret_cast<uint32_t*>(base + f[1]);
     P.tab = reinterpret_cast<double*>(base + f[2]);
-    P.tabf = reinterpret_cast<float*>(base + f[3]);
     P.ypart = reinterpret_cast<double*>(base + f[4]);
     P.y = reinterpret_cast<double*>(base + f[5]);
     P.sqrw = base + f[6];

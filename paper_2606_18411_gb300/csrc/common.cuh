@@ -82,16 +82,6 @@ __device__ __forceinline__ float round_to_bf16(double x) {
   asm("cvt.rn.bf16.f64 %0, %1;" : "=h"(u) : "d"(x));
   return __bfloat162float(__ushort_as_bfloat16(u));
 }
-__device__ __forceinline__ unsigned short bits_f16(double x) {
-  unsigned short u;
-  asm("cvt.rn.f16.f64 %0, %1;" : "=h"(u) : "d"(x));
-  return u;
-}
-__device__ __forceinline__ unsigned short bits_bf16(double x) {
-  unsigned short u;
-  asm("cvt.rn.bf16.f64 %0, %1;" : "=h"(u) : "d"(x));
-  return u;
-}
 
 template <int PREC>
 __device__ __forceinline__ float round_to_p(double x) {
@@ -161,13 +151,6 @@ __device__ __forceinline__ void cos_phase_bits(const double* __restrict__ tab, i
   const uint2 w = __ldg(reinterpret_cast<const uint2*>(tab) + r);
   lo = w.x;
   hi = w.y ^ neg;
-}
-
-// Same phase from the FP32 copy of the table.
-__device__ __forceinline__ float cos_phase_f(const float* __restrict__ tabf, int64_t r, int64_t m) {
-  if (r >= 2 * m) r = 4 * m - r;
-  if (r > m) return -__ldg(tabf + (2 * m - r));
-  return __ldg(tabf + r);
 }
 
 // ---------------------------------------------------------------------------

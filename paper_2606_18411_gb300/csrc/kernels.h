@@ -27,7 +27,6 @@ struct Prob {
   Ctl* ctl;
   uint32_t* idx;
   double* tab;
-  float* tabf;
   double* ypart;
   double* y;
   void* sqrw;
@@ -71,17 +70,17 @@ void launch_g_publish(const Group& g, cudaStream_t st);
 // tf: the sketch transform (T_DCT, T_RFFT, T_RFFT_REIM of common.cuh); s rows (DCT) or bins (real FFT), written
 // to idx[0..s) and, for T_RFFT_REIM, their Im rows to idx[s..2s).
 void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ctl, cudaStream_t st, int tf = 0);
-void launch_costab(int64_t m, double* tab, float* tabf, cudaStream_t st);
+void launch_costab(int64_t m, double* tab, cudaStream_t st);
 int sketch_chunks(int64_t m, int n, int s);
 // variant: 0 = auto (tensor cores when eligible), 1 = SIMT, 2 = tensor cores (falls back to SIMT when
 // the TMA preconditions fail).  Returns the variant launched (1 or 2).
 int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m, int n, int s,
-                  const uint32_t* idx, const double* tab, const float* tabf, uint64_t seed, int chunks,
+                  const uint32_t* idx, const double* tab, uint64_t seed, int chunks,
                   double* Ypart, Ctl* ctl, int level, cudaStream_t st, int tf = 0);
 // tensor-core sketch (sketch_tc.cu): FP16/BF16/FP32, A 16-byte aligned, lda even
 bool sketch_tc_eligible(int prec, const double* A, int64_t lda);
 bool launch_sketch_tc(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,
-                      const double* tab, const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl,
+                      const double* tab, uint64_t seed, int chunks, double* Ypart, Ctl* ctl,
                       int level, cudaStream_t st, int tf = 0);
 void launch_sketch_reduce(int64_t m, int n, int s, int chunks, const double* Ypart, const uint32_t* idx,
                           double* Y, Ctl* ctl, int level, cudaStream_t st, int tf = 0);

@@ -108,12 +108,6 @@ __device__ __forceinline__ float small_int_to_float(int v) {
   return __int_as_float(0x4B400000 + v) - 12582912.0f;
 }
 
-// Packed FP16 pair of two signed digits.
-__device__ __forceinline__ uint32_t pack_f16x2(int v0, int v1) {
-  const __half2 h = __floats2half2_rn(small_int_to_float(v0), small_int_to_float(v1));
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-
 // Adds one level's exact FP32 accumulator (an integer, |v| <= 2^24) into the
 // 64-bit halves of T.
 __device__ __forceinline__ void add_level(int L, float v, long long& hi, long long& lo) {

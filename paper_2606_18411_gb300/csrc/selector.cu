@@ -411,11 +411,6 @@ __global__ void k_mlp_reduce_adamw(int nparts, const float* __restrict__ part, c
   wbf16[p] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
 }
 
-__global__ void k_to_bf16(int n, const float* __restrict__ src, unsigned short* __restrict__ dst) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = __bfloat16_as_ushort(__float2bfloat16_rn(src[i]));
-}
-
 // Per-device selector weights used by MRCQR_PREC_AUTO.
 struct DevSel {
   unsigned short* w = nullptr;
@@ -491,10 +486,6 @@ void launch_mlp_reduce_adamw(int nparts, const float* part, const float* loss_pa
                              float wd, int step, int apply, float* grad_out, float* loss_out, cudaStream_t st) {
   { ::mrcqr::note_launch(); k_mlp_reduce_adamw<<<(kNParams + 255) / 256, 256, 0, st>>>(nparts, part, loss_part, master, mom, var, wbf16, lr,
                                                              beta1, beta2, eps, wd, step, apply, grad_out, loss_out); }
-}
-
-void launch_to_bf16(int n, const float* src, unsigned short* dst, cudaStream_t st) {
-  { ::mrcqr::note_launch(); k_to_bf16<<<(n + 255) / 256, 256, 0, st>>>(n, src, dst); }
 }
 
 }  // namespace mrcqr

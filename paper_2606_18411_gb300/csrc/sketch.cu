@@ -102,19 +102,18 @@ void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ct
 }
 
 // ---------------------------------------------------------------------------
-// Quarter-wave table cos(pi q / (2m)), q = 0..m, in FP64 and rounded to FP32.
-__global__ void k_costab(int64_t m, double* __restrict__ tab, float* __restrict__ tabf) {
+// Quarter-wave table cos(pi q / (2m)), q = 0..m, in FP64.
+__global__ void k_costab(int64_t m, double* __restrict__ tab) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q <= m) {
     const double c = cospi((double)q / (2.0 * (double)m));
     tab[q] = c;
-    tabf[q] = (float)c;
   }
 }
 
-void launch_costab(int64_t m, double* tab, float* tabf, cudaStream_t st) {
+void launch_costab(int64_t m, double* tab, cudaStream_t st) {
   const int64_t nq = m + 1;
-  { ::mrcqr::note_launch(); k_costab<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(m, tab, tabf); }
+  { ::mrcqr::note_launch(); k_costab<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(m, tab); }
 }
 
 // fl_p exactly as the tensor-core sketch computes it (integer RNE on the
@@ -295,10 +294,10 @@ static int64_t rows_per_chunk(int64_t m, int chunks) {
 }
 
 int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m, int n, int s,
-                  const uint32_t* idx, const double* tab, const float* tabf, uint64_t seed, int chunks,
+                  const uint32_t* idx, const double* tab, uint64_t seed, int chunks,
                   double* Ypart, Ctl* ctl, int level, cudaStream_t st, int tf) {
   if (variant != 1 && sketch_tc_eligible(prec, A, lda) &&
-      launch_sketch_tc(prec, A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf))
+      launch_sketch_tc(prec, A, lda, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf))
     return 2;
   const dim3 grid(chunks, (s + kSkST - 1) / kSkST, (n + kSkNT - 1) / kSkNT);
   const int64_t rpc = rows_per_chunk(m, chunks);
@@ -390,7 +389,6 @@ __global__ void kg_costab(Group g) {
     if (q <= P.m) {
       const double c = cospi((double)q / (2.0 * (double)P.m));
       P.tab[q] = c;
-      P.tabf[q] = (float)c;
     }
   }
 }

@@ -122,7 +122,7 @@ struct Phase {
 template <int PREC, int MT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sketch_tc(const __grid_constant__ CUtensorMap tmapA, int64_t m, int n, int s, const uint32_t* __restrict__ idx,
-                const double* __restrict__ tab, const float* __restrict__ tabf, uint2 key, int64_t rows_per_chunk,
+                const double* __restrict__ tab, uint2 key, int64_t rows_per_chunk,
                 double* __restrict__ Ypart, Ctl* ctl, int level, int tf) {
   using C = Cfg<PREC, MT>;
   constexpr int T = C::T;
@@ -384,7 +384,7 @@ EncodeFn encode_fn() {
 
 template <int PREC, int MT>
 bool launch_tc(const CUtensorMap& map, int64_t m, int n, int s, const uint32_t* idx, const double* tab,
-               const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level, cudaStream_t st,
+               uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level, cudaStream_t st,
                int tf) {
   using C = Cfg<PREC, MT>;
   const size_t smem = C::SMEM + 1024;
@@ -394,14 +394,14 @@ bool launch_tc(const CUtensorMap& map, int64_t m, int n, int s, const uint32_t* 
   int64_t rpc = (m + chunks - 1) / chunks;
   rpc = (rpc + 63) / 64 * 64;
   const dim3 grid((s + kM * MT - 1) / (kM * MT), (n + kN - 1) / kN, chunks);
-  { ::mrcqr::note_launch(); k_sketch_tc<PREC, MT><<<grid, kThreads, smem, st>>>(map, m, n, s, idx, tab, tabf, seed_key(seed), rpc, Ypart, ctl,
+  { ::mrcqr::note_launch(); k_sketch_tc<PREC, MT><<<grid, kThreads, smem, st>>>(map, m, n, s, idx, tab, seed_key(seed), rpc, Ypart, ctl,
                                                       level, tf); }
   return true;
 }
 
 template <int PREC>
 bool launch_prec(const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx, const double* tab,
-                 const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level, cudaStream_t st,
+                 uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level, cudaStream_t st,
                  int tf) {
   EncodeFn enc = encode_fn();
   if (!enc) return false;
@@ -414,8 +414,8 @@ bool launch_prec(const double* A, int64_t lda, int64_t m, int n, int s, const ui
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
-  if (s > kM) return launch_tc<PREC, 2>(map, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf);
-  return launch_tc<PREC, 1>(map, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf);
+  if (s > kM) return launch_tc<PREC, 2>(map, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf);
+  return launch_tc<PREC, 1>(map, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf);
 }
 
 }  // namespace
@@ -427,12 +427,12 @@ bool sketch_tc_eligible(int prec, const double* A, int64_t lda) {
 }
 
 bool launch_sketch_tc(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,
-                      const double* tab, const float* tabf, uint64_t seed, int chunks, double* Ypart, Ctl* ctl,
+                      const double* tab, uint64_t seed, int chunks, double* Ypart, Ctl* ctl,
                       int level, cudaStream_t st, int tf) {
   switch (prec) {
-    case P_FP16: return launch_prec<P_FP16>(A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf);
-    case P_BF16: return launch_prec<P_BF16>(A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf);
-    case P_FP32: return launch_prec<P_FP32>(A, lda, m, n, s, idx, tab, tabf, seed, chunks, Ypart, ctl, level, st, tf);
+    case P_FP16: return launch_prec<P_FP16>(A, lda, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf);
+    case P_BF16: return launch_prec<P_BF16>(A, lda, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf);
+    case P_FP32: return launch_prec<P_FP32>(A, lda, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf);
     default: return false;
   }
 }

@@ -121,30 +121,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "r"(smem_u32(bar)), "r"(parity));
   return ok != 0;
 }
-// Plain arrive (count 1), release semantics at CTA scope.
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 // Bounded wait: gives up after `limit` polls (each poll already blocks for a
 // hardware-defined time slice) and returns false.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = 1u << 24) {
   for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
-}
-
-// Named barrier over `count` threads (a multiple of 32), and the same barrier
-// returning the OR of a predicate over the participating threads.
-__device__ __forceinline__ void named_sync(int id, int count) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool named_sync_or(int id, int count, bool v) {
-  uint32_t r;
-  asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, %2, %3, q;\nselp.u32 %0, 1, 0, p;\n}\n"
-               : "=r"(r)
-               : "r"((uint32_t)v), "r"(id), "r"(count)
-               : "memory");
-  return r != 0;
 }
 
 // 2-D TMA tile load into shared memory, completion counted on `bar`.
