@@ -577,3 +577,35 @@ def test_onenorm_regime_estimate_brackets_kappa(kappa):
     k2 = O.cond2(A)
     assert est >= k2 / 2 and est <= n * k2 * (1 + 1e-8)
     assert O.onenorm_regime_estimate(inputs.make_matrix(m, n, 1e10, seed=5))[0] == math.inf
+
+
+# --- Small definitions the sketches and the estimator rest on --------------------
+
+def test_seed_key_splits_the_64_bit_seed():
+    # key = (low word, high word) of the seed, so seed = k0 + 2^32 k1
+    assert O.seed_key(0) == (0, 0)
+    assert O.seed_key(2 ** 40 + 5) == (5, 256)
+    assert O.seed_key(2 ** 64 - 1) == (2 ** 32 - 1, 2 ** 32 - 1)
+
+
+def test_column_scale_exponents_place_the_maximum_in_the_fp16_window():
+    # max_i |a_ij| 2^e_j in [2^13, 2^14) (keeps the FP16 sketch clear of underflow); zero columns keep 0
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((64, 6)) * np.array([1e-30, 1e-5, 1.0, 3.0, 1e12, 0.0])
+    A[0, 2] = 2.0 ** 13                # an exact power of two: e = 0
+    e = O.column_scale_exponents(A)
+    scaled = np.abs(np.ldexp(A, e[None, :])).max(axis=0)
+    assert np.all((scaled[:5] >= 2.0 ** 13) & (scaled[:5] < 2.0 ** 14))
+    assert e[2] == 0 and e[5] == 0
+
+
+def test_random_sign_columns_of_the_estimator():
+    # +-1 entries from Philox at counter (i, 2, draw, 0): deterministic, balanced, distinct across draws
+    a = O.random_sign_column(4096, seed=11, draw=0)
+    assert set(np.unique(a)) == {-1.0, 1.0}
+    np.testing.assert_array_equal(a, O.random_sign_column(4096, seed=11, draw=0))
+    assert abs(a.sum()) <= 5 * math.sqrt(4096)
+    b = O.random_sign_column(4096, seed=11, draw=1)
+    assert abs(float(a @ b)) < 4096 / 4          # a new draw is not (anti-)parallel
+    # the counter's second word separates it from the Rademacher signs (word 0 of counter (i, 0, 0, 0))
+    assert not np.array_equal(a, O.rademacher(4096, 11))
