@@ -239,7 +239,7 @@ int mrcqr_sketch_transform(int64_t m, int64_t n, const double* A, int64_t lda, i
 int mrcqr_sketch_qr(int64_t n, int64_t s, const double* Y, int prec, double* Rs, mrcqr_stream_t stream);
 
 /* CholQR2, the comparison method of the paper's stability experiment (Sec. I-A,
- * Sec. IV-B): Algorithm 1 run twice, R_1 = chol(A^T A), then Q, R_2 = CholQR(A R_1^{-1})
+ * Sec. III-B): Algorithm 1 run twice, R_1 = chol(A^T A), then Q, R_2 = CholQR(A R_1^{-1})
  * (A R_1^{-1} by substitution) and R = R_2 R_1, all products in emulated FP64
  * (as mrcqr_factor).  A (m x n, ld lda), Q (m x n, ld ldq), R (n x n, ld ldr,
  * strict lower triangle set to 0): DEVICE doubles, column-major, caller-owned;
@@ -336,9 +336,12 @@ int mrcqr_debug_wait_timeout(uint32_t polls, int32_t* status, mrcqr_stream_t str
  * (no cudaMalloc/cudaMallocAsync/cudaFree).  All calls share the array and it
  * keeps the last call's contents (each call clears what must start at zero),
  * so calls whose kernels overlap on the GPU race: order them on one stream
- * or with events.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * outside any stream capture. */
+ * or with events.  The stream must belong to the current device (another
+ * device's stream returns MRCQR_ERR_INVALID).  The first call in each CUDA
+ * context looks up the array's address (cudaGetSymbolAddress, with that
+ * device current) and caches it under the context's id, so a device reset
+ * (a new context) is followed by a fresh lookup; make the first call on a
+ * device, and the first after a reset, outside any stream capture. */
 int mrcqr_sketch_qr_noalloc(int64_t n, int64_t s, const double* Y, int prec, double* Rs, mrcqr_stream_t stream);
 
 /* ---- learned sketch-precision selector ------------------------------------

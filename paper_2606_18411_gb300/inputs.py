@@ -3,7 +3,7 @@ tests/bench and the CPU oracle).
 
 It holds no MRCQR arithmetic: it only builds inputs A = U diag(sigma) V^T with
 a prescribed 2-norm condition number, the construction of the paper's
-stability experiment (Sec. IV-B, test-matrix equation), with the spectra used
+stability experiment (Sec. III-B, test-matrix equation), with the spectra used
 by the workloads:
 
 * ``geometric``  sigma_i = kappa^(-i/(n-1)), from 1 down to 1/kappa

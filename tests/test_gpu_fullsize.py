@@ -91,6 +91,13 @@ def test_large_factorizations_rule_precision(env, n):
         o2, rf = _sampled_checks(A, Q, R, k_lead=32, n_extra=16, seed=n + i)
         assert o2 <= TOL and rf <= TOL, (n, kappa, o2, rf)
         assert _r_is_upper_positive(R)
+        if kappa <= 1e8:
+            # R[:16, :16] is the R factor of A[:, :16] (R upper triangular): against the
+            # oracle's Householder QR of those columns, O(kappa u) apart
+            Rl = R[:16, :16].cpu().numpy()
+            Rref = O.householder_qr(A[:, :16].cpu().numpy())
+            err = float(np.linalg.norm(Rl - Rref) / np.linalg.norm(Rref))
+            assert err <= 100 * kappa * O.U_FP64, (n, kappa, err)
         del A, Q, R
         torch.cuda.empty_cache()
 

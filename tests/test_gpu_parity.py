@@ -248,6 +248,44 @@ def test_rule_precision_end_to_end(M, kappa, m, n):
     assert o2 <= 1e-13 and rf <= 1e-13, (o2, rf)
 
 
+# Edge shapes: one column; the smallest legal m (m = s = 2n, every row of the
+# transform sampled); the widest n at a small ragged m.  Checked in
+# double-double, and R against the oracle's R: two backward-stable QRs of the
+# same A with diag(R) > 0 differ by O(kappa u) (the thin QR with a positive
+# diagonal is unique).
+@pytest.mark.parametrize("m,n,kappa", [(2, 1, 1.0), (4097, 1, 1.0), (64, 32, 1e4), (256, 128, 1e8),
+                                       (1024, 512, 1e2), (1031, 512, 1e8), (1031, 512, 1e12), (1030, 509, 1e6)])
+def test_edge_shapes_against_oracle(M, m, n, kappa):
+    prec = O.precision_rule(kappa)
+    A = inputs.make_matrix(m, n, kappa, seed=31 + m + n)
+    st, o2, rf, Qh, Rh = _check_factor(M, A, prec, seed=6)
+    assert st["status"] == "OK", st
+    assert o2 <= 1e-13 and rf <= 1e-13, (o2, rf)
+    assert np.all(np.diag(Rh) > 0)
+    np.testing.assert_array_equal(np.tril(Rh, -1), 0)
+    if kappa <= 1e8:
+        ref = O.mrcqr(A, seed=6, prec=st["prec_used"])
+        assert _rel(Rh, ref.R) <= 100 * kappa * O.U_FP64, _rel(Rh, ref.R)
+        # and against a plain Householder QR of A (the exact-definition check)
+        assert _rel(Rh, O.householder_qr(A)) <= 100 * kappa * O.U_FP64
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e8])
+def test_r_against_oracle_at_rule_precision(M, kappa):
+    # R against the oracle's R (same seed, same sketch precision) and the
+    # oracle's Householder R at C kappa u, ragged m and n
+    m, n = 20011, 96
+    prec = O.precision_rule(kappa)
+    A = inputs.make_matrix(m, n, kappa, seed=41)
+    st, o2, rf, Qh, Rh = _check_factor(M, A, prec, seed=8)
+    assert st["status"] == "OK" and st["retries"] == 0, st
+    ref = O.mrcqr(A, seed=8, prec=prec)
+    assert _rel(Rh, ref.R) <= 100 * kappa * O.U_FP64
+    assert _rel(Rh, O.householder_qr(A)) <= 100 * kappa * O.U_FP64
+    # Q against the oracle's Q: the same O(kappa u) forward error
+    assert _rel(Qh, ref.Q) <= 100 * kappa * O.U_FP64
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
 def test_escalation_on_underestimated_precision(M, prec):
     # Sec. II-C: a too-low precision is detected and re-run higher

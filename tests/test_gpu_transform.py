@@ -7,7 +7,7 @@ Bit-exact: the sampled bins.  Floating point: the sketch within the bounds of
 the DCT sketch tests (5e-3 FP16/BF16, 1e-5 FP32, 1e-13 FP64, relative
 Frobenius against the FP64 oracle); end to end ||I - Q^T Q||_2 <= 1e-13 and
 ||A - QR||_F / ||A||_F <= 1e-13 at the stability experiment's shape
-(m = 2^17, n = 50, c = 3n; Sec. IV-B)."""
+(m = 2^17, n = 50, c = 3n; Sec. III-B)."""
 from __future__ import annotations
 
 import numpy as np
@@ -130,7 +130,7 @@ def _factor(M, A, prec, transform, s_factor=3, escalate=True):
 @pytest.mark.parametrize("kappa", [1e0, 1e4, 1e8, 1e12, 1e16])
 @pytest.mark.parametrize("transform", ["rfft", "rfft_reim"])
 def test_paper_transform_stability_experiment_shape(M, transform, kappa):
-    # Sec. IV-B's shape with the paper's sketch, c = 3n bins, precision by the regime rule
+    # Sec. III-B's shape with the paper's sketch, c = 3n bins, precision by the regime rule
     m, n = 1 << 17, 50
     prec = O.precision_rule(kappa)
     A, U, sig, V = inputs.make_matrix(m, n, kappa, seed=21, return_factors=True)

@@ -372,7 +372,7 @@ def test_mrcqr_invariant_to_sketch_scale():
 @pytest.mark.parametrize("transform,prec,kappa", [("rfft", "fp64", 1e0), ("rfft", "fp64", 1e16), ("rfft", "fp32", 1e8),
                                                   ("rfft_reim", "fp64", 1e8), ("rfft_reim", "fp16", 1e4)])
 def test_mrcqr_paper_transform_stability_experiment_shape(transform, prec, kappa):
-    # Sec. IV-B's shape (m = 2^17, n = 50) with the paper's sketch: c = 3n real-FFT bins (Sec. II-A)
+    # Sec. III-B's shape (m = 2^17, n = 50) with the paper's sketch: c = 3n real-FFT bins (Sec. II-A)
     m, n = 1 << 17, 50
     A, U, sig, V = inputs.make_matrix(m, n, kappa, seed=21, return_factors=True)
     res = O.mrcqr(A, seed=0, prec=prec, s=3 * n, transform=transform)
@@ -398,7 +398,7 @@ def test_reduced_precision_sketch_within_threshold(prec, kappa):
 
 @pytest.mark.parametrize("prec,kappa", [("fp16", 1e8), ("bf16", 1e6), ("fp32", 1e13)])
 def test_reduced_precision_sketch_degrades_beyond_threshold(prec, kappa):
-    # Fig. 1 / Sec. IV-B: past the threshold orthogonality leaves O(u)
+    # Fig. 1 / Sec. III-B: past the threshold orthogonality leaves O(u)
     A = inputs.make_matrix(4096, 32, kappa, seed=13)
     try:
         res = O.mrcqr(A, seed=0, prec=prec)
@@ -421,6 +421,54 @@ def test_theorem1_bound_holds(prec, kappa):
     k1h = O.cond2(O.trsm_right_upper(A, Rh))
     assert k1h <= O.theorem1_bound(k1, eps, kRs) * (1 + 1e-9)
     assert k1 < 10          # SRTT preconditioning: kappa(A R_s^-1) = O(1)
+
+
+def test_theorem1_bound_hand_value_and_limits():
+    # kappa(A R_s^-1) (1 + eps k)/(1 - eps k) with eps k = 0.1 * 5 = 0.5: 2 * 1.5 / 0.5 = 6
+    assert O.theorem1_bound(2.0, 0.1, 5.0) == pytest.approx(6.0, rel=1e-15)
+    assert O.theorem1_bound(3.0, 0.0, 1e10) == 3.0                   # eps k -> 0: the bound is kappa
+    assert O.theorem1_bound(3.0, 1e-20, 1e10) == pytest.approx(3.0, rel=1e-9)
+    assert O.theorem1_bound(1.0, 1.0 - 1e-12, 1.0) > 1e11              # eps k -> 1: unbounded
+    assert math.isinf(O.theorem1_bound(1.0, 0.5, 2.0))                # eps k = 1: no bound
+    assert O.theorem1_bound(1.0, 0.2, 2.0) == pytest.approx(1.4 / 0.6, rel=1e-15)
+
+
+@pytest.mark.parametrize("t", [0.05, 0.3, 0.7, 0.95])
+def test_theorem1_bound_attained(t):
+    # Equality case: A = R_s = c I (kappa(A R_s^-1) = kappa(R_s) = 1) and
+    # E = c diag(t, -t, 0, ...), so ||E|| / ||R_s|| = t and R_s + E = c diag(1+t, 1-t, 1, ...):
+    # kappa(A (R_s + E)^-1) = (1 + t)/(1 - t), the bound with equality.  A
+    # dropped factor, a wrong sign or a swapped ratio fails here.
+    n, c = 6, 3.0
+    Rs = c * np.eye(n)
+    E = np.zeros((n, n))
+    E[0, 0], E[1, 1] = c * t, -c * t
+    A = inputs.make_matrix(64, n, 1.0, seed=2) @ Rs                   # A R_s^-1 orthonormal: kappa 1
+    eps = np.linalg.norm(E, 2) / np.linalg.norm(Rs, 2)
+    got = O.cond2(O.trsm_right_upper(A, Rs + E))
+    bound = O.theorem1_bound(O.cond2(O.trsm_right_upper(A, Rs)), eps, O.cond2(Rs))
+    assert got == pytest.approx((1 + t) / (1 - t), rel=1e-12)
+    assert bound == pytest.approx(got, rel=1e-12)
+
+
+def test_theorem1_bound_random_perturbations():
+    # general R_s and E with eps kappa(R_s) < 1: the bound holds, and is
+    # within a factor (1+t)^2/(1-t)^2 of the true value from below
+    rng = np.random.default_rng(11)
+    for trial in range(20):
+        n = int(rng.integers(2, 12))
+        Rs = np.triu(rng.standard_normal((n, n))) + 4 * np.eye(n)
+        kRs = O.cond2(Rs)
+        E = np.triu(rng.standard_normal((n, n)))
+        t = rng.uniform(0.01, 0.9)
+        E *= t / kRs * np.linalg.norm(Rs, 2) / np.linalg.norm(E, 2)
+        eps = np.linalg.norm(E, 2) / np.linalg.norm(Rs, 2)
+        A = inputs.make_matrix(200, n, 10.0 ** rng.uniform(0, 6), seed=trial)
+        k1 = O.cond2(O.trsm_right_upper(A, Rs))
+        k1h = O.cond2(O.trsm_right_upper(A, Rs + E))
+        b = O.theorem1_bound(k1, eps, kRs)
+        assert k1h <= b * (1 + 1e-10)
+        assert k1h >= k1 * (1 - t) / (1 + t) * (1 - 1e-10)
 
 
 def test_precision_rule_boundaries():

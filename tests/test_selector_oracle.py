@@ -104,3 +104,56 @@ def test_adamw_trains_separable_problem():
     l1 = S.loss_and_grad(theta, X, y, w)[0]
     acc = np.mean(np.argmax(S.forward(theta, X)[0], axis=1) == y)
     assert l1 < 0.3 * l0 and acc > 0.9
+
+
+def test_adamw_first_step_closed_form():
+    # Decoupled weight decay (Loshchilov & Hutter): on step 1 the bias
+    # corrections turn m and v into g and g^2, so the update is exactly
+    # lr (g / (|g| + eps) + wd theta).  A coupled decay (wd theta folded into g)
+    # or a missing bias correction gives a different step.
+    theta = np.array([0.5, -2.0, 3.0, 0.0])
+    g = np.array([0.1, 0.3, -4.0, 1e-3])
+    lr, wd, eps = 0.01, 0.1, 1e-8
+    t1, m1, v1 = S.adamw_step(theta, g, np.zeros(4), np.zeros(4), 1, lr=lr, beta1=0.9, beta2=0.999, eps=eps, wd=wd)
+    want = theta - lr * (g / (np.abs(g) + eps) + wd * theta)
+    np.testing.assert_allclose(t1, want, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(m1, 0.1 * g, rtol=1e-15)
+    np.testing.assert_allclose(v1, 0.001 * g * g, rtol=1e-12)   # 1 - 0.999 rounds
+    coupled = g + wd * theta
+    t_coupled = theta - lr * coupled / (np.abs(coupled) + eps)
+    assert np.abs(t1 - t_coupled).max() > 1e-4
+
+
+def test_adamw_second_step_hand_computed():
+    # step 2 by hand: m2 = b1 m1 + (1-b1) g2, v2 = b2 v1 + (1-b2) g2^2,
+    # bias-corrected by 1 - b^2; theta3 = theta2 - lr (mh / (sqrt(vh) + eps) + wd theta2)
+    b1, b2, lr, wd, eps = 0.9, 0.999, 0.05, 0.01, 1e-8
+    th = np.array([1.0])
+    g1, g2 = np.array([2.0]), np.array([-1.0])
+    th1, m1, v1 = S.adamw_step(th, g1, np.zeros(1), np.zeros(1), 1, lr=lr, beta1=b1, beta2=b2, eps=eps, wd=wd)
+    th2, _, _ = S.adamw_step(th1, g2, m1, v1, 2, lr=lr, beta1=b1, beta2=b2, eps=eps, wd=wd)
+    # by hand: th1 = 1 - 0.05 (2/(2+1e-8) + 0.01) = 0.9495 (to 5e-10)
+    assert abs(th1[0] - (1.0 - lr * (2.0 / (2.0 + eps) + wd))) < 1e-15
+    m2 = 0.9 * 0.2 + 0.1 * (-1.0)                   # 0.08
+    v2 = 0.999 * 0.004 + 0.001 * 1.0                # 0.004996
+    mh, vh = m2 / (1 - 0.81), v2 / (1 - 0.998001)
+    want = th1[0] - lr * (mh / (math.sqrt(vh) + eps) + wd * th1[0])
+    assert abs(th2[0] - want) < 1e-15
+
+
+def test_adamw_matches_torch_adamw_over_steps():
+    # a library routine with the same definition: torch.optim.AdamW (decoupled
+    # decay, bias correction), several steps with varying gradients, FP64
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    theta0 = rng.standard_normal(50)
+    grads = rng.standard_normal((6, 50))
+    lr, b1, b2, eps, wd = 3e-3, 0.9, 0.999, 1e-8, 1e-2
+    p = torch.nn.Parameter(torch.from_numpy(theta0.copy()))
+    opt = torch.optim.AdamW([p], lr=lr, betas=(b1, b2), eps=eps, weight_decay=wd)
+    th, m, v = theta0.copy(), np.zeros(50), np.zeros(50)
+    for k, g in enumerate(grads, start=1):
+        p.grad = torch.from_numpy(g.copy())
+        opt.step()
+        th, m, v = S.adamw_step(th, g, m, v, k, lr=lr, beta1=b1, beta2=b2, eps=eps, wd=wd)
+    np.testing.assert_allclose(th, p.detach().numpy(), rtol=0, atol=1e-14)
