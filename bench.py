@@ -1,19 +1,21 @@
 #!/usr/bin/env python3
 """MRCQR benchmark on GB300.
 
-One step = MRCQR (Algorithm 2) of the five m x n matrices of the large-
-factorization workload -- m = 2^20, n = 128, geometric spectra with
-kappa_2 in {1e2, 1e4, 1e8, 1e12, 1e16}, sketch precision by the paper's
-bounds (FP16 up to 1e4, FP32 up to 1e8, FP64 above), s = 2n, sketch seed 0 --
-with the device-side ||I - Q^T Q|| judge on.  Inputs are synthetic (seeded
-generator, U from the QR of a Gaussian, Haar V), 1 GiB each, so every step
-streams more than L2 holds.
+One step = MRCQR (Algorithm 2) of the twenty m x n matrices of the
+large-factorization workload -- m = 2^20, n in {64, 128, 256, 512}, each with
+geometric spectra of kappa_2 in {1e2, 1e4, 1e8, 1e12, 1e16}, sketch
+precision by the paper's bounds (FP16 up to 1e4, FP32 up to 1e8, FP64
+above), s = 2n, sketch seed 0 -- with the device-side ||I - Q^T Q|| judge
+and escalation on.  Inputs are synthetic (seeded generator, U from the QR of
+a Gaussian, Haar V), 0.5-4 GiB each, so every step streams far more than L2
+holds.
 
 Prints one JSON line (rank 0): factorizations/s over all ranks (weak scaling:
-every rank factors its own five matrices, no data-path collective), the
-FP64-sketch MRCQR on the same GPU as the in-GPU baseline, the end-to-end
-rate with host buffers, the dominant kernel's roofline, clocks and the CPU
-oracle baseline.
+every rank factors its own matrices, no data-path collective); per n the
+rule-precision, FP64-sketch and learned-selector rates; the end-to-end rate
+with host buffers; the dominant kernel's roofline; the small single
+factorization (m = 4096, n = 32) and the 512-problem batched plan; clocks and
+the CPU oracle baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -163,6 +165,33 @@ def load_traffic(kernel: str):
 
 
 # ---------------------------------------------------------------------------
+# Algorithmic work of one launch of a stage at (m, n): HBM bytes (A read once by
+# the sketch, A read + W written by the TRSM, W read by the Gram, W read + Q
+# written by the finalize, Q read by the check), FP64 flops of the method
+# (m n^2 per triangular solve or triangular product, m n (n + 1) per Gram;
+# the sketch's nominal real-transform count), and the FP16 tensor flops the
+# emulated FP64 products execute (36 digit-pair products per multiply-add).
+def stage_work(stage: str, m: int, n: int):
+    s = 2 * n
+    if stage == "trsm":
+        return 16.0 * m * n, 1.0 * m * n * n, 36.0 * m * n * (n - 16)
+    if stage in ("syrk", "check"):
+        return 8.0 * m * n, 1.0 * m * n * (n + 1), 36.0 * m * n * (n + 1)
+    if stage == "finalize":
+        return 16.0 * m * n, 1.0 * m * n * n, 36.0 * m * n * (n + 1)
+    if stage == "sketch":
+        return 8.0 * m * n, 2.5 * n * m * math.log2(m), 4.0 * s * m * n
+    return None
+
+
+def measured_hbm_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured (copy, MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback"
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -177,39 +206,43 @@ def run_ours(args):
     _build.build()
     lib = _lib.load()
     dev = torch.device("cuda", local)
-    m, n, K, W = args.m, args.n, args.steps, args.warmup
-    precs = [rule(k) for k in KAPPAS]
-    As = [inputs.make_matrix_device(m, n, k, seed=input_seed(rank, i), device=dev) for i, k in enumerate(KAPPAS)]
-    Qs = [M.empty_colmajor(m, n, device=dev) for _ in KAPPAS]
-    Rs = [M.empty_colmajor(n, n, device=dev) for _ in KAPPAS]
-    stats = torch.zeros((len(KAPPAS), 8), dtype=torch.float64, device=dev)   # 64 B per mrcqr_stats_t
+    m, K, W = args.m, args.steps, args.warmup
+    ns = [int(x) for x in args.ns.split(",")]
+    probs = [(n, kappa) for n in ns for kappa in KAPPAS]
+    precs = [rule(k) for _, k in probs]
+    As = [inputs.make_matrix_torch(m, n, k, seed=input_seed(rank, i), device=dev, rounds=2)
+          for i, (n, k) in enumerate(probs)]
+    Qs = [M.empty_colmajor(m, n, device=dev) for n, _ in probs]
+    Rs = [M.empty_colmajor(n, n, device=dev) for n, _ in probs]
+    stats = torch.zeros((len(probs), 8), dtype=torch.float64, device=dev)   # 64 B per mrcqr_stats_t
     torch.cuda.synchronize()
 
     # the factorizations of a step are independent problems: one CUDA stream each, so one problem's
     # single-CTA phases (sketch QR, Cholesky, judge) overlap another's full-GPU kernels
-    streams = [torch.cuda.Stream(dev) for _ in As]
-    joins = [torch.cuda.Event() for _ in As]
+    streams = [torch.cuda.Stream(dev) for _ in probs]
+    joins = [torch.cuda.Event() for _ in probs]
     cur = torch.cuda.current_stream(dev)
 
-    def step(pl, concurrent=True):
+    def step(pl, sel=None, concurrent=True):
+        sel = range(len(probs)) if sel is None else sel
         if not concurrent:
-            for i in range(len(As)):
+            for i in sel:
                 M.factor_ex(As[i], Qs[i], Rs[i], prec=pl[i], seed=0, stats_device=stats[i])
             return
         fork = torch.cuda.Event()
         fork.record(cur)
-        for i in range(len(As)):
+        for i in sel:
             streams[i].wait_event(fork)
             M.factor_ex(As[i], Qs[i], Rs[i], prec=pl[i], seed=0, stats_device=stats[i], stream=streams[i])
             joins[i].record(streams[i])
-        for ev in joins:
-            cur.wait_event(ev)
+        for i in sel:
+            cur.wait_event(joins[i])
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    def timed(pl, steps, profile=False, concurrent=True):
+    def timed(pl, steps, sel=None, profile=False, concurrent=True):
         barrier()
         torch.cuda.synchronize()
         if profile:
@@ -218,7 +251,7 @@ def run_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
-            step(pl, concurrent)
+            step(pl, sel, concurrent)
         e1.record()
         torch.cuda.synchronize()
         barrier()
@@ -227,7 +260,7 @@ def run_ours(args):
         if profile:
             import ctypes
             cnt = ctypes.c_int32()
-            cap = 100000
+            cap = 200000
             st = (ctypes.c_int32 * cap)()
             lv = (ctypes.c_int32 * cap)()
             ms = (ctypes.c_float * cap)()
@@ -236,201 +269,313 @@ def run_ours(args):
         t = max_over_ranks(e0.elapsed_time(e1) / 1000.0, dev, world)
         return t, launches, recs
 
-    def read_stats():
-        import ctypes
+    def read_stats(sel=None):
         raw = stats.cpu().numpy().tobytes()
-        out = []
-        for i in range(len(As)):
-            s = _lib.Stats.from_buffer_copy(raw[64 * i:64 * (i + 1)])
-            out.append(s.as_dict())
-        return out
-
-    for _ in range(W):
-        step(precs)
-    torch.cuda.synchronize()
-    st_ours = read_stats()
-    ok = all(s["status"] == "OK" and s["retries"] == 0 for s in st_ours)
-
-    smi = ClockSampler(local)
-    t_ours, launches, recs_conc = timed(precs, K, profile=True)
-    clocks = smi.stop()
-    st_after = read_stats()
-    ok = ok and all(s["status"] == "OK" for s in st_after)
-    units = len(As) * world * K
-    value = units / t_ours
-    # the same K steps on one stream: every stage's CUDA events then time that stage's kernels alone
-    # (in the timed region the stages of other streams' factorizations run inside them)
-    t_seq, _, recs = timed(precs, K, profile=True, concurrent=False)
+        sel = range(len(probs)) if sel is None else sel
+        return [_lib.Stats.from_buffer_copy(raw[64 * i:64 * (i + 1)]).as_dict() for i in sel]
 
     def per_stage(records):
         out = {}
         for sid, lv, ms in records or []:
-            if lv != 0:   # level 0 launches; no escalation happens here
-                continue
             name = lib.mrcqr_stage_name(sid).decode()
             d = out.setdefault(name, [0.0, 0])
             d[0] += ms
             d[1] += 1
         return out
 
-    # dominant kernel of the step
-    per = per_stage(recs)
-    per_conc = per_stage(recs_conc)
-    # algorithmic work per launch of the stage-2 kernels (emulated FP64 products): FP16 tensor flops
-    # (36 digit-pair products of the useful multiply-adds) and FP64 flops (the TRSM's diagonal blocks)
-    work = {"trsm": (36.0 * m * n * (n - 16), 16.0 * m * n),
-            "syrk": (36.0 * m * n * (n + 1), 0.0), "check": (36.0 * m * n * (n + 1), 0.0),
-            "finalize": (36.0 * m * n * (n + 1), 0.0)}
-    tensor_peak, tensor_src = measured_tensor_peak()
-    stage2 = {k: v for k, v in per.items() if k in work}
-    dom = max(stage2, key=lambda k: stage2[k][0]) if stage2 else None
-    roofline = None
-    if dom:
-        avg_ms = stage2[dom][0] / stage2[dom][1]
-        tf, ff = work[dom]
-        t_tensor = tf / (avg_ms / 1000.0) / 1e12
-        t_fp64 = ff / (avg_ms / 1000.0) / 1e12
-        comps = {"tensor_fp16": {"achieved": round(t_tensor, 2), "peak": round(tensor_peak, 1), "unit": "TFLOP/s",
-                                 "frac": round(t_tensor / tensor_peak, 4), "peak_source": tensor_src},
-                 "fp64_pipe": {"achieved": round(t_fp64, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                               "frac": round(t_fp64 / FP64_PEAK_TFLOPS, 4),
-                               "peak_source": "derived FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz"}}
-        key = max(comps, key=lambda c: comps[c]["frac"])
-        c = comps[key]
-        tr = load_traffic(dom)
-        traffic = None
-        if tr and tr.get("n") == n:
-            traffic = tr["bytes_per_row"] * m
-        roofline = {"bound": "tensor" if key == "tensor_fp16" else "alu", "kernel": dom, "achieved": c["achieved"],
-                    "peak": c["peak"], "unit": "TFLOP/s", "frac": c["frac"], "traffic": traffic,
-                    "peak_source": c["peak_source"], "avg_launch_ms": round(avg_ms, 4), "components": comps,
-                    "work": "emulated FP64: 36 FP16 digit-pair products per useful multiply-add",
-                    "timing": "CUDA events around each launch on its stream, K steps of the same workload on one "
-                              "stream right after the timed region",
-                    "avg_launch_ms_in_timed_region": (round(per_conc[dom][0] / per_conc[dom][1], 4)
-                                                      if dom in per_conc else None)}
-    step_ms_by_kernel = {k: round(v[0] / K, 3) for k, v in sorted(per.items(), key=lambda kv: -kv[1][0])}
-
-    # in-GPU baseline: the same step with every sketch in FP64
-    fp64 = ["fp64"] * len(As)
-    step(fp64)
+    # ---- the timed region: K steps of the whole workload, every problem on its own stream ----
+    for _ in range(W):
+        step(precs)
     torch.cuda.synchronize()
-    kb = max(1, min(K, 3))
-    t_b, _, _ = timed(fp64, kb)
-    baseline_value = len(As) * world * kb / t_b
-    st_b = read_stats()
+    smi = ClockSampler(local)
+    t_ours, launches, _ = timed(precs, K)
+    clocks = smi.stop()
+    st_after = read_stats()
+    ok = all(s["status"] == "OK" and s["ortho_fro"] <= 1e-13 for s in st_after)
+    units = len(probs) * world * K
+    value = units / t_ours
 
-    # the learned precision selector (AUTO): FP16 sketch, features, MLP choice, re-sketch if needed
-    auto = None
+    # ---- per n: rule precision, every sketch in FP64, the learned selector (>= 10 steps each), and a
+    # one-stream profiled step whose CUDA events time each stage's kernels alone ----
     try:
         from paper_2606_18411_gb300 import selector as _sel
         _sel.load_into_library()
-        autop = ["auto"] * len(As)
-        step(autop)
-        torch.cuda.synchronize()
-        t_a, _, _ = timed(autop, kb)
-        st_a = read_stats()
-        auto = {"value": round(len(As) * world * kb / t_a, 4), "unit": UNIT,
-                "speedup_vs_fp64_sketch": round(len(As) * world * kb / t_a / baseline_value, 3),
-                "precisions_used": [s["prec_used"] for s in st_a], "retries": [s["retries"] for s in st_a],
-                "all_ok": all(s["status"] == "OK" for s in st_a)}
-    except (OSError, RuntimeError) as exc:   # no shipped weights: report why
-        auto = {"unavailable": str(exc)}
+        have_auto = True
+    except (OSError, RuntimeError):
+        have_auto = False
+    kn = max(10, K)
+    per_n, stage_ms, stage_launch = {}, {}, {}
+    for n in ns:
+        sel = [i for i, (nn, _) in enumerate(probs) if nn == n]
+        row = {}
+        for mode in ("rule", "fp64", "auto"):
+            if mode == "auto" and not have_auto:
+                row["auto"] = {"unavailable": "no selector weights"}
+                continue
+            pl = precs if mode == "rule" else [mode] * len(probs)
+            step(pl, sel)
+            torch.cuda.synchronize()
+            t, _, _ = timed(pl, kn, sel)
+            sts = read_stats(sel)
+            row[mode] = {"value": round(len(sel) * world * kn / t, 4), "steps": kn,
+                         "precisions_used": [s["prec_used"] for s in sts], "retries": [s["retries"] for s in sts],
+                         "all_ok": all(s["status"] == "OK" and s["ortho_fro"] <= 1e-13 for s in sts)}
+        row["rule_over_fp64_sketch"] = round(row["rule"]["value"] / row["fp64"]["value"], 3)
+        if "value" in row.get("auto", {}):
+            row["auto_over_fp64_sketch"] = round(row["auto"]["value"] / row["fp64"]["value"], 3)
+        _, _, recs = timed(precs, 1, sel, profile=True, concurrent=False)
+        ps = per_stage(recs)
+        # every escalation level is enqueued and the inactive ones return at once: the heavy stages
+        # ran once per level actually taken (1 + retries per problem)
+        active = sum(1 + s_["retries"] for s_ in read_stats(sel))
+        row["one_stream_stage_ms"] = {k: round(v[0], 3) for k, v in sorted(ps.items(), key=lambda kv: -kv[1][0])}
+        row["active_levels"] = active
+        for k, v in ps.items():
+            stage_ms[k] = stage_ms.get(k, 0.0) + v[0]
+            stage_launch.setdefault(k, {})[n] = (v[0], active if stage_work(k, m, n) is not None else v[1])
+        per_n[str(n)] = row
 
-    # end to end through the public API with host buffers
-    hA = [a.t().contiguous().cpu().pin_memory() for a in As]       # n x m row-major = column-major m x n
-    hQ = [torch.empty((n, m), dtype=torch.float64).pin_memory() for _ in As]
-    hR = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in As]
-    dA = [M.empty_colmajor(m, n, device=dev) for _ in As]
+    # ---- roofline of the dominant kernel (largest one-stream time over the step), at the n where it
+    # spends the most time; achieved = algorithmic bytes per launch / average launch time ----
+    hbm_peak, hbm_src = measured_hbm_peak()
+    tensor_peak, tensor_src = measured_tensor_peak()
+    work_stages = [k for k in stage_ms if stage_work(k, m, 64) is not None]
+    dom = max(work_stages, key=lambda k: stage_ms[k]) if work_stages else None
+    roofline, per_n_roof = None, {}
+    for n in ns:
+        ent = {}
+        for k in ("sketch", "trsm", "syrk", "finalize", "check"):
+            if k in stage_launch and n in stage_launch[k]:
+                tot, cnt = stage_launch[k][n]
+                b, f64, tf = stage_work(k, m, n)
+                ms_l = tot / cnt
+                ent[k] = {"avg_launch_ms": round(ms_l, 4), "hbm_frac": round(b / (ms_l / 1e3) / 1e9 / hbm_peak, 4)}
+        s2 = [k for k in ("trsm", "syrk", "finalize", "check") if k in ent]
+        if s2:
+            t2 = sum(stage_launch[k][n][0] for k in s2) / len(KAPPAS)   # Stage 2 per factorization (ms)
+            ent["stage2_ms_per_factorization"] = round(t2, 3)
+            ent["stage2_hbm_frac"] = round(32.0 * m * n / (t2 / 1e3) / 1e9 / hbm_peak, 4)
+        per_n_roof[str(n)] = ent
+    if dom:
+        nstar = max(stage_launch[dom], key=lambda n: stage_launch[dom][n][0])
+        tot, cnt = stage_launch[dom][nstar]
+        avg_ms = tot / cnt
+        b, f64, tf = stage_work(dom, m, nstar)
+        ach_gbs = b / (avg_ms / 1e3) / 1e9
+        f64_tf = f64 / (avg_ms / 1e3) / 1e12
+        ten_tf = tf / (avg_ms / 1e3) / 1e12
+        tr = load_traffic(dom)
+        traffic = tr["bytes_per_row"] * m if (tr and tr.get("n") == nstar) else None
+        roofline = {
+            "bound": "hbm", "kernel": dom, "n": nstar, "achieved": round(ach_gbs, 1), "peak": round(hbm_peak, 1),
+            "unit": "GB/s", "frac": round(ach_gbs / hbm_peak, 4), "traffic": traffic,
+            "peak_source": hbm_src, "avg_launch_ms": round(avg_ms, 4),
+            "algorithmic_bytes_per_launch": b,
+            "components": {
+                "hbm": {"achieved_gbs": round(ach_gbs, 1), "peak_gbs": round(hbm_peak, 1),
+                        "frac": round(ach_gbs / hbm_peak, 4)},
+                "fp64_equivalent": {"achieved_tflops": round(f64_tf, 3), "peak_tflops": round(FP64_PEAK_TFLOPS, 4),
+                                    "frac": round(f64_tf / FP64_PEAK_TFLOPS, 4),
+                                    "note": "the method's FP64 flops over the FP64 pipe's peak; above 1 because the "
+                                            "products run as emulated FP64 on the tensor cores, so the HBM term is the "
+                                            "binding roofline"},
+                "tensor_emulation": {"achieved_tflops": round(ten_tf, 1), "peak_tflops": round(tensor_peak, 1),
+                                     "frac": round(ten_tf / tensor_peak, 4), "peak_source": tensor_src}},
+            "timing": "CUDA events around each launch on its stream, one-stream pass of the same problems after "
+                      "the timed region"}
+    step_ms_by_kernel = {k: round(v, 3) for k, v in sorted(stage_ms.items(), key=lambda kv: -kv[1])}
 
-    # copies in, factorizations and copies out on their own streams (one per factorization, as in
-    # the device-resident step), so uploads and downloads overlap factorizations; per-matrix
-    # events keep the device buffers of one step from being overwritten before the previous step
-    # is done
+    # ---- end to end through the public API with host buffers: every step uploads each A from pinned
+    # host memory and downloads each Q and R ----
+    try:
+        e2e = run_e2e(torch, M, dev, cur, streams, As, Qs, Rs, precs, stats, read_stats, world, barrier, min(K, 3))
+    except RuntimeError as exc:   # pinned host memory for every matrix not available: say so
+        e2e = {"unavailable": f"{type(exc).__name__}: {str(exc)[:160]}"}
+
+    # ---- small single factorization (m = 4096, n = 32, kappa = 1e8, FP32 sketch) and the batched plan ----
+    small = run_small(torch, M, dev) if not args.no_extras else None
+    del As, Qs, Rs
+    torch.cuda.empty_cache()
+    batched = None
+    if not args.no_extras and world == 1:
+        batched = batched_summary(torch, M, inputs, dev, rank, count=512, steps=3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ns, m)
+
+    if rank == 0:
+        flops = sum(fp64eq_flops(m, n) for n, _ in probs) * world * K
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": round(t_ours * 1000.0 / K, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded A = U diag(sigma) V^T)",
+            "config": {"workload": f"MRCQR m=2^{int(math.log2(m))}, n in {{{','.join(map(str, ns))}}} x geometric "
+                                   "kappa in {1e2,1e4,1e8,1e12,1e16}, sketch precision by rule, s=2n",
+                       "m": m, "ns": ns, "kappas": KAPPAS, "factorizations_per_step": len(probs),
+                       "sketch_precisions": precs, "l2": "inputs larger than L2 (0.5-4 GiB per matrix)",
+                       "parallelism": f"replicas x{world}", "streams": f"{len(probs)} per rank (one per factorization)"},
+            "fp64eq_gflops": round(flops / t_ours / 1e9, 2),
+            "per_n": per_n, "all_ok": ok, "retries": [s["retries"] for s in st_after],
+            "ortho_fro_max": max(s["ortho_fro"] for s in st_after),
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "roofline_per_n": per_n_roof,
+            "step_ms_by_kernel": step_ms_by_kernel,
+            "step_ms_by_kernel_note": "one-stream pass of one step of every problem (CUDA events around each stage)",
+            "small_factorization": small, "batched": batched, "clocks": clocks, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(torch, M, dev, cur, streams, As, Qs, Rs, precs, stats, read_stats, world, barrier, steps):
+    """The bench's metric through mrcqr_factor_ex with host buffers: each step copies every A from
+    pinned host memory and every Q and R back.  Uploads, downloads and each factorization run on
+    their own streams, ordered by per-matrix events, so copies overlap factorizations."""
+    cnt = len(As)
+    hA = []
+    for a in As:                                                      # n x m row-major = column-major m x n
+        h = torch.empty((a.shape[1], a.shape[0]), dtype=torch.float64, pin_memory=True)
+        h.copy_(a.t())
+        hA.append(h)
+    nmax = {}
+    for q in Qs:                                                      # one host Q per shape (downloads serialise)
+        nmax.setdefault(tuple(q.shape), torch.empty((q.shape[1], q.shape[0]), dtype=torch.float64).pin_memory())
+    hQ = [nmax[tuple(q.shape)] for q in Qs]
+    hR = [torch.empty((r.shape[1], r.shape[0]), dtype=torch.float64).pin_memory() for r in Rs]
+    dA = [M.empty_colmajor(a.shape[0], a.shape[1], device=dev) for a in As]
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    s_cs = streams
-    ev_in = [torch.cuda.Event() for _ in As]
-    ev_c = [torch.cuda.Event() for _ in As]
-    ev_out = [torch.cuda.Event() for _ in As]
-    for i in range(len(As)):   # "previous step done" for the first step
+    ev_in = [torch.cuda.Event() for _ in range(cnt)]
+    ev_c = [torch.cuda.Event() for _ in range(cnt)]
+    ev_out = [torch.cuda.Event() for _ in range(cnt)]
+    for i in range(cnt):
         ev_c[i].record(cur)
         ev_out[i].record(cur)
 
     def e2e_step():
-        for i in range(len(As)):
+        for i in range(cnt):
             s_in.wait_event(ev_c[i])                  # the previous factorization of dA[i] is done
             with torch.cuda.stream(s_in):
                 dA[i].t().copy_(hA[i], non_blocking=True)
             ev_in[i].record(s_in)
-            s_cs[i].wait_event(ev_in[i])
-            s_cs[i].wait_event(ev_out[i])             # the previous download of Q[i], R[i] is done
-            M.factor_ex(dA[i], Qs[i], Rs[i], prec=precs[i], seed=0, stats_device=stats[i], stream=s_cs[i])
-            ev_c[i].record(s_cs[i])
+            streams[i].wait_event(ev_in[i])
+            streams[i].wait_event(ev_out[i])          # the previous download of Q[i], R[i] is done
+            M.factor_ex(dA[i], Qs[i], Rs[i], prec=precs[i], seed=0, stats_device=stats[i], stream=streams[i])
+            ev_c[i].record(streams[i])
             s_out.wait_event(ev_c[i])
             with torch.cuda.stream(s_out):
                 hQ[i].copy_(Qs[i].t(), non_blocking=True)
                 hR[i].copy_(Rs[i].t(), non_blocking=True)
             ev_out[i].record(s_out)
 
-    def e2e_timed(steps):
-        start = torch.cuda.Event()
-        start.record(cur)
-        for st_ in (s_in, s_out, *s_cs):
-            st_.wait_event(start)
-        for _ in range(steps):
-            e2e_step()
-        for ev in ev_out:
-            cur.wait_event(ev)
-
     e2e_step()
     torch.cuda.synchronize()
-    ke = max(1, min(K, 3))
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(cur)
-    e2e_timed(ke)
+    start = torch.cuda.Event()
+    start.record(cur)
+    for st_ in (s_in, s_out, *streams):
+        st_.wait_event(start)
+    for _ in range(steps):
+        e2e_step()
+    for ev in ev_out:
+        cur.wait_event(ev)
     e1.record(cur)
     torch.cuda.synchronize()
     barrier()
     t_e = max_over_ranks(e0.elapsed_time(e1) / 1000.0, dev, world)
     st_e = read_stats()
-    e2e = {"value": round(len(As) * world * ke / t_e, 4), "unit": UNIT,
-           "h2d_bytes_per_step": int(len(As) * 8 * m * n),
-           "d2h_bytes_per_step": int(len(As) * 8 * (m * n + n * n)),
+    out = {"value": round(cnt * world * steps / t_e, 4), "unit": UNIT, "steps": steps,
+           "h2d_bytes_per_step": int(sum(8 * a.shape[0] * a.shape[1] for a in As)),
+           "d2h_bytes_per_step": int(sum(8 * (q.shape[0] * q.shape[1]) for q in Qs) +
+                                     sum(8 * r.shape[0] * r.shape[1] for r in Rs)),
            "overlap": "uploads, downloads and each factorization on its own stream",
            "all_ok": all(s_["status"] == "OK" for s_ in st_e)}
+    del hA, hQ, hR, dA
+    return out
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(n, m)
 
-    if rank == 0:
-        flops = sum(fp64eq_flops(m, n) for _ in As) * world * K
-        line = {
-            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": round(t_ours * 1000.0 / K, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded A = U diag(sigma) V^T)",
-            "config": {"workload": f"MRCQR m=2^{int(math.log2(m))} n={n} geometric kappa in "
-                                   "{1e2,1e4,1e8,1e12,1e16}, sketch precision by rule, s=2n",
-                       "m": m, "n": n, "kappas": KAPPAS, "sketch_precisions": precs, "s": 2 * n,
-                       "factorizations_per_step": len(As), "l2": "inputs larger than L2 (1 GiB per matrix)",
-                       "parallelism": f"replicas x{world}",
-                       "streams": f"{len(As)} per rank (one per factorization of the step)"},
-            "fp64eq_gflops": round(flops / t_ours / 1e9, 2),
-            "fp64_sketch_baseline": {"value": round(baseline_value, 4), "unit": UNIT,
-                                     "speedup_of_rule_precision": round(value / baseline_value, 3),
-                                     "all_ok": all(s["status"] == "OK" for s in st_b)},
-            "learned_selector": auto,
-            "all_ok": ok, "ortho_fro": [s["ortho_fro"] for s in st_after],
-            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-            "step_ms_by_kernel": step_ms_by_kernel,
-            "step_ms_by_kernel_note": "one-stream pass of the same steps (CUDA events around each stage)",
-            "one_stream_value": round(units / t_seq, 4), "clocks": clocks, "cpu_baseline": cpu,
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+def run_small(torch, M, dev, m=4096, n=32, kappa=1e8, calls=200):
+    """The small single factorization (m = 4096, n = 32, geometric kappa = 1e8, FP32 sketch, seed 0):
+    launch-latency bound, so reported per call, back to back on one stream, and as a CUDA graph
+    replay of the same call when the capture succeeds."""
+    from paper_2606_18411_gb300 import inputs
+    A = M.to_colmajor(inputs.make_matrix(m, n, kappa, seed=1001), device=dev)
+    Q, R = M.empty_colmajor(m, n, device=dev), M.empty_colmajor(n, n, device=dev)
+    st = torch.zeros(8, dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        for _ in range(5):
+            M.factor_ex(A, Q, R, prec="fp32", seed=0, stats_device=st, stream=s)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        e0.record(s)
+        for _ in range(calls):
+            M.factor_ex(A, Q, R, prec="fp32", seed=0, stats_device=st, stream=s)
+        e1.record(s)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    from paper_2606_18411_gb300 import _lib
+    sd = _lib.Stats.from_buffer_copy(st.cpu().numpy().tobytes()).as_dict()
+    out = {"workload": f"m={m} n={n} geometric kappa={kappa:g}, FP32 sketch, s=2n, seed 0",
+           "factorizations_per_s": round(calls / t, 1), "us_per_call": round(t / calls * 1e6, 2),
+           "status": sd["status"], "prec_used": sd["prec_used"], "ortho_fro": sd["ortho_fro"]}
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            M.factor_ex(A, Q, R, prec="fp32", seed=0, stats_device=st, stream=s)
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record(s)
+        with torch.cuda.stream(s):
+            for _ in range(calls):
+                g.replay()
+        e1.record(s)
+        torch.cuda.synchronize()
+        tg = e0.elapsed_time(e1) / 1e3
+        out["graph_factorizations_per_s"] = round(calls / tg, 1)
+        out["graph_us_per_call"] = round(tg / calls * 1e6, 2)
+    except Exception as exc:   # capture not possible: report why
+        out["graph"] = f"not captured: {type(exc).__name__}: {str(exc)[:120]}"
+    return out
+
+
+def batched_summary(torch, M, inputs, dev, rank, count=512, steps=3):
+    """The batched workload (count problems, m uniform in [2^14, 2^18], n in {16, 32, 64, 128},
+    kappa log-uniform in [1, 1e12], precision by rule) through one batched plan under a CUDA graph."""
+    import numpy as np
+    rng = np.random.default_rng(4000 + rank)
+    ms = rng.integers(1 << 14, (1 << 18) + 1, count)
+    ns = rng.choice([16, 32, 64, 128], count)
+    kap = 10.0 ** rng.uniform(0.0, 12.0, count)
+    precs = [rule(k) for k in kap]
+    As = [inputs.make_matrix_torch(int(m), int(n), float(k), seed=10000 * rank + i, device=dev)
+          for i, (m, n, k) in enumerate(zip(ms, ns, kap))]
+    Qs = [M.empty_colmajor(int(m), int(n), device=dev) for m, n in zip(ms, ns)]
+    Rs = [M.empty_colmajor(int(n), int(n), device=dev) for n in ns]
+    status = torch.zeros(count, dtype=torch.int32, device=dev)
+    plan = M.BatchedPlan(As, Qs, Rs, precs, list(range(count)), status, use_graph=True, autotune=True)
+    info = plan.info()
+    plan.execute()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.execute()
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    ok = status.cpu().tolist()
+    plan.close()
+    del As, Qs, Rs
+    torch.cuda.empty_cache()
+    return {"workload": f"{count} factorizations, m uniform in [2^14,2^18], n in {{16,32,64,128}}, kappa "
+                        "log-uniform in [1,1e12], precision by rule, one batched plan replayed as a CUDA graph",
+            "factorizations_per_s": round(count * steps / t, 1), "steps": steps,
+            "kernels_per_execute": info["kernels_per_execute"], "all_ok": all(v == 0 for v in ok)}
 
 
 def run_batched(args):
@@ -518,7 +663,7 @@ def run_batched(args):
 
 
 def run_sweep(args):
-    """Stability sweep of the paper's experiment (Sec. IV-B, Fig. 1) on the
+    """Stability sweep of the paper's experiment (Sec. III-B, Fig. 1) on the
     m = 2^22, n = 128 sweep workload: geometric, step-cliff and clustered
     spectra, kappa_2 = 1e0 .. 1e16 in decades, MRCQR with each sketch
     precision (FP16, BF16, FP32, FP64; no escalation, so each precision's own
@@ -595,47 +740,52 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(n: int, m_full: int, m_sample: int = 1 << 18):
-    """The CPU oracle, as it stands, on one matrix of the workload cut to
-    m_sample rows (its cost is linear in m), scaled to factorizations/s of
-    the full m."""
+def oracle_sample_step(ns, m_sample, kappas, k, seed0=4242):
+    """One oracle factorization per n of the workload, cut to m_sample rows (kappa cycling with k)."""
     import oracle
     from paper_2606_18411_gb300 import inputs
-    A = inputs.make_matrix(m_sample, n, 1e8, seed=4242)
-    t0 = time.perf_counter()
-    oracle.mrcqr(A, seed=0, prec=rule(1e8))
-    t = time.perf_counter() - t0
-    return {"value": round((m_sample / m_full) / t, 6), "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-            "sample": f"1 factorization, m={m_sample} n={n} kappa=1e8 fp32-emulated sketch, {t:.2f} s; "
-                      f"scaled by m/{m_full} (oracle cost is linear in m)"}
+    t = 0.0
+    for j, n in enumerate(ns):
+        kappa = kappas[(k + j) % len(kappas)]
+        A = inputs.make_matrix(m_sample, n, kappa, seed=seed0 + 7 * k + j)
+        t0 = time.perf_counter()
+        oracle.mrcqr(A, seed=0, prec=rule(kappa))
+        t += time.perf_counter() - t0
+    return t
+
+
+def cpu_baseline(ns, m_full: int, m_sample: int = 1 << 15):
+    """The CPU oracle, as it stands, on one factorization per n of the workload cut to m_sample rows
+    (its cost is linear in m for fixed n), scaled to factorizations/s of the full workload."""
+    t = oracle_sample_step(ns, m_sample, KAPPAS, 0)
+    value = len(ns) * (m_sample / m_full) / t
+    return {"value": round(value, 6), "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": f"1 factorization per n in {ns}, m={m_sample}, kappa cycling {KAPPAS}, {t:.2f} s; scaled by "
+                      f"m/{m_full} (oracle cost is linear in m)"}
 
 
 def run_reference(args):
-    """The oracle on the host cores: each step one factorization of the
-    workload cut to 2^16 rows, scaled to the full m."""
+    """The oracle on the host cores: each step one factorization per n of the workload cut to 2^14
+    rows (kappa cycling), scaled to the full m."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    import numpy as np
-    import oracle
-    from paper_2606_18411_gb300 import inputs
-    m_s, n = 1 << 16, args.n
-    mats = [inputs.make_matrix(m_s, n, k, seed=3000 + i) for i, k in enumerate(KAPPAS)]
+    ns = [int(x) for x in args.ns.split(",")]
+    m_s = 1 << 14
     for w in range(args.warmup):
-        oracle.mrcqr(mats[w % len(mats)], seed=0, prec=rule(KAPPAS[w % len(mats)]))
-    t0 = time.perf_counter()
+        oracle_sample_step(ns, m_s, KAPPAS, w)
+    t = 0.0
     for k in range(args.steps):
-        i = k % len(mats)
-        oracle.mrcqr(mats[i], seed=0, prec=rule(KAPPAS[i]))
-    t = time.perf_counter() - t0
-    value = args.steps * (m_s / args.m) / t
-    sample = f"each step 1 factorization, m={m_s} n={n}, kappa cycling {KAPPAS}, scaled by m/{args.m}"
+        t += oracle_sample_step(ns, m_s, KAPPAS, k)
+    value = args.steps * len(ns) * (m_s / args.m) / t
+    sample = (f"each step 1 factorization per n in {ns}, m={m_s}, kappa cycling {KAPPAS}, scaled by "
+              f"m/{args.m}")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1000 / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded A = U diag(sigma) V^T)",
-            "config": {"workload": f"MRCQR m=2^{int(math.log2(args.m))} n={n} geometric kappa in "
-                                   "{1e2,1e4,1e8,1e12,1e16}, sketch precision by rule, s=2n", "m": args.m, "n": n},
+            "config": {"workload": f"MRCQR m=2^{int(math.log2(args.m))}, n in {{{args.ns}}} x geometric kappa in "
+                                   "{1e2,1e4,1e8,1e12,1e16}, sketch precision by rule, s=2n", "m": args.m, "ns": ns},
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -649,8 +799,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--m", type=int, default=1 << 20)
-    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--n", type=int, default=128, help="columns (sweep and reference workloads)")
+    ap.add_argument("--ns", default="64,128,256,512", help="columns of the large-factorization workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the small-factorization and batched keys")
     ap.add_argument("--workload", choices=["large", "batched", "sweep"], default="large")
     ap.add_argument("--transform", choices=["dct", "rfft", "rfft_reim"], default="dct",
                     help="sketch transform of the sweep workload")

@@ -82,10 +82,15 @@ typedef struct mrcqr_opts {
   int32_t check;      /* 1 (default): measure ||I - Q^T Q||_F on device and judge the result */
   int32_t escalate;   /* 1 (default): on failure re-run at the next precision (Sec. II-C),
                          FP16/BF16 -> FP32 -> FP64 */
-  int32_t sketch_variant; /* 0 (default): tensor-core sketch for FP16/BF16/FP32 when A is 16-byte aligned
-                             and lda is even, SIMT otherwise; the FP64 sketch as emulated FP64 on the
-                             tensor cores (unless fp64_products = 1); 1: SIMT (FP64 FMA for FP64);
-                             2: tensor cores when possible */
+  int32_t sketch_variant; /* 0 (default): for FP16/BF16/FP32, the faster of the two tensor-core variants
+                             by a table measured on GB300 (dense sampled rows, or the four-step
+                             transform where it applies) when A is 16-byte aligned and lda is even,
+                             SIMT otherwise; the FP64 sketch as emulated FP64 on the tensor cores
+                             (unless fp64_products = 1); 1: SIMT (FP64 FMA for FP64); 2: tensor-core
+                             dense sampled rows when possible; 4: the four-step transform (a radix-64
+                             DFT of the strided subsequences on the tensor cores, then only the
+                             sampled outputs) when possible -- DCT, FP16/BF16/FP32, m a multiple of
+                             1024 up to 2^22, at most 1024 sampled rows -- else as 2 */
   double ortho_tol;   /* acceptance threshold on ||I - Q^T Q||_F (default 1e-13) */
   void* stats_device; /* optional DEVICE pointer to an mrcqr_stats_t written at the end */
   int32_t fp64_products; /* 0 (default): the FP64 sketch, the off-diagonal updates of W = A R_s^{-1},
@@ -383,8 +388,8 @@ int mrcqr_mlp_train_step(int batch, const float* X, const int32_t* y, const floa
 /* ---- instrumentation (per-kernel timing) ------ */
 
 /* Sketch kernel variant used by the most recent sketch launch of this
- * process: 1 SIMT, 2 tensor cores, 3 emulated FP64 on the tensor cores
- * (0 before any). */
+ * process: 1 SIMT, 2 tensor-core dense sampled rows, 3 emulated FP64 on the
+ * tensor cores, 4 four-step transform (0 before any). */
 int mrcqr_last_sketch_variant(void);
 
 /* Number of kernels this library has launched from the host in this process

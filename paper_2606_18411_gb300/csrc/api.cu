@@ -52,7 +52,7 @@ Plan make_plan(int64_t m, int n, int s, int tf = T_DCT) {
   p.off_ctl = take(sizeof(Ctl));
   p.off_idx = take(sizeof(uint32_t) * (size_t)s);
   p.off_tab = take(sizeof(double) * (size_t)(m + 1));
-  p.off_ypart = take(sizeof(double) * (size_t)p.chunks * s * n);
+  p.off_ypart = take(sizeof(double) * (size_t)sketch_max_chunks(m, n, s) * s * n);
   p.off_y = take(sizeof(double) * (size_t)s * n);
   p.off_sqr = take(sqr_workspace_bytes(n, s));
   p.off_rs = take(sizeof(double) * (size_t)n * n);
@@ -245,12 +245,13 @@ int enqueue_sketch(const Plan& p, void* ws, int prec, int variant, int fp64_prod
     return 3;
   }
   double* ypart = at<double>(ws, p.off_ypart);
+  int chunks = p.chunks;
   launch(SG_SKETCH, lvl, st, [&] {
     used = launch_sketch(prec, variant, A, lda, p.m, p.n, p.s, idx, tab, seed, p.chunks,
-                         ypart, ctl, lvl, st, p.tf);
+                         ypart, ctl, lvl, st, p.tf, &chunks);
   });
   launch(SG_SKREDUCE, lvl, st, [&] {
-    launch_sketch_reduce(p.m, p.n, p.s, p.chunks, ypart, idx, Y, ctl, lvl, st, p.tf);
+    launch_sketch_reduce(p.m, p.n, p.s, chunks, ypart, idx, Y, ctl, lvl, st, p.tf);
   });
   return used;
 }

@@ -72,11 +72,21 @@ void launch_g_publish(const Group& g, cudaStream_t st);
 void launch_sample(int64_t m, int s, uint64_t seed, uint32_t* idx, const Ctl* ctl, cudaStream_t st, int tf = 0);
 void launch_costab(int64_t m, double* tab, cudaStream_t st);
 int sketch_chunks(int64_t m, int n, int s);
-// variant: 0 = auto (tensor cores when eligible), 1 = SIMT, 2 = tensor cores (falls back to SIMT when
-// the TMA preconditions fail).  Returns the variant launched (1 or 2).
+// variant: 0 = auto (the faster of the tensor-core variants by the measured choice table, SIMT when
+// neither is eligible), 1 = SIMT, 2 = tensor-core dense rows (falls back to SIMT when the TMA
+// preconditions fail), 4 = four-step (falls back to 2).  Returns the variant launched (1, 2 or 4) and
+// the number of partial-sum chunks written to Ypart in *chunks_used (at most max_chunks).
 int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m, int n, int s,
                   const uint32_t* idx, const double* tab, uint64_t seed, int chunks,
-                  double* Ypart, Ctl* ctl, int level, cudaStream_t st, int tf = 0);
+                  double* Ypart, Ctl* ctl, int level, cudaStream_t st, int tf = 0, int* chunks_used = nullptr);
+// four-step sketch (sketch_fs.cu): DCT, FP16/BF16/FP32, m a multiple of 1024 (<= 2^22), s <= 1024
+bool sketch_fs_eligible(int prec, int tf, const double* A, int64_t lda, int64_t m, int n, int s);
+int sketch_fs_chunks(int prec, int64_t m, int n);
+bool launch_sketch_fs(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,
+                      const double* tab, uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level,
+                      cudaStream_t st);
+// Partial-sum chunks the sketch of (m, n, s) may write (the larger of the variants' counts).
+int sketch_max_chunks(int64_t m, int n, int s);
 // tensor-core sketch (sketch_tc.cu): FP16/BF16/FP32, A 16-byte aligned, lda even
 bool sketch_tc_eligible(int prec, const double* A, int64_t lda);
 bool launch_sketch_tc(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,

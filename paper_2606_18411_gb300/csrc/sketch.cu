@@ -293,9 +293,40 @@ static int64_t rows_per_chunk(int64_t m, int chunks) {
   return (r + 63) / 64 * 64;
 }
 
+int sketch_max_chunks(int64_t m, int n, int s) {
+  int c = sketch_chunks(m, n, s);
+  for (int prec : {P_FP16, P_FP32}) {
+    const int f = sketch_fs_chunks(prec, m, n);
+    if (f > c) c = f;
+  }
+  return c;
+}
+
+// The faster tensor-core variant by measurement (dense rows V1 against the
+// four-step V2) for precision prec at n columns (s = 2n); true picks the
+// four-step.  Measured at m = 2^20 on GB300 (ms, V1 / V2): FP16 and BF16
+// n = 64: 0.51 / 0.79, 128: 0.83 / 1.47, 256: 2.78 / 3.22, 512: 19.6 / 8.7;
+// FP32 n = 64: 0.84 / 1.31, 128: 1.78 / 2.56, 256: 6.66 / 5.59,
+// 512: 49.1 / 14.8.  The dense-row variant's work grows as s n, the
+// four-step's as n; the switch points sit between the measured sizes.
+static bool four_step_preferred(int prec, int64_t m, int n) {
+  (void)m;
+  if (prec == P_FP32) return n >= 192;
+  return n >= 320;
+}
+
 int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m, int n, int s,
                   const uint32_t* idx, const double* tab, uint64_t seed, int chunks,
-                  double* Ypart, Ctl* ctl, int level, cudaStream_t st, int tf) {
+                  double* Ypart, Ctl* ctl, int level, cudaStream_t st, int tf, int* chunks_used) {
+  if (chunks_used) *chunks_used = chunks;
+  const bool fs_ok = (variant == 0 || variant == 4) && sketch_fs_eligible(prec, tf, A, lda, m, n, s);
+  if (fs_ok && (variant == 4 || four_step_preferred(prec, m, n))) {
+    const int fc = sketch_fs_chunks(prec, m, n);
+    if (launch_sketch_fs(prec, A, lda, m, n, s, idx, tab, seed, fc, Ypart, ctl, level, st)) {
+      if (chunks_used) *chunks_used = fc;
+      return 4;
+    }
+  }
   if (variant != 1 && sketch_tc_eligible(prec, A, lda) &&
       launch_sketch_tc(prec, A, lda, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf))
     return 2;

@@ -322,7 +322,131 @@ __global__ void __launch_bounds__(1024) k_chol_smem(int n, double* __restrict__ 
   }
 }
 
+// Blocked right-looking Cholesky over many CTAs (n > kCholBlockedMin): the
+// single-CTA elimination puts all n^3/3 FP64 flops on one SM's 1/64-rate
+// FP64 pipe (5.4 ms at n = 512), here the trailing updates spread over the
+// GPU.  Panels of kCB = 32 columns; for the panel at columns c0 .. c0 + 31:
+//   k_chol_diag    R_pp = chol(G_pp): one warp, lane j holds column j of the
+//                  block, pivots broadcast by shuffles (no block barriers);
+//   k_chol_panel   R_{p,j} = R_pp^{-T} G_{p,j} for the columns j beyond the
+//                  panel: forward substitution, one warp per column;
+//   k_chol_update  G_ij -= R_{p,i}^T R_{p,j} on the trailing upper triangle,
+//                  one CTA per 32 x 32 tile.
+// Same arithmetic per entry as the elimination (a sum over k of products,
+// one FMA each), a different order of the updates.  A pivot that is not
+// positive and finite raises BREAKDOWN; the later launches then return.
+constexpr int kCB = 32;
+constexpr int kCholBlockedMin = 64;
+
+__global__ void __launch_bounds__(32) k_chol_diag(int n, int c0, double* __restrict__ G, Ctl* ctl, int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int lane = threadIdx.x;
+  const int w = min(kCB, n - c0);
+  const int64_t col = (int64_t)(c0 + lane) * n + c0;   // column c0 + lane, row c0
+  double g[kCB];
+#pragma unroll
+  for (int i = 0; i < kCB; ++i) g[i] = (lane < w && i <= lane) ? G[col + i] : 0.0;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < kCB; ++k) {
+    if (k >= w) break;
+    const double d = __shfl_sync(0xffffffffu, g[k], k);
+    const double piv = (d > 0.0 && isfinite(d)) ? sqrt(d) : -1.0;
+    if (!(piv > 0.0)) {
+      ok = false;
+      break;
+    }
+    const double ip = 1.0 / piv;
+    if (lane == k) g[k] = piv;
+    else if (lane > k) g[k] *= ip;                      // r_k,lane
+#pragma unroll
+    for (int i = k + 1; i < kCB; ++i) {
+      const double rki = __shfl_sync(0xffffffffu, g[k], i);
+      if (i <= lane) g[i] = fma(-rki, g[k], g[i]);
+    }
+  }
+  if (!ok) {
+    if (lane == 0) raise_level_status(ctl, ST_BREAKDOWN);
+    return;
+  }
+  if (lane < w) {
+#pragma unroll
+    for (int i = 0; i < kCB; ++i)
+      if (i < w) G[col + i] = i <= lane ? g[i] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_chol_panel(int n, int c0, double* __restrict__ G, const Ctl* ctl,
+                                                    int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  __shared__ double Rp[kCB][kCB + 1];   // Rp[t][i] = R[c0 + t][c0 + i]
+  __shared__ double rdiag[kCB];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int e = tid; e < kCB * kCB; e += blockDim.x) {
+    const int t = e % kCB, i = e / kCB;
+    Rp[t][i] = G[(int64_t)(c0 + i) * n + c0 + t];
+  }
+  __syncthreads();
+  if (tid < kCB) rdiag[tid] = 1.0 / Rp[tid][tid];
+  __syncthreads();
+  const int j = c0 + kCB + blockIdx.x * 8 + (tid >> 5);
+  if (j >= n) return;
+  double* colj = G + (int64_t)j * n + c0;
+  double b = colj[lane];
+#pragma unroll
+  for (int t = 0; t < kCB; ++t) {
+    const double xt = __shfl_sync(0xffffffffu, b, t) * rdiag[t];
+    if (lane == t) b = xt;
+    else if (lane > t) b = fma(-Rp[t][lane], xt, b);
+  }
+  colj[lane] = b;
+  G[(int64_t)(c0 + lane) * n + j] = 0.0;   // strict lower triangle of the panel columns
+}
+
+__global__ void __launch_bounds__(256) k_chol_update(int n, int c0, double* __restrict__ G, const Ctl* ctl,
+                                                     int level) {
+  if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
+  const int c1 = c0 + kCB;
+  // tile (I, J), I <= J, of the trailing upper triangle, numbered column by column
+  int J = 0, b = blockIdx.x;
+  while (b > J) {
+    b -= J + 1;
+    ++J;
+  }
+  const int I = b;
+  __shared__ double PI[kCB][kCB], PJ[kCB][kCB];   // P[t][i] = R[c0 + t][c1 + 32 X + i]
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kCB * kCB; e += blockDim.x) {
+    const int t = e % kCB, i = e / kCB;
+    const int ci = c1 + kCB * I + i, cj = c1 + kCB * J + i;
+    PI[t][i] = ci < n ? G[(int64_t)ci * n + c0 + t] : 0.0;
+    PJ[t][i] = cj < n ? G[(int64_t)cj * n + c0 + t] : 0.0;
+  }
+  __syncthreads();
+  const int ii = tid & 31, gi = c1 + kCB * I + ii;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int jj = (tid >> 5) + 8 * q, gj = c1 + kCB * J + jj;
+    if (gi >= n || gj >= n || gi > gj) continue;
+    double acc = G[(int64_t)gj * n + gi];
+#pragma unroll 8
+    for (int t = 0; t < kCB; ++t) acc = fma(-PI[t][ii], PJ[t][jj], acc);
+    G[(int64_t)gj * n + gi] = acc;
+  }
+}
+
 void launch_chol(int n, double* G, Ctl* ctl, int level, cudaStream_t st) {
+  if (n > kCholBlockedMin) {
+    for (int c0 = 0; c0 < n; c0 += kCB) {
+      { ::mrcqr::note_launch(); k_chol_diag<<<1, 32, 0, st>>>(n, c0, G, ctl, level); }
+      const int ncols = n - c0 - kCB;
+      if (ncols <= 0) break;
+      { ::mrcqr::note_launch(); k_chol_panel<<<(ncols + 7) / 8, 256, 0, st>>>(n, c0, G, ctl, level); }
+      const int T = (ncols + kCB - 1) / kCB;
+      { ::mrcqr::note_launch(); k_chol_update<<<T * (T + 1) / 2, 256, 0, st>>>(n, c0, G, ctl, level); }
+    }
+    return;
+  }
   if (n <= kCholSmemN) {
     const size_t smem = sizeof(double) * (size_t)n * n;
     cudaFuncSetAttribute(k_chol_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,

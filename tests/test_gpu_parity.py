@@ -135,6 +135,38 @@ def test_sketch_variants_agree_and_fall_back(M):
     assert M.last_sketch_variant() == 1
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+@pytest.mark.parametrize("m,n,s", [(2048, 5, 30), (3072, 7, 14), (8192, 33, 66), (1 << 16, 128, 256),
+                                   (5 << 13, 100, 200), (1 << 15, 3, 1024), (1 << 17, 64, 128)])
+def test_sketch_four_step_against_oracle(M, prec, m, n, s):
+    # the four-step variant (radix-64 DFT of the strided subsequences on the tensor cores, then only
+    # the s sampled outputs): m a multiple of 1024 (power of two or not), ragged n, s up to 1024
+    A = inputs.make_matrix(m, n, 1e6, seed=m + 5 * n)
+    Y = _np(M.sketch(M.to_colmajor(A), s, prec, seed=19, variant=4))
+    assert M.last_sketch_variant() == 4
+    d, idx = O.rademacher(m, 19), O.sample_rows(m, s, 19)
+    ref = O.sketch(A, idx, d)
+    assert _rel(Y, ref) <= SKETCH_TOL[prec], _rel(Y, ref)
+    emu = O.sketch_emulated(A, idx, d, prec)
+    assert _rel(Y, emu) <= 2 * SKETCH_TOL[prec]
+    # per column as well (the 2^e scale is per tile and column)
+    colerr = np.linalg.norm(Y - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert colerr.max() <= 2 * SKETCH_TOL[prec]
+
+
+def test_sketch_four_step_falls_back(M):
+    # not a multiple of 1024 rows, or the real-FFT transform: the dense-row tensor-core variant runs
+    A = inputs.make_matrix(5000, 16, 1e3, seed=3)
+    _ = M.sketch(M.to_colmajor(A), 32, "fp16", seed=1, variant=4)
+    assert M.last_sketch_variant() == 2
+    B = M.to_colmajor(inputs.make_matrix(4096, 16, 1e3, seed=4))
+    _ = M.sketch_transform(B, 32, "rfft", prec="fp16", seed=1, variant=4)
+    assert M.last_sketch_variant() == 2
+    # odd leading dimension: no TMA at all
+    _ = M.sketch(M.to_colmajor(inputs.make_matrix(4096, 16, 1e3, seed=5), ld=4097), 32, "fp16", seed=1, variant=4)
+    assert M.last_sketch_variant() == 1
+
+
 def test_sketch_scale_exponent_keeps_fp16_in_range(M):
     # columns of very different magnitude (1e-12 .. 1e6): per-column 2^e scaling
     m, n = 8192, 8
