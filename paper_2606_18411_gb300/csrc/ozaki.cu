@@ -312,17 +312,21 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       if (tid < kM) rowE[tid] = oz::exp_field(max(max(redE[0][tid], redE[1][tid]), max(redE[2][tid], redE[3][tid])));
       __syncthreads();
     }
-    const int r = tid & (kM - 1), pp = tid >> 7;   // producer role: row r, column pairs pp + 4 i
+    const int r = tid & (kM - 1), pp = tid >> 7;   // producer role: row r, 16-byte chunk pp of each K chunk
     const bool live = r0 + r < m;
     for (int t = ntiles - 1; t >= 0 && !abort; --t) {
       long long hi[16], lo[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
       double v[4][2];
-      auto load_w = [&](int kc) {   // W of columns [32 kc, 32 kc + 32): row r, column pairs pp + 4 i
+      // row r, the four column pairs of 16-byte chunk pp of each 32-column chunk; lane group
+      // lane / 8 starts at a different pair, so a warp's 4-byte panel stores hit 32 banks
+      const int lg = lane >> 3;
+      auto pair_of = [&](int i) { return 4 * pp + ((lg + i) & 3); };
+      auto load_w = [&](int kc) {   // W of columns [32 kc, 32 kc + 32)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int k0 = kc * kK + 2 * (pp + 4 * i);
+          const int k0 = kc * kK + 2 * pair_of(i);
           v[i][0] = (live && k0 < n) ? Q[r0 + r + (int64_t)k0 * ldq] : 0.0;
           v[i][1] = (live && k0 + 1 < n) ? Q[r0 + r + (int64_t)(k0 + 1) * ldq] : 0.0;
         }
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         const uint32_t Er = rowE[r];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-          oz_store_pair(v[i][0], v[i][1], 0u, 0u, Er, a + tc::sw64_offset(r, 2 * (pp + 4 * i), 2), kAPanel);
+          oz_store_pair(v[i][0], v[i][1], 0u, 0u, Er, a + tc::sw64_offset(r, 2 * pair_of(i), 2), kAPanel);
         if (kc + 1 < nch) load_w(kc + 1);
         tc::cp_async_wait_all();
       };
@@ -733,7 +737,7 @@ __global__ void __launch_bounds__(kTThreads, 2)
   uint32_t commits = 0;
   bool abort = false;
   const int64_t nblocks = (m + kM - 1) / kM;
-  const int pr = tid & (kM - 1), ph = tid >> 7;   // producer role: row pr, column pairs ph + 2 i
+  const int pr = tid & (kM - 1), ph = tid >> 7;   // producer role: row pr, 16-byte chunks 2 ph, 2 ph + 1
   constexpr int kNoEntry = -100000, kNonfinite = 100000;
   for (int k = tid; k < n; k += kTThreads) {
     eRs[k] = eR[k];
@@ -773,18 +777,22 @@ __global__ void __launch_bounds__(kTThreads, 2)
           const uint4* src = reinterpret_cast<const uint4*>(Rd + (size_t)(J * nkc + kc) * oz::kSlices * kTBPanel);
 #pragma unroll
           for (int i = 0; i < 2; ++i) tc::cp_async16(bs + 16 * (tid + kTThreads * i), src + tid + kTThreads * i);
-          // W digits of columns [32 kc, 32 kc + 32) (zero from c0 on): row pr, column pairs ph + 2 i
+          // W digits of columns [32 kc, 32 kc + 32) (zero from c0 on): row pr, the eight column
+          // pairs of 16-byte chunks 2 ph and 2 ph + 1; lane group lane / 8 rotates through the
+          // chunk's four pairs, so a warp's 4-byte panel stores hit 32 banks
+          const int lg = lane >> 3;
+          auto pair_of = [&](int i) { return 4 * (2 * ph + (i & 1)) + ((lg + (i >> 1)) & 3); };
           double v[8][2];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const int k0 = kc * kK + 2 * (ph + 2 * i);
+            const int k0 = kc * kK + 2 * pair_of(i);
             v[i][0] = (plive && k0 < c0) ? W[r0 + pr + (int64_t)k0 * ldw] : 0.0;
             v[i][1] = (plive && k0 + 1 < c0) ? W[r0 + pr + (int64_t)(k0 + 1) * ldw] : 0.0;
           }
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const int k0 = kc * kK + 2 * (ph + 2 * i);
-            oz_store_pair(v[i][0], v[i][1], 0u, 0u, Er, as + tc::sw64_offset(pr, 2 * (ph + 2 * i), 2), kTAPanel,
+            const int k0 = kc * kK + 2 * pair_of(i);
+            oz_store_pair(v[i][0], v[i][1], 0u, 0u, Er, as + tc::sw64_offset(pr, 2 * pair_of(i), 2), kTAPanel,
                           k0 < n ? eRs[k0] : 0, k0 + 1 < n ? eRs[k0 + 1] : 0);
           }
           tc::cp_async_wait_all();

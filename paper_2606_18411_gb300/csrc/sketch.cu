@@ -305,9 +305,9 @@ int sketch_max_chunks(int64_t m, int n, int s) {
 // The faster tensor-core variant by measurement (dense rows V1 against the
 // four-step V2) for precision prec at n columns (s = 2n); true picks the
 // four-step.  Measured at m = 2^20 on GB300 (ms, V1 / V2): FP16 and BF16
-// n = 64: 0.51 / 0.79, 128: 0.83 / 1.47, 256: 2.78 / 3.22, 512: 19.6 / 8.7;
-// FP32 n = 64: 0.84 / 1.31, 128: 1.78 / 2.56, 256: 6.66 / 5.59,
-// 512: 49.1 / 14.8.  The dense-row variant's work grows as s n, the
+// n = 64: 0.51 / 0.74, 128: 0.83 / 1.36, 256: 2.78 / 2.81, 512: 19.6 / 8.1;
+// FP32 n = 64: 0.84 / 1.03, 128: 1.79 / 2.21, 256: 6.67 / 4.53,
+// 512: 49.1 / 11.8.  The dense-row variant's work grows as s n, the
 // four-step's as n; the switch points sit between the measured sizes.
 static bool four_step_preferred(int prec, int64_t m, int n) {
   (void)m;

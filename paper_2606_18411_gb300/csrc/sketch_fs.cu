@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t mma_bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ float colscale[2][C];
-  __shared__ uint64_t redmax[kThreads / 32][C];
+  __shared__ uint32_t red32[kThreads / 32][C];
+  __shared__ uint64_t redmax[kThreads / 32];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t m1 = m / kM2;
@@ -175,18 +176,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0)
     for (; issued < F::STAGES && issued < total; ++issued) issue_tma(issued);
 
-  // step-2 identity: samples tid + 512 i, all C columns of the tile
+  // step-2 identity: G thread groups share the samples when s is small (each group takes C / G of
+  // the tile's columns, so every thread works); thread t: group t / SPT, sample slots t % SPT + SPT i
+  int G = 1;
+  while (G < C && s * (G * 2) <= kThreads) G *= 2;
+  const int SPT = kThreads / G;
+  const int grp = tid / SPT, slot = tid % SPT;
+  const int cg_lo = grp * (C / G), cg_hi = cg_lo + C / G;
+  const float inv2m = 1.0f / (2.0f * (float)m);
+  const uint32_t fm32 = (uint32_t)four_m;   // 4m <= 2^24
   int srow_r[kKpt], srow_i[kKpt];
   float ssig[kKpt], rot_c[kKpt], rot_s[kKpt];
-  uint32_t sk[kKpt];
+  uint32_t sk[kKpt], sk2[kKpt], sk32[kKpt], ph[kKpt];   // k, 2k, 32k mod 4m, phase k (2 j1_0 + 1) mod 4m
 #pragma unroll
   for (int i = 0; i < kKpt; ++i) {
-    const int si = tid + kThreads * i;
+    const int si = slot + SPT * i;
     srow_r[i] = srow_i[i] = kRows;
     ssig[i] = 0.f;
     rot_c[i] = 1.f;
     rot_s[i] = 0.f;
-    sk[i] = 0u;
+    sk[i] = sk2[i] = sk32[i] = ph[i] = 0u;
     if (si < s) {
       const uint32_t k = idx[si];
       const int r = (int)(k & 127u);
@@ -195,8 +204,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       srow_i[i] = (rp == 0 || rp == 64) ? kRows : 64 + rp;
       ssig[i] = r <= 64 ? 1.f : -1.f;
       sk[i] = k;
-      // rotation by pi k / m per j1 step (k / m exact for power-of-two m; otherwise within an ulp)
-      sincospif((float)k / (float)m, &rot_s[i], &rot_c[i]);
+      sk2[i] = 2u * k;
+      sk32[i] = (uint32_t)((32ull * k) % four_m);
+      // rotation by pi k / m per j1 step (exact argument for power-of-two m; otherwise within an ulp)
+      sincospif((float)sk2[i] * inv2m, &rot_s[i], &rot_c[i]);
     }
   }
   float acc[kKpt][C];
@@ -211,44 +222,53 @@ __global__ void __launch_bounds__(kThreads, 1)
   bool abort = false;
   int consumed = 0, mma_issued = 0, mma_done = 0;
 
-  auto step2 = [&](int u) {   // U holds the tile u products
+  auto step2 = [&](int u) {   // U holds the tile u products; column c, j1 jj at U column c kB + jj
     int item, j1_0;
     tile_of(u, item, j1_0);
     const int b = u & 1;
+    const bool first = u % tiles_per_chunk == 0;
 #pragma unroll
     for (int i = 0; i < kKpt; ++i) {
-      if (tid + kThreads * i >= s) continue;
+      if (slot + SPT * i >= s) continue;
+      // phase at this tile's first j1: from scratch at an item's first tile, else advanced by 16 j1
+      if (first) ph[i] = (uint32_t)(((uint64_t)sk[i] * (uint64_t)(2 * j1_0 + 1)) % four_m);
+      uint32_t P = ph[i];
       const float* ur = U + srow_r[i] * F::USTR;
       const float* ui = U + srow_i[i] * F::USTR;
       const float sg = ssig[i];
       float cph = 0.f, sph = 0.f;
 #pragma unroll
       for (int jj = 0; jj < kB; ++jj) {
-        if ((jj & 3) == 0) {   // exact twiddle: phase k (2 j1 + 1) mod 4m, an integer below 2^24 for m <= 2^22
-          const uint64_t P = ((uint64_t)sk[i] * (uint64_t)(2 * (j1_0 + jj) + 1)) % four_m;
-          sincospif((float)P / (float)(2 * m), &sph, &cph);
+        if ((jj & 3) == 0) {   // exact twiddle every four j1, the phase an integer below 2^24
+          sincospif((float)P * inv2m, &sph, &cph);
         } else {
           const float c2 = cph * rot_c[i] - sph * rot_s[i];
           sph = sph * rot_c[i] + cph * rot_s[i];
           cph = c2;
         }
+        P += sk2[i];
+        if (P >= fm32) P -= fm32;
         const float ss = sg * sph;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          const float t = fmaf(cph, ur[jj * C + c], -ss * ui[jj * C + c]);
+          if (c < cg_lo || c >= cg_hi) continue;
+          const float t = fmaf(cph, ur[c * kB + jj], -ss * ui[c * kB + jj]);
           acc[i][c] = fmaf(t, colscale[b][c], acc[i][c]);
         }
       }
+      uint32_t nx = ph[i] + sk32[i];
+      if (nx >= fm32) nx -= fm32;
+      ph[i] = nx;
     }
     if (u % tiles_per_chunk == tiles_per_chunk - 1) {   // last tile of the item: write its partial sums
       const int ch = item / ncb, c0 = (item % ncb) * C;
       double* out = Ypart + (size_t)ch * (size_t)s * (size_t)n;
 #pragma unroll
       for (int i = 0; i < kKpt; ++i) {
-        const int si = tid + kThreads * i;
+        const int si = slot + SPT * i;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          if (si < s && c0 + c < n) out[(size_t)(c0 + c) * s + si] = (double)acc[i][c];
+          if (si < s && c >= cg_lo && c < cg_hi && c0 + c < n) out[(size_t)(c0 + c) * s + si] = (double)acc[i][c];
           acc[i][c] = 0.f;
         }
       }
@@ -297,25 +317,40 @@ __global__ void __launch_bounds__(kThreads, 1)
         vh[c][h] = w.y ^ sgn[h];
         vl[c][h] = w.x;
       }
-      const uint64_t a0 = ((uint64_t)(vh[c][0] & 0x7FFFFFFFu) << 32) | vl[c][0];
-      const uint64_t a1 = ((uint64_t)(vh[c][1] & 0x7FFFFFFFu) << 32) | vl[c][1];
-      const uint64_t mx = u64_max_warp(a0 > a1 ? a0 : a1);
-      if (lane == 0) redmax[warp][c] = mx;
+      // the exponent field orders |x| like the value: the high words' maximum gives the scale
+      const uint32_t mx = __reduce_max_sync(0xffffffffu, max(vh[c][0] & 0x7FFFFFFFu, vh[c][1] & 0x7FFFFFFFu));
+      if (lane == 0) red32[warp][c] = mx;
     }
     __syncthreads();
     if (tid < C) {
-      uint64_t mx = 0;
-      for (int w = 0; w < kThreads / 32; ++w) mx = redmax[w][tid] > mx ? redmax[w][tid] : mx;
-      redmax[0][tid] = mx;
+      uint32_t mx = 0u;
+      for (int w = 0; w < kThreads / 32; ++w) mx = max(mx, red32[w][tid]);
+      red32[0][tid] = mx;
     }
     __syncthreads();
     unsigned char* xb = xop + buf * F::PARTS * F::KPANELS * F::X_PANEL;
+    const int c0t = (item % ncb) * C;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const uint64_t mx = redmax[0][c];
-      const int e = scale_exponent_bits((uint32_t)(mx >> 32), (uint32_t)mx);
+      const uint32_t hmx = red32[0][c];
+      int e = 0;
+      if (c0t + c < n) {
+        if ((hmx >> 20) != 0u) {
+          e = scale_exponent_bits(hmx, 1u);
+        } else {   // no normal value in this tile column: the exact 64-bit maximum (uniform branch)
+          const uint64_t a0 = ((uint64_t)(vh[c][0] & 0x7FFFFFFFu) << 32) | vl[c][0];
+          const uint64_t a1 = ((uint64_t)(vh[c][1] & 0x7FFFFFFFu) << 32) | vl[c][1];
+          const uint64_t mw = u64_max_warp(a0 > a1 ? a0 : a1);
+          __syncthreads();
+          if (lane == 0) redmax[warp] = mw;
+          __syncthreads();
+          uint64_t mb = 0;
+          for (int w = 0; w < kThreads / 32; ++w) mb = redmax[w] > mb ? redmax[w] : mb;
+          e = scale_exponent_bits((uint32_t)(mb >> 32), (uint32_t)mb);
+        }
+      }
       if (tid == 0) colscale[buf][c] = ldexpf(1.0f, -e);
-      const int row = cj1 * C + c;   // MMA N index: (j1, column)
+      const int row = c * kB + cj1;   // MMA N index: (column, j1)
       if constexpr (PREC == P_FP32) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {

@@ -3,8 +3,8 @@
 Every step runs in libmrcqr's kernels (features, MLP forward/backward,
 AdamW); this module only generates data, drives the training loop and
 stores the weights.  Data: synthetic m x n FP64 matrices A = U diag(sigma)
-V^T (spectra geometric, step-cliff, clustered, log-uniform; kappa_2
-log-uniform in [1, 1e16]), each labelled by running MRCQR without
+V^T (spectra geometric, step-cliff, clustered, log-uniform; n uniform in
+[32, 512]; kappa_2 log-uniform in [1, 1e16]), each labelled by running MRCQR without
 escalation at FP16 and at FP32: label 0 if FP16 passes the 1e-13 judge,
 1 if only FP32 does, 2 otherwise (FP64).
 
@@ -63,7 +63,7 @@ def passes(A: torch.Tensor, prec: str, seed: int = 0) -> bool:
     return M.last_status()["status"] == "OK"
 
 
-def make_dataset(count: int, m: int, seed0: int, n_range=(32, 256), verify_fp64_every: int = 20, device="cuda",
+def make_dataset(count: int, m: int, seed0: int, n_range=(32, 512), verify_fp64_every: int = 20, device="cuda",
                  log_every: int = 0):
     """Features X (count x 16), labels y, and (n, kappa, spectrum) of each matrix."""
     rng = np.random.default_rng(seed0)
@@ -181,7 +181,7 @@ def set_weights(params, mu, sd, costs) -> None:
     M._selector_state["loaded"] = True
 
 
-def measure_costs(m=1 << 16, n=144, reps=5, device="cuda"):
+def measure_costs(m=1 << 16, n=256, reps=5, device="cuda"):
     """Relative time of one MRCQR run per sketch precision (FP16 = 1)."""
     A = inputs.make_matrix_torch(m, n, 10.0, seed=1, device=device)
     Q = M.empty_colmajor(m, n, device=device)
@@ -204,7 +204,7 @@ def ladder_cost(start: int, label: int, costs) -> float:
     return costs[start] if start >= label else float(sum(costs[start:label + 1]))
 
 
-def heldout_matrices(count: int, m: int, seed0: int = 2, n_range=(32, 256), device="cuda"):
+def heldout_matrices(count: int, m: int, seed0: int = 2, n_range=(32, 512), device="cuda"):
     """The matrices of ``make_dataset(count, m, seed0)`` in order (the same draws), with (n, kappa, kind)."""
     rng = np.random.default_rng(seed0)
     for i in range(count):
@@ -281,6 +281,44 @@ def evaluate_baselines(count: int, m: int, weights: str = DEFAULT_WEIGHTS, log_e
     return rep
 
 
+def policy_times(count: int, m: int, seed0: int = 5, n_choices=(64, 128, 256), reps: int = 2, device="cuda"):
+    """Measured wall time of three policies over the same held-out mix (kappa_2 log-uniform in
+    [1, 1e16], the four spectra, n from n_choices): AUTO (the selector's FP16 sketch, features and
+    choice included), always FP32 (escalating on failure) and always FP64.  Each matrix is factored
+    once per policy per repetition, the policies interleaved per matrix; CUDA events around each
+    call.  Returns total ms per policy and the statuses."""
+    rng = np.random.default_rng(seed0)
+    mats = []
+    for i in range(count):
+        n = int(rng.choice(n_choices))
+        kind = SPECTRA[int(rng.integers(len(SPECTRA)))]
+        kappa = float(10.0 ** rng.uniform(0.0, 16.0))
+        mats.append((inputs.make_matrix_torch(m, n, kappa, kind=kind, seed=seed0 * 1000003 + i, device=device),
+                     (n, kappa, kind)))
+    load_into_library()
+    tot = {"auto": 0.0, "fp32": 0.0, "fp64": 0.0}
+    ok = {k: True for k in tot}
+    stats = torch.zeros(8, dtype=torch.float64, device=device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for r in range(reps + 1):          # the first pass warms up
+        for i, (A, _) in enumerate(mats):
+            mm, n = A.shape
+            Q = M.empty_colmajor(mm, n, device=device)
+            R = M.empty_colmajor(n, n, device=device)
+            for pol in ("auto", "fp32", "fp64"):
+                torch.cuda.synchronize()
+                e0.record()
+                M.factor_ex(A, Q, R, prec=pol, seed=i, stats_device=stats)
+                e1.record()
+                torch.cuda.synchronize()
+                if r > 0:
+                    tot[pol] += e0.elapsed_time(e1)
+                    ok[pol] = ok[pol] and _lib.Stats.from_buffer_copy(stats.cpu().numpy().tobytes()).status == 0
+    return {"count": count, "m": m, "n_choices": list(n_choices), "reps": reps,
+            "total_ms": {k: v / reps for k, v in tot.items()}, "all_ok": ok,
+            "auto_speedup": {"vs_fp32": tot["fp32"] / tot["auto"], "vs_fp64": tot["fp64"] / tot["auto"]}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -289,6 +327,7 @@ def main():
     t.add_argument("--heldout", type=int, default=2000)
     t.add_argument("--m", type=int, default=1 << 16)
     t.add_argument("--epochs", type=int, default=40)
+    t.add_argument("--n-max", type=int, default=512)
     t.add_argument("--out", default=DEFAULT_WEIGHTS)
     t.add_argument("--report", default=None)
     b = sub.add_parser("baselines")
@@ -296,12 +335,15 @@ def main():
     b.add_argument("--m", type=int, default=1 << 16)
     b.add_argument("--weights", default=DEFAULT_WEIGHTS)
     b.add_argument("--report", default=None)
+    b.add_argument("--policy-count", type=int, default=48)
+    b.add_argument("--policy-m", type=int, default=1 << 20)
     args = ap.parse_args()
     from . import build
     build.build()
     torch.cuda.set_device(0)
     if args.cmd == "baselines":
         rep = evaluate_baselines(args.heldout, args.m, args.weights, log_every=500)
+        rep["measured_policy_times"] = policy_times(args.policy_count, args.policy_m)
         print(json.dumps(rep), flush=True)
         if args.report:
             with open(args.report, "w") as f:
@@ -310,8 +352,9 @@ def main():
     t0 = time.time()
     costs, times = measure_costs(m=args.m)
     print(f"relative run costs fp16/fp32/fp64: {costs} ({times} ms)", flush=True)
-    Xtr, ytr, _, v1 = make_dataset(args.count, args.m, seed0=1, log_every=2000)
-    Xte, yte, meta_te, v2 = make_dataset(args.heldout, args.m, seed0=2, log_every=1000)
+    nr = (32, args.n_max)
+    Xtr, ytr, _, v1 = make_dataset(args.count, args.m, seed0=1, n_range=nr, log_every=2000)
+    Xte, yte, meta_te, v2 = make_dataset(args.heldout, args.m, seed0=2, n_range=nr, log_every=1000)
     t_data = time.time() - t0
     tr, mu, sd, losses = train(Xtr, ytr, epochs=args.epochs, log=lambda s: print(s, flush=True))
     params = tr.master.cpu().numpy()
