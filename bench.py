@@ -570,12 +570,27 @@ def batched_summary(torch, M, inputs, dev, rank, count=512, steps=3):
     t = e0.elapsed_time(e1) / 1e3
     ok = status.cpu().tolist()
     plan.close()
+    # the same batch with the emulated-FP64 heavy phases as single-problem kernels per problem on side streams
+    plan_pp = M.BatchedPlan(As, Qs, Rs, precs, list(range(count)), status, use_graph=True, oz_per_problem=1)
+    info_pp = plan_pp.info()
+    plan_pp.execute()
+    torch.cuda.synchronize()
+    e0.record()
+    plan_pp.execute()
+    e1.record()
+    torch.cuda.synchronize()
+    t_pp = e0.elapsed_time(e1) / 1e3
+    ok_pp = status.cpu().tolist()
+    plan_pp.close()
     del As, Qs, Rs
     torch.cuda.empty_cache()
     return {"workload": f"{count} factorizations, m uniform in [2^14,2^18], n in {{16,32,64,128}}, kappa "
                         "log-uniform in [1,1e12], precision by rule, one batched plan replayed as a CUDA graph",
             "factorizations_per_s": round(count * steps / t, 1), "steps": steps,
-            "kernels_per_execute": info["kernels_per_execute"], "all_ok": all(v == 0 for v in ok)}
+            "kernels_per_execute": info["kernels_per_execute"], "tuning": info, "all_ok": all(v == 0 for v in ok),
+            "per_problem_heavy_phases": {"factorizations_per_s": round(count / t_pp, 1),
+                                         "kernels_per_execute": info_pp["kernels_per_execute"],
+                                         "all_ok": all(v == 0 for v in ok_pp)}}
 
 
 def run_batched(args):
@@ -792,6 +807,54 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kernels(args):
+    """Kernel-level workload for profiling captures: `reps` sketches (--stage sketch, variant --variant)
+    or factorizations (--stage factor, escalation off) of one m x n matrix (geometric spectrum,
+    kappa --kappa) at precision --prec; prints the per-stage CUDA-event times of the last rep."""
+    import ctypes
+    import torch
+    from paper_2606_18411_gb300 import build as _build
+    from paper_2606_18411_gb300 import inputs, _lib
+    from paper_2606_18411_gb300 import mrcqr as M
+    rank, _, local = env_rank()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    _build.build()
+    lib = _lib.load()
+    m, n = args.m, args.n
+    A = inputs.make_matrix_torch(m, n, args.kappa, seed=4, device="cuda")
+    Q, R = M.empty_colmajor(m, n), M.empty_colmajor(n, n)
+
+    def one():
+        if args.stage == "sketch":
+            M.sketch(A, 2 * n, args.prec, seed=0, variant=args.variant)
+        else:
+            M.factor_ex(A, Q, R, prec=args.prec, seed=0, escalate=False, sketch_variant=args.variant)
+
+    for _ in range(args.reps - 1):
+        one()
+    torch.cuda.synchronize()
+    lib.mrcqr_profile_begin()
+    one()
+    torch.cuda.synchronize()
+    cap = 10000
+    cnt = ctypes.c_int32()
+    st = (ctypes.c_int32 * cap)()
+    lv = (ctypes.c_int32 * cap)()
+    ms = (ctypes.c_float * cap)()
+    lib.mrcqr_profile_end(cap, st, lv, ms, ctypes.byref(cnt))
+    per = {}
+    for i in range(cnt.value):
+        k = lib.mrcqr_stage_name(st[i]).decode()
+        per[k] = round(per.get(k, 0.0) + ms[i], 4)
+    out = {"workload": f"{args.stage} m={m} n={n} prec={args.prec} variant={args.variant} kappa={args.kappa:g}",
+           "stage_ms": per, "sketch_variant": M.last_sketch_variant()}
+    if args.stage == "factor":
+        out["status"] = M.last_status()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -803,7 +866,12 @@ def main():
     ap.add_argument("--ns", default="64,128,256,512", help="columns of the large-factorization workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the small-factorization and batched keys")
-    ap.add_argument("--workload", choices=["large", "batched", "sweep"], default="large")
+    ap.add_argument("--workload", choices=["large", "batched", "sweep", "kernels"], default="large")
+    ap.add_argument("--stage", choices=["sketch", "factor"], default="factor", help="kernels workload: what to run")
+    ap.add_argument("--prec", default="fp16", help="kernels workload: sketch precision")
+    ap.add_argument("--variant", type=int, default=0, help="kernels workload: sketch variant (0 auto, 2 V1, 4 V2)")
+    ap.add_argument("--kappa", type=float, default=1e2, help="kernels workload: condition number")
+    ap.add_argument("--reps", type=int, default=2, help="kernels workload: repetitions (the last is timed)")
     ap.add_argument("--transform", choices=["dct", "rfft", "rfft_reim"], default="dct",
                     help="sketch transform of the sweep workload")
     ap.add_argument("--s-factor", type=int, default=2, help="sampled rows or bins per column (sweep workload)")
@@ -817,6 +885,8 @@ def main():
         run_batched(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "kernels":
+        run_kernels(args)
     else:
         run_ours(args)
 

@@ -175,12 +175,15 @@ typedef struct mrcqr_batched_opts {
   double ortho_tol;       /* default 1e-13 */
   int64_t rows_per_split; /* SYRK rows per partial (0: tuned or default 4096) */
   int64_t rows_per_chunk; /* sketch rows per partial (0: tuned or default 8192) */
-  int32_t fp64_products;  /* 0 (default): emulated FP64 products, the single-problem tensor-core kernels of the
-                             FP64 sketch and stage 2 run per problem on side streams (fork/join inside the plan);
-                             1: every phase grouped with FP64 FMA kernels */
+  int32_t fp64_products;  /* 0 (default): emulated FP64 products on the tensor cores; 1: every phase grouped with
+                             FP64 FMA kernels */
   int32_t transform;      /* mrcqr_transform_t of every problem's sketch (default DCT): 2n sampled rows, or 2n
                              bins of the real FFT (then 2n <= floor(m/2) + 1 for every problem, and 4n <= 8192
                              for MRCQR_TRANSFORM_RFFT_REIM; INVALID otherwise) */
+  int32_t oz_per_problem; /* with emulated FP64 products: 0 (default) runs the FP64 sketch, W = A R_s^-1, the
+                             Gram, Q = W R_c^-1 and the check as one grouped persistent launch per kernel over
+                             every problem's {problem, row block or tile} items; 1 runs the single-problem
+                             kernels per problem on side streams (fork/join inside the plan) */
 } mrcqr_batched_opts_t;
 
 int mrcqr_batched_plan_create(int count, const int64_t* m, const int64_t* n, const double* const* A,

@@ -30,7 +30,8 @@ class Opts(ctypes.Structure):
 class BatchedOpts(ctypes.Structure):
     _fields_ = [("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32), ("check", ctypes.c_int32),
                 ("escalate", ctypes.c_int32), ("ortho_tol", ctypes.c_double), ("rows_per_split", ctypes.c_int64),
-                ("rows_per_chunk", ctypes.c_int64), ("fp64_products", ctypes.c_int32), ("transform", ctypes.c_int32)]
+                ("rows_per_chunk", ctypes.c_int64), ("fp64_products", ctypes.c_int32), ("transform", ctypes.c_int32),
+                ("oz_per_problem", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -8,9 +8,11 @@
 //
 // With emulated FP64 products (the default, as in mrcqr_factor) the heavy
 // phases -- the FP64 sketch, W = A R_s^{-1}, the Gram, Q = W R_c^{-1} and the
-// check -- run the single-problem tensor-core kernels per problem, spread over
-// side streams so that problems overlap; the light phases stay grouped.
-// fp64_products = 1 runs every phase grouped with FP64 FMA kernels.
+// check -- run as grouped persistent tensor-core kernels too: one launch per
+// kernel walks the {problem, row block / tile} items of every problem
+// (oz_per_problem = 1 instead runs the single-problem kernels per problem on
+// side streams).  fp64_products = 1 runs every phase grouped with FP64 FMA
+// kernels.
 //
 // A plan (mrcqr_batched_plan_*) keeps the workspace, the uploaded work lists
 // and optionally the whole launch sequence captured as a CUDA graph, so a
@@ -43,7 +45,10 @@ enum Kind {
   K_INIT, K_SAMPLE, K_COSTAB, K_SKETCH, K_SKREDUCE, K_SQR, K_TRSM, K_SYRK, K_GREDUCE, K_CHOL, K_TRINV, K_RMUL,
   K_FINALIZE, K_CHECK, K_EREDUCE, K_JUDGE, K_PUBLISH,
   // emulated-FP64 phases of one problem (param = problem) between a fork and a join of the side streams
-  K_FORK, K_JOIN, K_OZ_SKETCH, K_OZ_STAGE2A, K_OZ_STAGE2B
+  K_FORK, K_JOIN, K_OZ_SKETCH, K_OZ_STAGE2A, K_OZ_STAGE2B,
+  // grouped emulated-FP64 kernels (param = 1: the check's Gram)
+  KG_OZ_COLHI, KG_OZ_SKETCH, KG_OZ_SKREDUCE, KG_OZ_ROWSCALE, KG_OZ_PREPR, KG_OZ_TRSM, KG_OZ_SYRK, KG_OZ_SYREDUCE,
+  KG_OZ_PREPX, KG_OZ_FINALIZE
 };
 
 constexpr int kSideStreams = 8;
@@ -68,6 +73,7 @@ struct Launch {
 struct Tuning {
   int64_t rows_per_split = 4096;
   int64_t rows_per_chunk = 8192;
+  int64_t oz_rows_per_slab = 0;   // emulated Gram and check: rows per partial (0: chosen per problem)
 };
 
 }  // namespace
@@ -90,6 +96,7 @@ struct mrcqr_batched_plan_s {
   cudaGraphExec_t exec = nullptr;
   int kernels = 0;
   bool emu = true;                    // emulated-FP64 heavy phases
+  bool oz_grouped = true;             // ... as grouped persistent launches (else per problem on side streams)
   std::vector<OzWs> oz;               // per problem (emu)
   cudaStream_t side[kSideStreams] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
@@ -121,15 +128,17 @@ void load_tune_file() {
   if (!f) return;
   std::ifstream in(f);
   std::string key;
-  int64_t a, b;
-  while (in >> key >> a >> b) g_tune_cache[key] = Tuning{a, b};
+  int64_t a, b, c;
+  while (in >> key >> a >> b >> c) g_tune_cache[key] = Tuning{a, b, c};
 }
 
 void save_tune_file() {
   const char* f = getenv("MRCQR_TUNE_CACHE");
   if (!f) return;
   std::ofstream out(f);
-  for (auto& kv : g_tune_cache) out << kv.first << " " << kv.second.rows_per_split << " " << kv.second.rows_per_chunk << "\n";
+  for (auto& kv : g_tune_cache)
+    out << kv.first << " " << kv.second.rows_per_split << " " << kv.second.rows_per_chunk << " "
+        << kv.second.oz_rows_per_slab << "\n";
 }
 
 int ladder(int p, bool escalate, int* lv) {
@@ -207,7 +216,7 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
   for (int i = 0; i < (pl.emu ? count : 0); ++i) {
     const Prob& P = pl.probs[i];
     OzWs& z = pl.oz[i];
-    z.sp = syrk_oz_plan(P.m, P.n);
+    z.sp = syrk_oz_plan(P.m, P.n, pl.tuning.oz_rows_per_slab);
     z.kp = sketch_oz_plan(P.m, P.n, P.s);
     z.seed = seeds[i];
     auto& g = ozoff[i];
@@ -264,7 +273,21 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
       }
       add(K_SKETCH, L, pr, v);
     }
-    per_problem(K_OZ_SKETCH, L, oz_sk);
+    if (pl.oz_grouped) {
+      std::vector<int4> ch, sk, rd;
+      for (int i : oz_sk) {
+        const Prob& P = pl.probs[i];
+        const OzWs& z = pl.oz[i];
+        for (int j = 0; j < (P.n + 127) / 128 * 128; ++j) ch.push_back(make_int4(i, j, 0, 0));
+        for (int t = 0; t < z.kp.mblocks * z.kp.ntiles * z.kp.slabs; ++t) sk.push_back(make_int4(i, t, 0, 0));
+        for (int b = 0; b < blocks((int64_t)P.s * P.n, 256); ++b) rd.push_back(make_int4(i, b, 0, 0));
+      }
+      add(KG_OZ_COLHI, L, 0, ch);
+      add(KG_OZ_SKETCH, L, 0, sk);
+      add(KG_OZ_SKREDUCE, L, 0, rd);
+    } else {
+      per_problem(K_OZ_SKETCH, L, oz_sk);
+    }
     std::vector<int4> red, q32, q64, tr, gr, one, ti, rm, fi;
     for (int i : live) {
       const Prob& P = pl.probs[i];
@@ -281,7 +304,27 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     add(K_SKREDUCE, L, 0, red);
     add(K_SQR, L, 0, q32);
     add(K_SQR, L, 1, q64);
-    if (pl.emu) {
+    // emulated-FP64 stage 2 work lists (grouped form)
+    std::vector<int4> z_rs, z_pr, z_tr, z_sy, z_gr, z_px, z_fi;
+    if (pl.emu && pl.oz_grouped)
+      for (int i : live) {
+        const Prob& P = pl.probs[i];
+        const OzWs& z = pl.oz[i];
+        for (int b = 0; b < blocks(P.n, 8); ++b) z_rs.push_back(make_int4(i, b, 0, 0));
+        for (int c = 0; c < (P.n + 15) / 16 * 16; ++c) z_pr.push_back(make_int4(i, c, 0, 0));
+        for (int b = 0; b < blocks(P.m, 128); ++b) z_tr.push_back(make_int4(i, b, 0, 0));
+        for (int t = 0; t < z.sp.ntiles * z.sp.slabs; ++t) z_sy.push_back(make_int4(i, t, 0, 0));
+        for (int b = 0; b < blocks((int64_t)P.n * P.n, 256); ++b) z_gr.push_back(make_int4(i, b, 0, 0));
+        for (int j = 0; j < (P.n + 63) / 64 * 64; ++j) z_px.push_back(make_int4(i, j, 0, 0));
+        for (int b = 0; b < blocks(P.m, 128); ++b) z_fi.push_back(make_int4(i, b, 0, 0));
+      }
+    if (pl.emu && pl.oz_grouped) {   // W = A R_s^{-1} (folding W's column maxima), G = W^T W
+      add(KG_OZ_ROWSCALE, L, 0, z_rs);
+      add(KG_OZ_PREPR, L, 0, z_pr);
+      add(KG_OZ_TRSM, L, 0, z_tr);
+      add(KG_OZ_SYRK, L, 0, z_sy);
+      add(KG_OZ_SYREDUCE, L, 0, z_gr);
+    } else if (pl.emu) {
       per_problem(K_OZ_STAGE2A, L, live);   // W = A R_s^{-1}, G = W^T W
     } else {
       add(K_TRSM, L, 0, tr);
@@ -301,8 +344,18 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     add(K_CHOL, L, 0, one);
     add(K_TRINV, L, 0, ti);
     add(K_RMUL, L, 0, rm);
-    if (pl.emu) per_problem(K_OZ_STAGE2B, L, live);   // Q = W R_c^{-1}, E = Q^T Q
-    else add(K_FINALIZE, L, 0, fi);
+    if (pl.emu && pl.oz_grouped) {   // Q = W R_c^{-1} (folding Q's column maxima), E = Q^T Q
+      add(KG_OZ_PREPX, L, 0, z_px);
+      add(KG_OZ_FINALIZE, L, 0, z_fi);
+      if (check) {
+        add(KG_OZ_SYRK, L, 1, z_sy);
+        add(KG_OZ_SYREDUCE, L, 1, z_gr);
+      }
+    } else if (pl.emu) {
+      per_problem(K_OZ_STAGE2B, L, live);   // Q = W R_c^{-1}, E = Q^T Q
+    } else {
+      add(K_FINALIZE, L, 0, fi);
+    }
     if (check && !pl.emu) {
       for (int tn : {16, 32, 64}) {
         std::vector<int4> v;
@@ -350,6 +403,18 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     z.trd = reinterpret_cast<unsigned char*>(base + g[3]);
     z.oze = reinterpret_cast<uint32_t*>(base + g[4]);
     z.ozx = reinterpret_cast<unsigned char*>(base + g[5]);
+  }
+  for (int i = 0; i < (int)pl.oz.size(); ++i) {
+    Prob& P = pl.probs[i];
+    const OzWs& z = pl.oz[i];
+    P.oz_sp = z.sp;
+    P.oz_kp = z.kp;
+    P.oz_colhi = z.colhi;
+    P.oz_part = z.part;
+    P.oz_cole = reinterpret_cast<int*>(z.tcole);
+    P.oz_rd = z.trd;
+    P.oz_xe = z.oze;
+    P.oz_xs = z.ozx;
   }
   pl.d_probs = reinterpret_cast<Prob*>(base + probs_off);
   pl.d_items = reinterpret_cast<int4*>(base + items_off);
@@ -416,6 +481,16 @@ void enqueue(mrcqr_batched_plan_s& pl, cudaStream_t st) {
       case K_EREDUCE: launch_g_reduce(g, true, L.level, st); break;
       case K_JUDGE: launch_g_judge(g, L.level, st); break;
       case K_PUBLISH: launch_g_publish(Group{pl.d_probs, nullptr, L.cnt}, st); break;
+      case KG_OZ_COLHI: launch_g_oz_colhi(g, L.level, st); break;
+      case KG_OZ_SKETCH: launch_g_oz_sketch(g, L.level, st); break;
+      case KG_OZ_SKREDUCE: launch_g_oz_sketch_reduce(g, L.level, st); break;
+      case KG_OZ_ROWSCALE: launch_g_oz_row_scale(g, L.level, st); break;
+      case KG_OZ_PREPR: launch_g_oz_prep_r(g, L.level, st); break;
+      case KG_OZ_TRSM: launch_g_oz_trsm(g, L.level, st); break;
+      case KG_OZ_SYRK: launch_g_oz_syrk(g, L.param == 1, L.level, st); break;
+      case KG_OZ_SYREDUCE: launch_g_oz_syrk_reduce(g, L.param == 1, L.level, st); break;
+      case KG_OZ_PREPX: launch_g_oz_prep_x(g, L.level, st); break;
+      case KG_OZ_FINALIZE: launch_g_oz_finalize(g, L.level, st); break;
     }
   }
   pl.kernels = (int)(mrcqr_launch_count() - c0);
@@ -483,6 +558,7 @@ float time_phase(mrcqr_batched_plan_s& pl, int kind, cudaStream_t st) {
     Group g{pl.d_probs, pl.d_items + L.off, L.cnt};
     if (kind == K_SYRK) launch_g_syrk(g, L.param, false, 0, st);
     if (kind == K_SKETCH) launch_g_sketch(g, L.param, 0, st);
+    if (kind == KG_OZ_SYRK && L.param == 0) launch_g_oz_syrk(g, false, 0, st);
   }
   cudaEventRecord(b, st);
   cudaEventSynchronize(b);
@@ -518,6 +594,7 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
   const double tol = (opts && opts->ortho_tol > 0) ? opts->ortho_tol : 1e-13;
   pl->use_graph = opts ? (opts->use_graph != 0) : false;
   pl->emu = opts ? (opts->fp64_products == 0) : true;
+  pl->oz_grouped = !(opts && opts->oz_per_problem);
   if (!make_streams(*pl)) {
     free_streams(*pl);
     delete pl;
@@ -536,11 +613,16 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
   const bool tune = opts && opts->autotune && !async;
   pl->async_ws = async;
   Tuning best = pl->tuning;
-  if (tune) {
-    // size the workspace for the smallest candidates (most partials)
-    pl->tuning = Tuning{1024, 2048};
-  }
   build(*pl, count, m, n, A, lda, Q, ldq, R, sketch_prec, seeds, status, check, escalate, tol, tf, &bytes);
+  if (tune) {
+    // size the workspace for the candidates with the most partials
+    for (const Tuning& t : {Tuning{1024, 2048, 4096}, Tuning{1024, 2048, 0}}) {
+      size_t b = 0;
+      pl->tuning = t;
+      build(*pl, count, m, n, A, lda, Q, ldq, R, sketch_prec, seeds, status, check, escalate, tol, tf, &b);
+      bytes = std::max(bytes, b);
+    }
+  }
   if ((async ? cudaMallocAsync(&pl->ws, bytes, st) : cudaMalloc(&pl->ws, bytes)) != cudaSuccess) {
     cudaGetLastError();
     free_streams(*pl);
@@ -568,12 +650,13 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
     return MRCQR_OK;
   };
   prepare_g_kernels(2 * 512);
+  prepare_g_oz_kernels();
   if (tune) {
     cudaStream_t ts;
     cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
     float bt = 1e30f;
     for (int64_t rps : {1024, 2048, 4096, 8192}) {
-      pl->tuning = Tuning{rps, 2048};
+      pl->tuning = Tuning{rps, 2048, 0};
       if ((rc = upload()) != MRCQR_OK) break;
       time_phase(*pl, K_SYRK, ts);   // warm
       const float t = time_phase(*pl, K_SYRK, ts);
@@ -581,11 +664,21 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
     }
     bt = 1e30f;
     for (int64_t rpc : {2048, 4096, 8192, 16384}) {
-      pl->tuning = Tuning{best.rows_per_split, rpc};
+      pl->tuning = Tuning{best.rows_per_split, rpc, 0};
       if ((rc = upload()) != MRCQR_OK) break;
       time_phase(*pl, K_SKETCH, ts);
       const float t = time_phase(*pl, K_SKETCH, ts);
       if (t < bt) { bt = t; best.rows_per_chunk = rpc; }
+    }
+    if (pl->emu && pl->oz_grouped) {   // the emulated Gram's slab height, on the grouped launch itself
+      bt = 1e30f;
+      for (int64_t rps : {0, 4096, 16384, 65536}) {
+        pl->tuning = Tuning{best.rows_per_split, best.rows_per_chunk, rps};
+        if (upload() != MRCQR_OK) continue;
+        time_phase(*pl, KG_OZ_SYRK, ts);
+        const float t = time_phase(*pl, KG_OZ_SYRK, ts);
+        if (t < bt) { bt = t; best.oz_rows_per_slab = rps; }
+      }
     }
     cudaStreamDestroy(ts);
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -10,6 +10,17 @@ namespace mrcqr {
 // before its <<<...>>>); read through mrcqr_launch_count.
 void note_launch();
 
+struct SyrkOzPlan {     // emulated-FP64 Gram: output tiles (128 x 64) and row slabs
+  int ntiles, slabs;
+  int64_t rows_per_slab;
+  int8_t ti[20], tj[20];       // I block (128 columns), J block (64 columns) of each tile
+  int8_t tile_of[4][8];        // (I, J) -> tile, -1 where no tile
+};
+struct SketchOzPlan {   // emulated-FP64 sketch: 128-column blocks of A x 64-row sample tiles x row slabs
+  int mblocks, ntiles, slabs;
+  int64_t rows_per_slab;
+};
+
 // One problem of a grouped (batched) launch: caller buffers, shape, tuned
 // split sizes and its slice of the batch workspace.
 struct Prob {
@@ -38,6 +49,15 @@ struct Prob {
   double* xt;
   double* e;
   int32_t* status;   // caller's status entry
+  // emulated-FP64 products (grouped heavy phases): plans and this problem's scratch
+  SyrkOzPlan oz_sp;
+  SketchOzPlan oz_kp;
+  uint32_t* oz_colhi;     // column maxima of A, W or Q (high words)
+  long long* oz_part;     // Gram / check / FP64-sketch partials
+  int* oz_cole;           // TRSM: column exponents of D^-1 R, then e_k (2 x n16 ints)
+  unsigned char* oz_rd;   // TRSM: digit panels of D^-1 R
+  uint32_t* oz_xe;        // finalize: column exponents of R_c^-1
+  unsigned char* oz_xs;   // finalize: digit panels of R_c^-1
 };
 
 // A grouped launch walks a list of work items {problem, a, b, c} with a
@@ -65,6 +85,24 @@ void launch_g_rmul(const Group& g, int level, cudaStream_t st);
 void launch_g_finalize(const Group& g, int level, cudaStream_t st);
 void launch_g_judge(const Group& g, int level, cudaStream_t st);
 void launch_g_publish(const Group& g, cudaStream_t st);
+// grouped emulated-FP64 heavy phases (ozaki.cu): one persistent launch per kernel over the work list
+//   colhi        items {i, column}: column maxima of A (FP64 sketch)
+//   sketch_oz    items {i, item of the problem's SketchOzPlan}   sketch_oz_reduce {i, 256-entry block}
+//   row_scale    items {i, 8-row block of R_s}                   prep_r {i, column < n16}
+//   trsm_oz      items {i, 128-row block}
+//   syrk_oz      items {i, item of the problem's SyrkOzPlan}     syrk_oz_reduce {i, 256-entry block}
+//   prep_x       items {i, column < n64}                         finalize_oz {i, 128-row block}
+void prepare_g_oz_kernels();   // kernel attributes; call outside stream capture
+void launch_g_oz_colhi(const Group& g, int level, cudaStream_t st);
+void launch_g_oz_sketch(const Group& g, int level, cudaStream_t st);
+void launch_g_oz_sketch_reduce(const Group& g, int level, cudaStream_t st);
+void launch_g_oz_row_scale(const Group& g, int level, cudaStream_t st);
+void launch_g_oz_prep_r(const Group& g, int level, cudaStream_t st);
+void launch_g_oz_trsm(const Group& g, int level, cudaStream_t st);
+void launch_g_oz_syrk(const Group& g, bool check, int level, cudaStream_t st);
+void launch_g_oz_syrk_reduce(const Group& g, bool check, int level, cudaStream_t st);
+void launch_g_oz_prep_x(const Group& g, int level, cudaStream_t st);
+void launch_g_oz_finalize(const Group& g, int level, cudaStream_t st);
 
 // --- sketch (sketch.cu) ------------------------------------------------------
 // tf: the sketch transform (T_DCT, T_RFFT, T_RFFT_REIM of common.cuh); s rows (DCT) or bins (real FFT), written
@@ -124,23 +162,14 @@ void launch_judge(int n, const double* E, int check, Ctl* ctl, int level, cudaSt
 
 // --- emulated FP64 products on tensor cores (ozaki.cu) ---------------------------
 size_t oz_xs_bytes(int n);
-struct SyrkOzPlan {     // emulated-FP64 Gram: output tiles (128 x 64) and row slabs
-  int ntiles, slabs;
-  int64_t rows_per_slab;
-  int8_t ti[20], tj[20];       // I block (128 columns), J block (64 columns) of each tile
-  int8_t tile_of[4][8];        // (I, J) -> tile, -1 where no tile
-};
-SyrkOzPlan syrk_oz_plan(int64_t m, int n);
+// rows_per_slab > 0: that slab height (a tuned value); 0: slabs chosen so tiles x slabs fills the GPU
+SyrkOzPlan syrk_oz_plan(int64_t m, int n, int64_t rows_per_slab = 0);
 size_t syrk_oz_part_bytes(const SyrkOzPlan& P);
 size_t syrk_oz_colhi_bytes(int n);
 // colHi holds the column maxima of |W| (high words); colhi_ready: the producer of W
 // (launch_trsm_oz / launch_finalize_oz given colHiOut = colHi) already wrote them.
 void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOzPlan& P, uint32_t* colHi,
                     long long* part, double* out, Ctl* ctl, int level, cudaStream_t st, bool colhi_ready = false);
-struct SketchOzPlan {   // emulated-FP64 sketch: 128-column blocks of A x 64-row sample tiles x row slabs
-  int mblocks, ntiles, slabs;
-  int64_t rows_per_slab;
-};
 SketchOzPlan sketch_oz_plan(int64_t m, int n, int s);
 size_t trsm_oz_rd_bytes(int n);
 size_t trsm_oz_cole_bytes(int n);

@@ -131,7 +131,8 @@ class BatchedPlan:
 
     def __init__(self, As, Qs, Rs, precs, seeds, status: torch.Tensor, use_graph: bool = False,
                  autotune: bool = False, check_ortho: bool = True, escalate: bool = True, tol: float = 1e-13,
-                 rows_per_split: int = 0, rows_per_chunk: int = 0, fp64_products: int = 0, transform="dct"):
+                 rows_per_split: int = 0, rows_per_chunk: int = 0, fp64_products: int = 0, transform="dct",
+                 oz_per_problem: int = 0):
         cnt = len(As)
         arr = lambda ct, vals: (ct * cnt)(*vals)
         self._keep = dict(
@@ -145,7 +146,7 @@ class BatchedPlan:
         o = _lib.BatchedOpts(use_graph=int(use_graph), autotune=int(autotune), check=int(check_ortho),
                              escalate=int(escalate), ortho_tol=tol, rows_per_split=rows_per_split,
                              rows_per_chunk=rows_per_chunk, fp64_products=int(fp64_products),
-                             transform=_transform(transform))
+                             transform=_transform(transform), oz_per_problem=int(oz_per_problem))
         self._plan = ctypes.c_void_p()
         k = self._keep
         check(_lib.load().mrcqr_batched_plan_create(cnt, k["m"], k["n"], k["pa"], k["lda"], k["pq"], k["ldq"],

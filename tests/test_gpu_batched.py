@@ -179,3 +179,35 @@ def test_batched_plan_rejects_too_few_bins(env):
     torch.cuda.synchronize()
     assert status.cpu().tolist() == [0]
     plan.close()
+
+
+def test_grouped_heavy_phases_match_per_problem_kernels(env):
+    # the emulated-FP64 heavy phases as grouped persistent launches (the default) against the same
+    # single-problem kernels run per problem on side streams: the per-item arithmetic is the same and
+    # the Gram and check sums are exact integer sums, so Q and R agree bit for bit; the grouped plan
+    # launches a fixed number of kernels per phase instead of several per problem
+    torch, M = env
+    shapes = SHAPES + [(70000, 200, 1e13), (33333, 96, 1e5)]
+    mats, kappas = _batch(shapes, seed0=2100)
+    precs = [O.precision_rule(k) for k in kappas]
+    precs[3] = "fp16"   # kappa 1e9 from FP16: escalates inside the grouped launches
+    As = [M.to_colmajor(a) for a in mats]
+    out = {}
+    for per_problem in (0, 1):
+        Qs = [M.empty_colmajor(*a.shape) for a in mats]
+        Rs = [M.empty_colmajor(a.shape[1], a.shape[1]) for a in mats]
+        status = torch.full((len(mats),), -1, dtype=torch.int32, device="cuda")
+        plan = M.BatchedPlan(As, Qs, Rs, precs, list(range(len(mats))), status, use_graph=True,
+                             oz_per_problem=per_problem)
+        plan.execute()
+        torch.cuda.synchronize()
+        assert status.cpu().tolist() == [0] * len(mats), per_problem
+        out[per_problem] = ([q.cpu().numpy() for q in Qs], [r.cpu().numpy() for r in Rs], plan.info())
+        plan.close()
+    for qg, qp, rg, rp in zip(out[0][0], out[1][0], out[0][1], out[1][1]):
+        np.testing.assert_array_equal(qg, qp)
+        np.testing.assert_array_equal(rg, rp)
+    for A, Q, R in zip(mats, out[0][0], out[0][1]):
+        assert O.orthogonality_error(Q)[0] <= 1e-13
+        assert O.residual_error(A, Q, R)[0] <= 1e-13
+    assert out[0][2]["kernels_per_execute"] < 120 < out[1][2]["kernels_per_execute"], (out[0][2], out[1][2])
