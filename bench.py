@@ -822,6 +822,27 @@ def run_kernels(args):
     torch.cuda.set_device(local)
     _build.build()
     lib = _lib.load()
+    if args.stage == "batched":   # the 512-problem batched plan (no graph, default tuning), `reps` executes
+        import numpy as np
+        rng = np.random.default_rng(4000)
+        cnt = args.count
+        ms = rng.integers(1 << 14, (1 << 18) + 1, cnt)
+        ns = rng.choice([16, 32, 64, 128], cnt)
+        kap = 10.0 ** rng.uniform(0.0, 12.0, cnt)
+        As = [inputs.make_matrix_torch(int(mm), int(nn), float(k), seed=i, device="cuda")
+              for i, (mm, nn, k) in enumerate(zip(ms, ns, kap))]
+        Qs = [M.empty_colmajor(int(mm), int(nn)) for mm, nn in zip(ms, ns)]
+        Rs = [M.empty_colmajor(int(nn), int(nn)) for nn in ns]
+        status = torch.zeros(cnt, dtype=torch.int32, device="cuda")
+        plan = M.BatchedPlan(As, Qs, Rs, [rule(k) for k in kap], list(range(cnt)), status,
+                             oz_per_problem=args.variant)
+        for _ in range(args.reps):
+            plan.execute()
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": f"batched plan, {cnt} problems, oz_per_problem={args.variant}",
+                          "plan": plan.info(), "all_ok": all(v == 0 for v in status.cpu().tolist())}), flush=True)
+        plan.close()
+        return
     m, n = args.m, args.n
     A = inputs.make_matrix_torch(m, n, args.kappa, seed=4, device="cuda")
     Q, R = M.empty_colmajor(m, n), M.empty_colmajor(n, n)
@@ -867,9 +888,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the small-factorization and batched keys")
     ap.add_argument("--workload", choices=["large", "batched", "sweep", "kernels"], default="large")
-    ap.add_argument("--stage", choices=["sketch", "factor"], default="factor", help="kernels workload: what to run")
+    ap.add_argument("--stage", choices=["sketch", "factor", "batched"], default="factor",
+                    help="kernels workload: what to run")
     ap.add_argument("--prec", default="fp16", help="kernels workload: sketch precision")
-    ap.add_argument("--variant", type=int, default=0, help="kernels workload: sketch variant (0 auto, 2 V1, 4 V2)")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="kernels workload: sketch variant (0 auto, 2 V1, 4 V2); batched stage: oz_per_problem")
     ap.add_argument("--kappa", type=float, default=1e2, help="kernels workload: condition number")
     ap.add_argument("--reps", type=int, default=2, help="kernels workload: repetitions (the last is timed)")
     ap.add_argument("--transform", choices=["dct", "rfft", "rfft_reim"], default="dct",

@@ -48,7 +48,9 @@ enum Kind {
   K_FORK, K_JOIN, K_OZ_SKETCH, K_OZ_STAGE2A, K_OZ_STAGE2B,
   // grouped emulated-FP64 kernels (param = 1: the check's Gram)
   KG_OZ_COLHI, KG_OZ_SKETCH, KG_OZ_SKREDUCE, KG_OZ_ROWSCALE, KG_OZ_PREPR, KG_OZ_TRSM, KG_OZ_SYRK, KG_OZ_SYREDUCE,
-  KG_OZ_PREPX, KG_OZ_FINALIZE
+  KG_OZ_PREPX, KG_OZ_FINALIZE, KG_OZ_ROWSCALE32, KG_OZ_PREPR32, KG_OZ_TRSM32,
+  // grouped tensor-core sketch, param = 2 precision + (MT - 1)
+  KG_TC_SKETCH
 };
 
 constexpr int kSideStreams = 8;
@@ -90,6 +92,8 @@ struct mrcqr_batched_plan_s {
   std::vector<Prob> probs;   // host copy (device pointers inside)
   std::vector<int4> items;
   std::vector<Launch> launches;
+  std::vector<unsigned char> maps;    // TMA maps of every A (slabs of 64 and 32 rows), host copy
+  size_t maps_off = 0;
   Tuning tuning;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
@@ -228,6 +232,15 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     g[5] = take(oz_xs_bytes(P.n));
   }
   const size_t probs_off = take(sizeof(Prob) * (size_t)count);
+  const size_t map_bytes = sketch_tc_map_bytes();
+  pl.maps_off = take(2 * map_bytes * (size_t)count);
+  pl.maps.assign(2 * map_bytes * (size_t)count, 0);
+  std::vector<char> tc_ok(count, 0);
+  for (int i = 0; i < count; ++i) {
+    const Prob& P = pl.probs[i];
+    tc_ok[i] = sketch_tc_encode(64, P.A, P.lda, P.m, P.n, pl.maps.data() + (2 * i) * map_bytes) &&
+               sketch_tc_encode(32, P.A, P.lda, P.m, P.n, pl.maps.data() + (2 * i + 1) * map_bytes);
+  }
   // work lists
   pl.items.clear();
   pl.launches.clear();
@@ -259,7 +272,7 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
       if (pl.probs[i].nlevels > L) live.push_back(i);
     std::vector<int> oz_sk;   // problems whose sketch at this level is the emulated FP64 one
     for (int pr = P_FP16; pr <= P_FP64; ++pr) {
-      std::vector<int4> v;
+      std::vector<int4> v, tcv[2];
       for (int i : live) {
         const Prob& P = pl.probs[i];
         if (P.lvl_prec[L] != pr) continue;
@@ -267,11 +280,21 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
           oz_sk.push_back(i);
           continue;
         }
+        if (tc_ok[i] && pr != P_FP64) {   // tensor cores: 128 or 256 sampled rows per tile
+          const int mt = P.s > 128 ? 2 : 1;
+          std::vector<int4>& t = tcv[mt - 1];
+          for (int c = 0; c < P.chunks; ++c)
+            for (int a = 0; a < blocks(P.s, 128 * mt); ++a)
+              for (int b = 0; b < blocks(P.n, 64); ++b) t.push_back(make_int4(i, c, a, b));
+          continue;
+        }
         for (int c = 0; c < P.chunks; ++c)
           for (int a = 0; a < blocks(P.s, 64); ++a)
             for (int b = 0; b < blocks(P.n, 64); ++b) v.push_back(make_int4(i, c, a, b));
       }
       add(K_SKETCH, L, pr, v);
+      add(KG_TC_SKETCH, L, 2 * pr, tcv[0]);
+      add(KG_TC_SKETCH, L, 2 * pr + 1, tcv[1]);
     }
     if (pl.oz_grouped) {
       std::vector<int4> ch, sk, rd;
@@ -305,14 +328,18 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     add(K_SQR, L, 0, q32);
     add(K_SQR, L, 1, q64);
     // emulated-FP64 stage 2 work lists (grouped form)
-    std::vector<int4> z_rs, z_pr, z_tr, z_sy, z_gr, z_px, z_fi;
+    std::vector<int4> z_rs, z_pr, z_tr, z_rs32, z_pr32, z_tr32, z_sy, z_gr, z_px, z_fi;
     if (pl.emu && pl.oz_grouped)
       for (int i : live) {
         const Prob& P = pl.probs[i];
         const OzWs& z = pl.oz[i];
-        for (int b = 0; b < blocks(P.n, 8); ++b) z_rs.push_back(make_int4(i, b, 0, 0));
-        for (int c = 0; c < (P.n + 15) / 16 * 16; ++c) z_pr.push_back(make_int4(i, c, 0, 0));
-        for (int b = 0; b < blocks(P.m, 128); ++b) z_tr.push_back(make_int4(i, b, 0, 0));
+        const bool wide = trsm_oz_wide(P.n);
+        for (int b = 0; b < blocks(P.n, 8); ++b) (wide ? z_rs32 : z_rs).push_back(make_int4(i, b, 0, 0));
+        if (wide)
+          for (int c = 0; c < (P.n + 31) / 32 * 32; ++c) z_pr32.push_back(make_int4(i, c, 0, 0));
+        else
+          for (int c = 0; c < (P.n + 15) / 16 * 16; ++c) z_pr.push_back(make_int4(i, c, 0, 0));
+        for (int b = 0; b < blocks(P.m, 128); ++b) (wide ? z_tr32 : z_tr).push_back(make_int4(i, b, 0, 0));
         for (int t = 0; t < z.sp.ntiles * z.sp.slabs; ++t) z_sy.push_back(make_int4(i, t, 0, 0));
         for (int b = 0; b < blocks((int64_t)P.n * P.n, 256); ++b) z_gr.push_back(make_int4(i, b, 0, 0));
         for (int j = 0; j < (P.n + 63) / 64 * 64; ++j) z_px.push_back(make_int4(i, j, 0, 0));
@@ -322,6 +349,9 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
       add(KG_OZ_ROWSCALE, L, 0, z_rs);
       add(KG_OZ_PREPR, L, 0, z_pr);
       add(KG_OZ_TRSM, L, 0, z_tr);
+      add(KG_OZ_ROWSCALE32, L, 0, z_rs32);
+      add(KG_OZ_PREPR32, L, 0, z_pr32);
+      add(KG_OZ_TRSM32, L, 0, z_tr32);
       add(KG_OZ_SYRK, L, 0, z_sy);
       add(KG_OZ_SYREDUCE, L, 0, z_gr);
     } else if (pl.emu) {
@@ -416,6 +446,10 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     P.oz_xe = z.oze;
     P.oz_xs = z.ozx;
   }
+  for (int i = 0; i < count; ++i) {
+    pl.probs[i].tmap64 = tc_ok[i] ? base + pl.maps_off + (2 * i) * map_bytes : nullptr;
+    pl.probs[i].tmap32 = tc_ok[i] ? base + pl.maps_off + (2 * i + 1) * map_bytes : nullptr;
+  }
   pl.d_probs = reinterpret_cast<Prob*>(base + probs_off);
   pl.d_items = reinterpret_cast<int4*>(base + items_off);
 }
@@ -487,6 +521,10 @@ void enqueue(mrcqr_batched_plan_s& pl, cudaStream_t st) {
       case KG_OZ_ROWSCALE: launch_g_oz_row_scale(g, L.level, st); break;
       case KG_OZ_PREPR: launch_g_oz_prep_r(g, L.level, st); break;
       case KG_OZ_TRSM: launch_g_oz_trsm(g, L.level, st); break;
+      case KG_OZ_ROWSCALE32: launch_g_oz_row_scale32(g, L.level, st); break;
+      case KG_OZ_PREPR32: launch_g_oz_prep_r32(g, L.level, st); break;
+      case KG_OZ_TRSM32: launch_g_oz_trsm32(g, L.level, st); break;
+      case KG_TC_SKETCH: launch_g_sketch_tc(g, L.param / 2, L.param % 2 + 1, L.level, st); break;
       case KG_OZ_SYRK: launch_g_oz_syrk(g, L.param == 1, L.level, st); break;
       case KG_OZ_SYREDUCE: launch_g_oz_syrk_reduce(g, L.param == 1, L.level, st); break;
       case KG_OZ_PREPX: launch_g_oz_prep_x(g, L.level, st); break;
@@ -558,6 +596,7 @@ float time_phase(mrcqr_batched_plan_s& pl, int kind, cudaStream_t st) {
     Group g{pl.d_probs, pl.d_items + L.off, L.cnt};
     if (kind == K_SYRK) launch_g_syrk(g, L.param, false, 0, st);
     if (kind == K_SKETCH) launch_g_sketch(g, L.param, 0, st);
+    if (kind == KG_TC_SKETCH) launch_g_sketch_tc(g, L.param / 2, L.param % 2 + 1, 0, st);
     if (kind == KG_OZ_SYRK && L.param == 0) launch_g_oz_syrk(g, false, 0, st);
   }
   cudaEventRecord(b, st);
@@ -637,6 +676,8 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
     if (async) {   // pageable sources: the copies are staged before these calls return
       if (cudaMemcpyAsync(pl->d_probs, pl->probs.data(), sizeof(Prob) * pl->probs.size(), cudaMemcpyHostToDevice,
                           st) != cudaSuccess ||
+          cudaMemcpyAsync(static_cast<char*>(pl->ws) + pl->maps_off, pl->maps.data(), pl->maps.size(),
+                          cudaMemcpyHostToDevice, st) != cudaSuccess ||
           cudaMemcpyAsync(pl->d_items, pl->items.data(), sizeof(int4) * pl->items.size(), cudaMemcpyHostToDevice,
                           st) != cudaSuccess)
         return MRCQR_ERR_CUDA;
@@ -644,6 +685,8 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
     }
     if (cudaMemcpy(pl->d_probs, pl->probs.data(), sizeof(Prob) * pl->probs.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
+        cudaMemcpy(static_cast<char*>(pl->ws) + pl->maps_off, pl->maps.data(), pl->maps.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(pl->d_items, pl->items.data(), sizeof(int4) * pl->items.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess)
       return MRCQR_ERR_CUDA;
@@ -651,6 +694,7 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
   };
   prepare_g_kernels(2 * 512);
   prepare_g_oz_kernels();
+  prepare_g_sketch_tc();
   if (tune) {
     cudaStream_t ts;
     cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
@@ -667,7 +711,8 @@ int plan_create(int count, const int64_t* m, const int64_t* n, const double* con
       pl->tuning = Tuning{best.rows_per_split, rpc, 0};
       if ((rc = upload()) != MRCQR_OK) break;
       time_phase(*pl, K_SKETCH, ts);
-      const float t = time_phase(*pl, K_SKETCH, ts);
+      time_phase(*pl, KG_TC_SKETCH, ts);
+      const float t = time_phase(*pl, K_SKETCH, ts) + time_phase(*pl, KG_TC_SKETCH, ts);
       if (t < bt) { bt = t; best.rows_per_chunk = rpc; }
     }
     if (pl->emu && pl->oz_grouped) {   // the emulated Gram's slab height, on the grouped launch itself

@@ -58,6 +58,10 @@ struct Prob {
   unsigned char* oz_rd;   // TRSM: digit panels of D^-1 R
   uint32_t* oz_xe;        // finalize: column exponents of R_c^-1
   unsigned char* oz_xs;   // finalize: digit panels of R_c^-1
+  // tensor-core sketch (grouped): TMA maps of A with slabs of 64 rows (FP16/BF16) and 32 rows (FP32);
+  // null when A is not eligible (16-byte alignment, even lda)
+  const void* tmap64;
+  const void* tmap32;
 };
 
 // A grouped launch walks a list of work items {problem, a, b, c} with a
@@ -99,6 +103,10 @@ void launch_g_oz_sketch_reduce(const Group& g, int level, cudaStream_t st);
 void launch_g_oz_row_scale(const Group& g, int level, cudaStream_t st);
 void launch_g_oz_prep_r(const Group& g, int level, cudaStream_t st);
 void launch_g_oz_trsm(const Group& g, int level, cudaStream_t st);
+// the same for problems whose W = A R_s^-1 uses 32-column update blocks (trsm_oz_wide(n))
+void launch_g_oz_row_scale32(const Group& g, int level, cudaStream_t st);
+void launch_g_oz_prep_r32(const Group& g, int level, cudaStream_t st);
+void launch_g_oz_trsm32(const Group& g, int level, cudaStream_t st);
 void launch_g_oz_syrk(const Group& g, bool check, int level, cudaStream_t st);
 void launch_g_oz_syrk_reduce(const Group& g, bool check, int level, cudaStream_t st);
 void launch_g_oz_prep_x(const Group& g, int level, cudaStream_t st);
@@ -127,6 +135,13 @@ bool launch_sketch_fs(int prec, const double* A, int64_t lda, int64_t m, int n, 
 int sketch_max_chunks(int64_t m, int n, int s);
 // tensor-core sketch (sketch_tc.cu): FP16/BF16/FP32, A 16-byte aligned, lda even
 bool sketch_tc_eligible(int prec, const double* A, int64_t lda);
+// A TMA map of A with slabs of `rows` rows and 64 columns into map_out (host memory of
+// sketch_tc_map_bytes(), 64-byte aligned); false when A is not eligible
+bool sketch_tc_encode(int rows, const double* A, int64_t lda, int64_t m, int n, void* map_out);
+size_t sketch_tc_map_bytes();
+void prepare_g_sketch_tc();   // kernel attributes; call outside stream capture
+// grouped tensor-core sketch: items {problem, chunk, sample tile of 128 mt rows, 64-column block}
+void launch_g_sketch_tc(const Group& g, int prec, int mt, int level, cudaStream_t st);
 bool launch_sketch_tc(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,
                       const double* tab, uint64_t seed, int chunks, double* Ypart, Ctl* ctl,
                       int level, cudaStream_t st, int tf = 0);
@@ -171,6 +186,8 @@ size_t syrk_oz_colhi_bytes(int n);
 void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOzPlan& P, uint32_t* colHi,
                     long long* part, double* out, Ctl* ctl, int level, cudaStream_t st, bool colhi_ready = false);
 SketchOzPlan sketch_oz_plan(int64_t m, int n, int s);
+// W = A R^{-1}: true when n uses 32-column update blocks (k_trsm_oz32), else 16-column ones (k_trsm_oz)
+bool trsm_oz_wide(int n);
 size_t trsm_oz_rd_bytes(int n);
 size_t trsm_oz_cole_bytes(int n);
 void launch_trsm_oz(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv,

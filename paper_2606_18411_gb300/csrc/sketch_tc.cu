@@ -119,40 +119,43 @@ struct Phase {
   }
 };
 
+// Shared state of one CTA of the tensor-core sketch (kept across work items).
 template <int PREC, int MT>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_sketch_tc(const __grid_constant__ CUtensorMap tmapA, int64_t m, int n, int s, const uint32_t* __restrict__ idx,
-                const double* __restrict__ tab, uint2 key, int64_t rows_per_chunk,
-                double* __restrict__ Ypart, Ctl* ctl, int level, int tf) {
+struct TcCta {
+  unsigned char* tabs;
+  unsigned char* xt;
+  double* xd;
+  uint64_t* tma_bar;
+  uint64_t* mma_bar;
+  uint32_t tmem;
+  float (*colscale)[kN];
+  uint32_t (*sgnmask)[Cfg<PREC, MT>::T];
+  uint32_t seq;   // slabs this CTA has run: drives every barrier phase and buffer index
+};
+
+// One work item: sampled rows s0 .. s0 + 128 MT - 1, columns n0 .. n0 + 63,
+// rows [j_begin, j_end) of A (TMA map tmap); the partial sums go to
+// out[col s + row].  False when a wait timed out (every thread together; this
+// CTA's copies and MMAs in flight are awaited first).
+template <int PREC, int MT>
+__device__ __forceinline__ bool sketch_tc_item(const CUtensorMap* tmap, int64_t m, int n, int s,
+                                               const uint32_t* __restrict__ idx, const double* __restrict__ tab,
+                                               uint2 key, int64_t j_begin, int64_t j_end, int s0, int n0,
+                                               double* __restrict__ out, int tf, TcCta<PREC, MT>& S) {
   using C = Cfg<PREC, MT>;
   constexpr int T = C::T;
-  if (level_inactive(ctl, level)) return;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* tabs = smem + C::TAB_OFF;
-  unsigned char* xt = smem + C::XT_OFF;
-  double* xd = reinterpret_cast<double*>(smem + C::XD_OFF);
-  __shared__ __align__(8) uint64_t tma_bar[C::STAGES];
-  __shared__ __align__(8) uint64_t mma_bar[2];
-  __shared__ uint32_t tmem_base;
-  __shared__ float colscale[2][kN];
-  __shared__ uint32_t sgnmask[2][T];
-
+  unsigned char* tabs = S.tabs;
+  unsigned char* xt = S.xt;
+  double* xd = S.xd;
+  uint64_t* tma_bar = S.tma_bar;
+  uint64_t* mma_bar = S.mma_bar;
+  const uint32_t tmem = S.tmem;
+  float(*colscale)[kN] = S.colscale;
+  uint32_t(*sgnmask)[T] = S.sgnmask;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int s0 = blockIdx.x * (kM * MT), n0 = blockIdx.y * kN;
-  const int64_t j_begin = (int64_t)blockIdx.z * rows_per_chunk;
-  const int64_t j_end = min(m, j_begin + rows_per_chunk);
   const int nslabs = j_begin < j_end ? (int)((j_end - j_begin + T - 1) / T) : 0;
   const uint64_t four_m = 4ull * (uint64_t)m;
-
-  if (warp == 0) tc::tmem_alloc(&tmem_base, C::TMEM_COLS);
-  if (tid == 0) {
-    for (int st = 0; st < C::STAGES; ++st) tc::mbar_init(&tma_bar[st], 1);
-    tc::mbar_init(&mma_bar[0], 1);
-    tc::mbar_init(&mma_bar[1], 1);
-    tc::mbar_fence_init();
-  }
+  __syncthreads();   // the previous item's MMAs and epilogue are done with the tables
   // slab-invariant transform tables: two threads per sampled row (halves of
   // t), phases dk t mod 4m advanced by additions along t
   for (int w = tid; w < 2 * kM * MT; w += kThreads) {
@@ -182,13 +185,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t tmem = tmem_base;
 
-  int issued = 0;   // TMA loads issued (thread 0)
+  int issued = 0;   // TMA loads of this item issued (thread 0)
   if (tid == 0) {
     for (int st = 0; st < C::STAGES && st < nslabs; ++st) {
-      tc::mbar_expect_tx(&tma_bar[st], C::XD_BYTES);
-      tc::tma_load_2d(xd + st * (C::XD_BYTES / 8), &tmapA, (int)(j_begin + st * T), n0, &tma_bar[st]);
+      const int sg = (int)((S.seq + (uint32_t)st) % C::STAGES);
+      tc::mbar_expect_tx(&tma_bar[sg], C::XD_BYTES);
+      tc::tma_load_2d(xd + sg * (C::XD_BYTES / 8), tmap, (int)(j_begin + st * T), n0, &tma_bar[sg]);
       ++issued;
     }
   }
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
   for (int c = 0; c < C::ACC; ++c) acc[c] = 0.f;
   bool abort = false;
-  int consumed = 0;
+  int consumed = 0, mma_issued = 0, mma_done = 0;
 
   // rotation factors cos/sin(theta_i) of slab sl, theta_i = pi r / (2m) with
   // the exact integer phase r: computed at the start of iteration sl (no
@@ -242,11 +245,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
 
   for (int sl = 0; sl < nslabs; ++sl) {
-    const int stage = sl % C::STAGES;
-    const uint32_t par = (uint32_t)((sl / C::STAGES) & 1);
-    const int buf = sl & 1;
+    const uint32_t u = S.seq + (uint32_t)sl;   // slab index over the CTA's items: stage, parity, buffer
+    const int stage = (int)(u % C::STAGES);
+    const uint32_t par = (u / C::STAGES) & 1u;
+    const int buf = (int)(u & 1u);
     const int64_t j0 = j_begin + (int64_t)sl * T;
-    prefetch_rotation(sl);
+    prefetch_rotation((int)u);
     if (tid < T) {
       const int64_t j = j0 + tid;
       sgnmask[buf][tid] = j < j_end ? (philox4x32_10(make_uint4((uint32_t)j, 0u, 0u, 0u), key).x & 1u) << 31
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
       if (issued < nslabs) {   // refill the stage just consumed
         tc::mbar_expect_tx(&tma_bar[stage], C::XD_BYTES);
-        tc::tma_load_2d(xd + stage * (C::XD_BYTES / 8), &tmapA, (int)(j_begin + (int64_t)issued * T), n0,
+        tc::tma_load_2d(xd + stage * (C::XD_BYTES / 8), tmap, (int)(j_begin + (int64_t)issued * T), n0,
                         &tma_bar[stage]);
         ++issued;
       }
@@ -326,41 +330,120 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       tc::mma_commit(&mma_bar[buf]);
+      mma_issued = sl + 1;
     }
     // the previous slab's products are read while this slab's MMAs run
     if (sl > 0) {
-      const bool ok_mma = tc::mbar_wait(&mma_bar[buf ^ 1], (uint32_t)(((sl - 1) >> 1) & 1));
+      const bool ok_mma = tc::mbar_wait(&mma_bar[buf ^ 1], ((u - 1) >> 1) & 1u);
       if (__syncthreads_or(!ok_mma)) { abort = true; break; }
+      mma_done = sl;
       tc::fence_after();
-      epilogue(sl - 1);
+      epilogue((int)(u - 1));
     }
   }
   if (!abort && nslabs > 0) {
-    const int sl = nslabs - 1;
-    const bool ok_mma = tc::mbar_wait(&mma_bar[sl & 1], (uint32_t)((sl >> 1) & 1));
+    const uint32_t u = S.seq + (uint32_t)(nslabs - 1);
+    const bool ok_mma = tc::mbar_wait(&mma_bar[u & 1u], (u >> 1) & 1u);
     if (__syncthreads_or(!ok_mma)) abort = true;
     else {
+      mma_done = nslabs;
       tc::fence_after();
-      epilogue(sl);
+      epilogue((int)u);
     }
   }
 
-  if (abort && tid == 0) {
-    // let this CTA's own copies in flight land before its shared memory goes away
-    for (int u = consumed; u < issued; ++u)
-      tc::mbar_wait(&tma_bar[u % C::STAGES], (uint32_t)((u / C::STAGES) & 1), 1u << 20);
-    raise_level_status(ctl, ST_TIMEOUT);
+  if (abort) {
+    if (tid == 0) {   // this CTA's own copies and MMAs in flight land before its shared memory and TMEM go away
+      for (int v = consumed; v < issued; ++v) {
+        const uint32_t u = S.seq + (uint32_t)v;
+        tc::mbar_wait(&tma_bar[u % C::STAGES], (u / C::STAGES) & 1u, 1u << 20);
+      }
+      for (int v = mma_done; v < mma_issued; ++v) {
+        const uint32_t u = S.seq + (uint32_t)v;
+        tc::mbar_wait(&mma_bar[u & 1u], (u >> 1) & 1u, 1u << 20);
+      }
+    }
+    return false;
   }
-  tc::fence_before();
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
-  if (abort) return;
-  double* out = Ypart + (size_t)blockIdx.z * (size_t)s * (size_t)n;
+  S.seq += (uint32_t)nslabs;
 #pragma unroll
   for (int c = 0; c < C::ACC; ++c) {
     const int col = n0 + c_lo + c;
     if (row_ok && col < n) out[(size_t)col * s + s0 + erow] = (double)acc[c];
   }
+  return true;
+}
+
+// CTA prologue of the tensor-core sketch kernels: shared memory, TMEM and
+// barriers, gathered in the TcCta named S.
+#define MRCQR_SKETCH_TC_CTA(S)                                                                        \
+  using C = Cfg<PREC, MT>;                                                                            \
+  extern __shared__ unsigned char smem_raw[];                                                         \
+  unsigned char* smem =                                                                               \
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023)); \
+  __shared__ __align__(8) uint64_t tma_bar_s[C::STAGES];                                              \
+  __shared__ __align__(8) uint64_t mma_bar_s[2];                                                      \
+  __shared__ uint32_t tmem_base;                                                                      \
+  __shared__ float colscale_s[2][kN];                                                                 \
+  __shared__ uint32_t sgnmask_s[2][C::T];                                                             \
+  if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&tmem_base, C::TMEM_COLS);                              \
+  if (threadIdx.x == 0) {                                                                             \
+    for (int st = 0; st < C::STAGES; ++st) tc::mbar_init(&tma_bar_s[st], 1);                          \
+    tc::mbar_init(&mma_bar_s[0], 1);                                                                  \
+    tc::mbar_init(&mma_bar_s[1], 1);                                                                  \
+    tc::mbar_fence_init();                                                                            \
+  }                                                                                                   \
+  tc::fence_before();                                                                                 \
+  __syncthreads();                                                                                    \
+  tc::fence_after();                                                                                  \
+  TcCta<PREC, MT> S{smem + C::TAB_OFF, smem + C::XT_OFF, reinterpret_cast<double*>(smem + C::XD_OFF), \
+                    tma_bar_s,          mma_bar_s,         tmem_base, colscale_s, sgnmask_s, 0u};
+
+template <int PREC, int MT>
+__device__ __forceinline__ void sketch_tc_cta_end(TcCta<PREC, MT>& S, bool abort, Ctl* ctl) {
+  if (abort && threadIdx.x == 0 && ctl) raise_level_status(ctl, ST_TIMEOUT);
+  tc::fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(S.tmem, Cfg<PREC, MT>::TMEM_COLS);
+}
+
+template <int PREC, int MT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sketch_tc(const __grid_constant__ CUtensorMap tmapA, int64_t m, int n, int s, const uint32_t* __restrict__ idx,
+                const double* __restrict__ tab, uint2 key, int64_t rows_per_chunk,
+                double* __restrict__ Ypart, Ctl* ctl, int level, int tf) {
+  if (level_inactive(ctl, level)) return;
+  MRCQR_SKETCH_TC_CTA(S)
+  const int64_t j_begin = (int64_t)blockIdx.z * rows_per_chunk;
+  const bool ok = sketch_tc_item<PREC, MT>(&tmapA, m, n, s, idx, tab, key, j_begin, min(m, j_begin + rows_per_chunk),
+                                           blockIdx.x * (kM * MT), blockIdx.y * kN,
+                                           Ypart + (size_t)blockIdx.z * (size_t)s * (size_t)n, tf, S);
+  sketch_tc_cta_end(S, !ok, ctl);
+}
+
+// Grouped form for batched plans: items {problem, chunk, 128 MT-row sample
+// tile, 64-column block}; each problem's TMA maps (slabs of 64 and of 32 rows)
+// sit in the plan's workspace.
+template <int PREC, int MT>
+__global__ void __launch_bounds__(kThreads, 1) kg_sketch_tc(Group g, int level) {
+  MRCQR_SKETCH_TC_CTA(S)
+  bool abort = false;
+  Ctl* actl = nullptr;
+  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+    const int4 w = g.items[it];
+    const Prob& P = g.probs[w.x];
+    if (level_inactive(P.ctl, level)) continue;
+    const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(PREC == P_FP32 ? P.tmap32 : P.tmap64);
+    const int64_t j_begin = (int64_t)w.y * P.rows_per_chunk;
+    if (!sketch_tc_item<PREC, MT>(map, P.m, P.n, P.s, P.idx, P.tab, P.key, j_begin, min(P.m, j_begin + P.rows_per_chunk),
+                                  w.z * (kM * MT), w.w * kN, P.ypart + (size_t)w.y * (size_t)P.s * (size_t)P.n, P.tf,
+                                  S)) {
+      abort = true;
+      actl = P.ctl;
+      break;
+    }
+  }
+  sketch_tc_cta_end(S, abort, actl);
 }
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -419,6 +502,43 @@ bool launch_prec(const double* A, int64_t lda, int64_t m, int n, int s, const ui
 }
 
 }  // namespace
+
+bool sketch_tc_encode(int rows, const double* A, int64_t lda, int64_t m, int n, void* map_out) {
+  EncodeFn enc = encode_fn();
+  if (!enc || (reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda & 1) != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)lda * sizeof(double)};
+  const cuuint32_t box[2] = {(cuuint32_t)rows, (cuuint32_t)kN};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(A), dims,
+             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t sketch_tc_map_bytes() { return sizeof(CUtensorMap); }
+
+void prepare_g_sketch_tc() {
+  cudaFuncSetAttribute(kg_sketch_tc<P_FP16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<P_FP16, 1>::SMEM + 1024);
+  cudaFuncSetAttribute(kg_sketch_tc<P_FP16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<P_FP16, 2>::SMEM + 1024);
+  cudaFuncSetAttribute(kg_sketch_tc<P_BF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<P_BF16, 1>::SMEM + 1024);
+  cudaFuncSetAttribute(kg_sketch_tc<P_BF16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<P_BF16, 2>::SMEM + 1024);
+  cudaFuncSetAttribute(kg_sketch_tc<P_FP32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<P_FP32, 1>::SMEM + 1024);
+  cudaFuncSetAttribute(kg_sketch_tc<P_FP32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<P_FP32, 2>::SMEM + 1024);
+}
+
+void launch_g_sketch_tc(const Group& g, int prec, int mt, int level, cudaStream_t st) {
+  if (!g.nitems) return;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)(g.nitems < sms ? g.nitems : sms);
+#define MRCQR_G_TC(PR, MTV)                                                                                \
+  { ::mrcqr::note_launch(); kg_sketch_tc<PR, MTV><<<grid, kThreads, Cfg<PR, MTV>::SMEM + 1024, st>>>(g, level); }
+  if (prec == P_FP16) { if (mt == 2) MRCQR_G_TC(P_FP16, 2) else MRCQR_G_TC(P_FP16, 1) }
+  else if (prec == P_BF16) { if (mt == 2) MRCQR_G_TC(P_BF16, 2) else MRCQR_G_TC(P_BF16, 1) }
+  else { if (mt == 2) MRCQR_G_TC(P_FP32, 2) else MRCQR_G_TC(P_FP32, 1) }
+#undef MRCQR_G_TC
+}
 
 bool sketch_tc_eligible(int prec, const double* A, int64_t lda) {
   if (prec != P_FP16 && prec != P_BF16 && prec != P_FP32) return false;
