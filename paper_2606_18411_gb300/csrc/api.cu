@@ -63,7 +63,7 @@ Plan make_plan(int64_t m, int n, int s, int tf = T_DCT) {
   p.off_xt = take(sizeof(double) * (size_t)n * p.npad);
   p.off_e = take(sizeof(double) * (size_t)n * n);
   p.off_feat = take(sizeof(float) * kNumFeatures);
-  p.off_oze = take(sizeof(uint32_t) * (size_t)((n + 63) / 64 * 64));
+  p.off_oze = take(sizeof(uint32_t) * (size_t)oz_x_cols(n));
   p.off_ozx = take(oz_xs_bytes(n));
   p.oz = syrk_oz_plan(m, n);
   p.sk = sketch_oz_plan(m, n, s);

@@ -48,7 +48,7 @@ enum Kind {
   K_FORK, K_JOIN, K_OZ_SKETCH, K_OZ_STAGE2A, K_OZ_STAGE2B,
   // grouped emulated-FP64 kernels (param = 1: the check's Gram)
   KG_OZ_COLHI, KG_OZ_SKETCH, KG_OZ_SKREDUCE, KG_OZ_ROWSCALE, KG_OZ_PREPR, KG_OZ_TRSM, KG_OZ_SYRK, KG_OZ_SYREDUCE,
-  KG_OZ_PREPX, KG_OZ_FINALIZE, KG_OZ_ROWSCALE32, KG_OZ_PREPR32, KG_OZ_TRSM32,
+  KG_OZ_PREPX, KG_OZ_FINALIZE,
   // grouped tensor-core sketch, param = 2 precision + (MT - 1)
   KG_TC_SKETCH
 };
@@ -228,18 +228,19 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     g[1] = take(std::max(syrk_oz_part_bytes(z.sp), sketch_oz_part_bytes(z.kp)));
     g[2] = take(trsm_oz_cole_bytes(P.n));
     g[3] = take(trsm_oz_rd_bytes(P.n));
-    g[4] = take(sizeof(uint32_t) * (size_t)((P.n + 63) / 64 * 64));
+    g[4] = take(sizeof(uint32_t) * (size_t)oz_x_cols(P.n));
     g[5] = take(oz_xs_bytes(P.n));
   }
   const size_t probs_off = take(sizeof(Prob) * (size_t)count);
   const size_t map_bytes = sketch_tc_map_bytes();
   pl.maps_off = take(2 * map_bytes * (size_t)count);
   pl.maps.assign(2 * map_bytes * (size_t)count, 0);
-  std::vector<char> tc_ok(count, 0);
+  std::vector<char> maps_ok(count, 0), tc_ok(count, 0);   // TMA maps of A; tensor-core sketch (maps or plain loads)
   for (int i = 0; i < count; ++i) {
     const Prob& P = pl.probs[i];
-    tc_ok[i] = sketch_tc_encode(64, P.A, P.lda, P.m, P.n, pl.maps.data() + (2 * i) * map_bytes) &&
-               sketch_tc_encode(32, P.A, P.lda, P.m, P.n, pl.maps.data() + (2 * i + 1) * map_bytes);
+    maps_ok[i] = sketch_tc_encode(64, P.A, P.lda, P.m, P.n, pl.maps.data() + (2 * i) * map_bytes) &&
+                 sketch_tc_encode(32, P.A, P.lda, P.m, P.n, pl.maps.data() + (2 * i + 1) * map_bytes);
+    tc_ok[i] = sketch_tc_eligible(P_FP16, P.A, P.lda);
   }
   // work lists
   pl.items.clear();
@@ -328,30 +329,23 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     add(K_SQR, L, 0, q32);
     add(K_SQR, L, 1, q64);
     // emulated-FP64 stage 2 work lists (grouped form)
-    std::vector<int4> z_rs, z_pr, z_tr, z_rs32, z_pr32, z_tr32, z_sy, z_gr, z_px, z_fi;
+    std::vector<int4> z_rs, z_pr, z_tr, z_sy, z_gr, z_px, z_fi;
     if (pl.emu && pl.oz_grouped)
       for (int i : live) {
         const Prob& P = pl.probs[i];
         const OzWs& z = pl.oz[i];
-        const bool wide = trsm_oz_wide(P.n);
-        for (int b = 0; b < blocks(P.n, 8); ++b) (wide ? z_rs32 : z_rs).push_back(make_int4(i, b, 0, 0));
-        if (wide)
-          for (int c = 0; c < (P.n + 31) / 32 * 32; ++c) z_pr32.push_back(make_int4(i, c, 0, 0));
-        else
-          for (int c = 0; c < (P.n + 15) / 16 * 16; ++c) z_pr.push_back(make_int4(i, c, 0, 0));
-        for (int b = 0; b < blocks(P.m, 128); ++b) (wide ? z_tr32 : z_tr).push_back(make_int4(i, b, 0, 0));
+        for (int b = 0; b < blocks(P.n, 8); ++b) z_rs.push_back(make_int4(i, b, 0, 0));
+        for (int c = 0; c < (P.n + 15) / 16 * 16; ++c) z_pr.push_back(make_int4(i, c, 0, 0));
+        for (int b = 0; b < blocks(P.m, 128); ++b) z_tr.push_back(make_int4(i, b, 0, 0));
         for (int t = 0; t < z.sp.ntiles * z.sp.slabs; ++t) z_sy.push_back(make_int4(i, t, 0, 0));
         for (int b = 0; b < blocks((int64_t)P.n * P.n, 256); ++b) z_gr.push_back(make_int4(i, b, 0, 0));
-        for (int j = 0; j < (P.n + 63) / 64 * 64; ++j) z_px.push_back(make_int4(i, j, 0, 0));
+        for (int j = 0; j < oz_x_cols(P.n); ++j) z_px.push_back(make_int4(i, j, 0, 0));
         for (int b = 0; b < blocks(P.m, 128); ++b) z_fi.push_back(make_int4(i, b, 0, 0));
       }
     if (pl.emu && pl.oz_grouped) {   // W = A R_s^{-1} (folding W's column maxima), G = W^T W
       add(KG_OZ_ROWSCALE, L, 0, z_rs);
       add(KG_OZ_PREPR, L, 0, z_pr);
       add(KG_OZ_TRSM, L, 0, z_tr);
-      add(KG_OZ_ROWSCALE32, L, 0, z_rs32);
-      add(KG_OZ_PREPR32, L, 0, z_pr32);
-      add(KG_OZ_TRSM32, L, 0, z_tr32);
       add(KG_OZ_SYRK, L, 0, z_sy);
       add(KG_OZ_SYREDUCE, L, 0, z_gr);
     } else if (pl.emu) {
@@ -447,8 +441,8 @@ void build(mrcqr_batched_plan_s& pl, int count, const int64_t* m, const int64_t*
     P.oz_xs = z.ozx;
   }
   for (int i = 0; i < count; ++i) {
-    pl.probs[i].tmap64 = tc_ok[i] ? base + pl.maps_off + (2 * i) * map_bytes : nullptr;
-    pl.probs[i].tmap32 = tc_ok[i] ? base + pl.maps_off + (2 * i + 1) * map_bytes : nullptr;
+    pl.probs[i].tmap64 = maps_ok[i] ? base + pl.maps_off + (2 * i) * map_bytes : nullptr;
+    pl.probs[i].tmap32 = maps_ok[i] ? base + pl.maps_off + (2 * i + 1) * map_bytes : nullptr;
   }
   pl.d_probs = reinterpret_cast<Prob*>(base + probs_off);
   pl.d_items = reinterpret_cast<int4*>(base + items_off);
@@ -521,9 +515,6 @@ void enqueue(mrcqr_batched_plan_s& pl, cudaStream_t st) {
       case KG_OZ_ROWSCALE: launch_g_oz_row_scale(g, L.level, st); break;
       case KG_OZ_PREPR: launch_g_oz_prep_r(g, L.level, st); break;
       case KG_OZ_TRSM: launch_g_oz_trsm(g, L.level, st); break;
-      case KG_OZ_ROWSCALE32: launch_g_oz_row_scale32(g, L.level, st); break;
-      case KG_OZ_PREPR32: launch_g_oz_prep_r32(g, L.level, st); break;
-      case KG_OZ_TRSM32: launch_g_oz_trsm32(g, L.level, st); break;
       case KG_TC_SKETCH: launch_g_sketch_tc(g, L.param / 2, L.param % 2 + 1, L.level, st); break;
       case KG_OZ_SYRK: launch_g_oz_syrk(g, L.param == 1, L.level, st); break;
       case KG_OZ_SYREDUCE: launch_g_oz_syrk_reduce(g, L.param == 1, L.level, st); break;

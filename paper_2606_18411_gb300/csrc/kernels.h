@@ -103,10 +103,6 @@ void launch_g_oz_sketch_reduce(const Group& g, int level, cudaStream_t st);
 void launch_g_oz_row_scale(const Group& g, int level, cudaStream_t st);
 void launch_g_oz_prep_r(const Group& g, int level, cudaStream_t st);
 void launch_g_oz_trsm(const Group& g, int level, cudaStream_t st);
-// the same for problems whose W = A R_s^-1 uses 32-column update blocks (trsm_oz_wide(n))
-void launch_g_oz_row_scale32(const Group& g, int level, cudaStream_t st);
-void launch_g_oz_prep_r32(const Group& g, int level, cudaStream_t st);
-void launch_g_oz_trsm32(const Group& g, int level, cudaStream_t st);
 void launch_g_oz_syrk(const Group& g, bool check, int level, cudaStream_t st);
 void launch_g_oz_syrk_reduce(const Group& g, bool check, int level, cudaStream_t st);
 void launch_g_oz_prep_x(const Group& g, int level, cudaStream_t st);
@@ -186,9 +182,10 @@ size_t syrk_oz_colhi_bytes(int n);
 void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOzPlan& P, uint32_t* colHi,
                     long long* part, double* out, Ctl* ctl, int level, cudaStream_t st, bool colhi_ready = false);
 SketchOzPlan sketch_oz_plan(int64_t m, int n, int s);
-// W = A R^{-1}: true when n uses 32-column update blocks (k_trsm_oz32), else 16-column ones (k_trsm_oz)
-bool trsm_oz_wide(int n);
+// W = A R^{-1} (k_trsm_oz, 16-column blocks): workspace of the R digit panels and exponents
 size_t trsm_oz_rd_bytes(int n);
+// columns of the finalize's X digits and exponents (n padded to its tile width)
+int oz_x_cols(int n);
 size_t trsm_oz_cole_bytes(int n);
 void launch_trsm_oz(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv,
                     uint32_t* colE, unsigned char* Rd, double* W, int64_t ldw, Ctl* ctl, int level, cudaStream_t st,

@@ -1093,452 +1093,6 @@ __global__ void __launch_bounds__(kTThreads, 2)
 
 
 // ---------------------------------------------------------------------------
-// W = A R^{-1} with 32-column update blocks.  For block J (columns
-// c0 = 32 J .. c0 + 31):
-//   B_J = A_J - W_{<c0} (D^-1 R)_{<c0, J}   one emulated product of N = 32
-//                                           (K chunks of 32 re-sliced once per
-//                                           32 columns instead of once per 16);
-//   W_J0 = B_J0 R_{J0 J0}^{-1}              FP64 substitution, 16 x 16 block;
-//   B_J1 -= W_J0 (D^-1 R)_{J0, J1}          one emulated product of K = 16,
-//                                           sliced from the fresh W_J0 in the
-//                                           substituting threads;
-//   W_J1 = B_J1 R_{J1 J1}^{-1}              FP64 substitution.
-// The digit stacking (B digits 0 .. 7 - a along N) gives MMAs of
-// N = 32 (8 - a) <= 256 for the update and 16 (8 - a) for the intra-block
-// product.  TMEM holds the 8 levels x 32 columns (256 columns), so two CTAs
-// share an SM and one's substitution overlaps the other's updates.  Every
-// product is the same exact-digit evaluation as in k_trsm_oz, with its own
-// row reference exponent and one rounding; W D is sliced against the running
-// row maxima of W D.
-constexpr int kT2B = 32;                              // update block width
-constexpr uint32_t kT2BPanel = kT2B * 64;            // one digit, 32 rows x 32 K (2 KiB)
-constexpr uint32_t kT2IPanel = kTB * 64;             // one digit, 16 rows x 32 K (1 KiB)
-constexpr size_t kT2Smem = (size_t)oz::kSlices * (kTAPanel + kT2BPanel) + sizeof(double) * kM * kTB + 1024;
-
-// Digits of D^-1 R for the 32-column blocks.  Column c (of 32 ceil(n / 32)),
-// block J = c / 32:
-//   update panels (J, kc), kc < J: rows k in [32 kc, 32 kc + 32) of R 2^-e_k,
-//     against colE[c] = the largest exponent of R[k][c] 2^-e_k over k < 32 J;
-//   for the second half of a block (c % 32 >= 16), the intra panel J: rows
-//     k in [32 J, 32 J + 16) against colEi[c] = the largest exponent over them.
-// 2047 marks a non-finite entry among those used.
-__device__ __forceinline__ void oz_prep_r32_col(int n, int npad, int nkc, const double* __restrict__ RT,
-                                                const int* __restrict__ eR, int* __restrict__ colE,
-                                                int* __restrict__ colEi, unsigned char* __restrict__ Rd,
-                                                unsigned char* __restrict__ Ri, uint32_t* __restrict__ colHiOut,
-                                                int nhi, int c, int* red, int* bad) {
-  if (colHiOut && c == 0)     // the TRSM folds the column maxima of W into these
-    for (int i = threadIdx.x; i < nhi; i += blockDim.x) colHiOut[i] = 0u;
-  const int J = c / kT2B, kend = kT2B * J;
-  const bool second = (c % kT2B) >= kTB;
-  auto col_exponent = [&](int k0, int k1, int* out) {   // max exponent of R[k][c] 2^-e_k over [k0, k1)
-    int mx = -100000, nf = 0;
-    for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x)
-      if (c < n) {
-        const int E = (int)oz::exp_field((uint32_t)__double2hiint(RT[(int64_t)k * npad + c]));
-        if (E == 2047) nf = 1;
-        else if (E != 0) mx = max(mx, E - eR[k]);
-      }
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    nf = __reduce_or_sync(0xffffffffu, nf);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) {
-      red[threadIdx.x >> 5] = mx;
-      bad[threadIdx.x >> 5] = nf;
-    }
-    __syncthreads();
-    int E = red[0], anybad = bad[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      E = max(E, red[w]);
-      anybad |= bad[w];
-    }
-    if (E == -100000) E = 0;   // no nonzero entry: every digit is zero
-    E = anybad ? 2047 : E;
-    if (threadIdx.x == 0) *out = E;
-    return E;
-  };
-  const int E = col_exponent(0, kend, colE + c);
-  for (int k = threadIdx.x; k < kend; k += blockDim.x) {
-    int d[oz::kSlices];
-    const double x = c < n ? RT[(int64_t)k * npad + c] : 0.0;
-    oz::digits8((uint32_t)__double2hiint(x), (uint32_t)__double2loint(x), E, d, -eR[k]);
-    unsigned char* panel = Rd + (size_t)(J * nkc + k / kK) * oz::kSlices * kT2BPanel;
-#pragma unroll
-    for (int b = 0; b < oz::kSlices; ++b)
-      *reinterpret_cast<__half*>(panel + b * kT2BPanel + tc::sw64_offset(c % kT2B, k % kK, 2)) =
-          __float2half_rn(oz::small_int_to_float(d[b]));
-  }
-  if (second) {
-    const int k0 = kend, k1 = min(kend + kTB, n);
-    const int Ei = col_exponent(k0, k1, colEi + c);
-    for (int k = k0 + (int)threadIdx.x; k < kend + kTB; k += blockDim.x) {
-      int d[oz::kSlices];
-      const double x = (c < n && k < n) ? RT[(int64_t)k * npad + c] : 0.0;
-      oz::digits8((uint32_t)__double2hiint(x), (uint32_t)__double2loint(x), Ei, d, k < n ? -eR[k] : 0);
-      unsigned char* panel = Ri + (size_t)J * oz::kSlices * kT2IPanel;
-#pragma unroll
-      for (int b = 0; b < oz::kSlices; ++b)
-        *reinterpret_cast<__half*>(panel + b * kT2IPanel + tc::sw64_offset(c % kTB, k - k0, 2)) =
-            __float2half_rn(oz::small_int_to_float(d[b]));
-    }
-  }
-}
-
-__global__ void __launch_bounds__(256) k_oz_prep_r32(int n, int npad, int nkc, const double* __restrict__ RT,
-                                                     const int* __restrict__ eR, int* __restrict__ colE,
-                                                     int* __restrict__ colEi, unsigned char* __restrict__ Rd,
-                                                     unsigned char* __restrict__ Ri, uint32_t* __restrict__ colHiOut,
-                                                     int nhi, const Ctl* ctl, int level) {
-  if (ctl && (level_inactive(ctl, level) || ctl->lvl_status != 0)) return;
-  __shared__ int red[8];
-  __shared__ int bad[8];
-  oz_prep_r32_col(n, npad, nkc, RT, eR, colE, colEi, Rd, Ri, colHiOut, nhi, blockIdx.x, red, bad);
-}
-
-struct Trsm32Args {
-  int64_t m;
-  int n;
-  const double* A;
-  int64_t lda;
-  const double* RT;
-  const double* rinv;
-  const int* eR;
-  const int* colE;        // update-panel column exponents
-  const int* colEi;       // intra-panel column exponents
-  const unsigned char* Rd;
-  const unsigned char* Ri;
-  int nkc;
-  double* W;
-  int64_t ldw;
-  uint32_t* colHiOut;
-  Ctl* ctl;
-};
-
-struct Trsm32Cta {
-  unsigned char* as;     // 8 digit panels of W, 128 rows x 32 K
-  unsigned char* bs;     // 8 digit panels of D^-1 R, 32 (update) or 16 (intra) rows x 32 K
-  double* Bblk;          // [16][128] right-hand sides of a diagonal block
-  uint64_t* bar;
-  uint32_t tmem;
-  uint32_t commits;
-  int* rowX;             // running max exponent of W D per row (kNonfinite: a non-finite entry)
-  int* rowXi;            // exponent reference of the intra-block product per row
-  int* eRs;
-  double (*Rd16)[kTB + 1];
-  double* rinv16;
-  uint32_t* cmax;
-};
-
-__device__ __forceinline__ void trsm32_begin(const Trsm32Args& a, Trsm32Cta& S) {
-  __syncthreads();
-  for (int k = threadIdx.x; k < a.n; k += kTThreads) {
-    S.eRs[k] = a.eR[k];
-    S.cmax[k] = 0u;
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void trsm32_end(const Trsm32Args& a, Trsm32Cta& S) {
-  __syncthreads();
-  if (a.colHiOut)
-    for (int k = threadIdx.x; k < a.n; k += kTThreads)
-      if (S.cmax[k]) atomicMax(a.colHiOut + k, S.cmax[k]);
-  __syncthreads();
-}
-
-// Diagonal block at columns c1 .. c1 + 15 into shared memory (all threads).
-__device__ __forceinline__ void trsm32_diag(const Trsm32Args& a, Trsm32Cta& S, int c1) {
-  const int npad = (a.n + 31) / 32 * 32;
-  const int tid = threadIdx.x, r = tid / kTB, b = tid % kTB;   // 256 threads = 16 x 16
-  S.Rd16[r][b] = (c1 + r < a.n && c1 + b < a.n) ? a.RT[(int64_t)(c1 + r) * npad + c1 + b] : 0.0;
-  if (tid < kTB) S.rinv16[tid] = a.rinv[c1 + tid];
-}
-
-// FP64 substitution of the 16 columns at c1 for this thread's row (tid < 128),
-// right-hand sides in Bblk; writes W, folds rowX and the column maxima.  With
-// intra, also slices the 16 results (times 2^e_k) into the A digit panels as
-// K = 0 .. 15 of the intra-block product, against their own row maximum.
-__device__ __forceinline__ void trsm32_subst(const Trsm32Args& a, Trsm32Cta& S, int64_t r0, int c1, bool intra) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  double t[kTB];
-#pragma unroll
-  for (int c = 0; c < kTB; ++c) t[c] = S.Bblk[c * kM + tid];
-  int mx = S.rowX[tid];
-#pragma unroll
-  for (int c = 0; c < kTB; ++c) {
-    t[c] *= S.rinv16[c];
-#pragma unroll
-    for (int c2 = c + 1; c2 < kTB; ++c2) t[c2] = fma(-t[c], S.Rd16[c][c2], t[c2]);
-  }
-  const bool live = r0 + tid < a.m;
-  int mi = kNoEntry;
-#pragma unroll
-  for (int c = 0; c < kTB; ++c)
-    if (c1 + c < a.n) {
-      const int E = (int)oz::exp_field((uint32_t)__double2hiint(t[c]));
-      if (live) a.W[r0 + tid + (int64_t)(c1 + c) * a.ldw] = t[c];
-      if (E == 2047) {
-        mx = kNonfinite;
-        mi = kNonfinite;
-      } else if (E != 0) {
-        if (mx != kNonfinite) mx = max(mx, E + S.eRs[c1 + c]);
-        if (mi != kNonfinite) mi = max(mi, E + S.eRs[c1 + c]);
-      }
-    }
-  S.rowX[tid] = live ? mx : S.rowX[tid];
-  if (a.colHiOut) {   // lane c keeps the warp's maximum of column c1 + c
-    uint32_t mine = 0u;
-#pragma unroll
-    for (int c = 0; c < kTB; ++c) {
-      const uint32_t h = (live && c1 + c < a.n) ? ((uint32_t)__double2hiint(t[c]) & 0x7FFFFFFFu) : 0u;
-      const uint32_t wm = __reduce_max_sync(0xffffffffu, h);
-      if (lane == c) mine = wm;
-    }
-    if (mine) atomicMax(&S.cmax[c1 + lane], mine);
-  }
-  if (intra) {
-    S.rowXi[tid] = live ? mi : kNoEntry;
-    const int Ei = (mi == kNoEntry || mi == kNonfinite) ? 0 : mi;
-#pragma unroll
-    for (int c = 0; c < kTB; c += 2) {
-      const bool ok0 = live && c1 + c < a.n, ok1 = live && c1 + c + 1 < a.n;
-      oz_store_pair(ok0 ? t[c] : 0.0, ok1 ? t[c + 1] : 0.0, 0u, 0u, Ei, S.as + tc::sw64_offset(tid, c, 2), kTAPanel,
-                    c1 + c < a.n ? S.eRs[c1 + c] : 0, c1 + c + 1 < a.n ? S.eRs[c1 + c + 1] : 0);
-    }
-  }
-}
-
-__device__ __forceinline__ bool trsm32_block(const Trsm32Args& a, Trsm32Cta& S, int64_t r0) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int q = warp & 3, g = warp >> 2;   // readout: lanes 32 q .., columns 16 g .. 16 g + 15
-  const int rr = q * 32 + lane;
-  const bool rlive = r0 + rr < a.m;
-  const int pr = tid & (kM - 1), ph = tid >> 7;   // producer role: row pr, 16-byte chunks 2 ph, 2 ph + 1
-  const int lg = lane >> 3;
-  auto pair_of = [&](int i) { return 4 * (2 * ph + (i & 1)) + ((lg + (i >> 1)) & 3); };
-  const int nblk = (a.n + kT2B - 1) / kT2B;
-  if (tid < kM) S.rowX[tid] = kNoEntry;
-  __syncthreads();
-  for (int J = 0; J < nblk; ++J) {
-    const int c0 = J * kT2B;
-    // B_J = A_J - W_{<c0} (D^-1 R)_{<c0, J}: thread (q, g) holds row rr, columns c0 + 16 g + c
-    double bv[kTB];
-    if (J == 0) {
-#pragma unroll
-      for (int c = 0; c < kTB; ++c) {
-        const int col = c0 + kTB * g + c;
-        bv[c] = (rlive && col < a.n) ? a.A[r0 + rr + (int64_t)col * a.lda] : 0.0;
-      }
-    } else {
-      long long hi[kTB], lo[kTB];
-#pragma unroll
-      for (int c = 0; c < kTB; ++c) hi[c] = lo[c] = 0;
-      const bool plive = r0 + pr < a.m;
-      const int Er = S.rowX[pr];
-      for (int kc = 0; kc < J; ++kc) {
-        // R digits of (J, kc): 16 KiB, four asynchronous 16-byte copies per thread
-        const uint4* src = reinterpret_cast<const uint4*>(a.Rd + (size_t)(J * a.nkc + kc) * oz::kSlices * kT2BPanel);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) tc::cp_async16(S.bs + 16 * (tid + kTThreads * i), src + tid + kTThreads * i);
-#pragma unroll
-        for (int h = 0; h < 8; h += 4) {   // two halves of four column pairs (register pressure)
-          double v[4][2];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int k0 = kc * kK + 2 * pair_of(h + i);   // < c0 <= n
-            v[i][0] = plive ? a.W[r0 + pr + (int64_t)k0 * a.ldw] : 0.0;
-            v[i][1] = plive ? a.W[r0 + pr + (int64_t)(k0 + 1) * a.ldw] : 0.0;
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int k0 = kc * kK + 2 * pair_of(h + i);
-            oz_store_pair(v[i][0], v[i][1], 0u, 0u, Er, S.as + tc::sw64_offset(pr, 2 * pair_of(h + i), 2),
-                          kTAPanel, S.eRs[k0], S.eRs[k0 + 1]);
-          }
-        }
-        tc::cp_async_wait_all();
-        tc::fence_proxy_async();
-        tc::fence_before();
-        __syncthreads();
-        if (tid == 0) {
-          tc::fence_after();
-          const uint64_t da = tc::sw64_desc(tc::smem_u32(S.as)), db = tc::sw64_desc(tc::smem_u32(S.bs));
-          const uint32_t first = (kc % kGroupChunks) == 0 ? 0u : 1u;
-          // one MMA per A digit against the stacked R digits 0 .. 7 - a (N = 32 (8 - a))
-#pragma unroll
-          for (int kk = 0; kk < kK; kk += 16)
-#pragma unroll
-            for (int d = 0; d < oz::kLevels; ++d)
-              tc::mma_f16(S.tmem + (uint32_t)(d * kT2B), da + (uint64_t)((d * kTAPanel + kk * 2) >> 4),
-                          db + (uint64_t)((kk * 2) >> 4), tc::idesc(tc::F16, kM, kT2B * (oz::kLevels - d)),
-                          (d == 0 && kk == 0) ? first : 1u);
-          tc::mma_commit(S.bar);
-        }
-        const bool ok = tc::mbar_wait(S.bar, S.commits & 1u);
-        ++S.commits;
-        if (__syncthreads_or(!ok)) return false;
-        tc::fence_after();
-        if (kc % kGroupChunks == kGroupChunks - 1 || kc == J - 1) {
-          const uint32_t base = S.tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * kTB);
-#pragma unroll 1
-          for (int L = 0; L < oz::kLevels; ++L) {
-            float f[kTB];
-            tc::tmem_ld16(base + (uint32_t)(L * kT2B), f);
-            tc::tmem_wait_ld();
-#pragma unroll
-            for (int c = 0; c < kTB; ++c) oz::add_level(L, f[c], hi[c], lo[c]);
-          }
-        }
-        tc::fence_before();
-        __syncthreads();   // panels and accumulators free for the next chunk
-      }
-      const int Erow = S.rowX[rr];
-#pragma unroll
-      for (int c = 0; c < kTB; ++c) {
-        const int col = c0 + kTB * g + c;
-        bv[c] = 0.0;
-        if (col < a.n) {
-          const int ce = a.colE[col];
-          const double p = (Erow == kNonfinite || ce == 2047)
-                               ? nan64()
-                               : oz::i128_to_double(hi[c], lo[c], Erow + ce - oz::kScaleBias);
-          bv[c] = (rlive ? a.A[r0 + rr + (int64_t)col * a.lda] : 0.0) - p;
-        }
-      }
-    }
-    // first half: right-hand sides from the g = 0 warps, diagonal block, substitution
-    if (g == 0) {
-#pragma unroll
-      for (int c = 0; c < kTB; ++c) S.Bblk[c * kM + rr] = bv[c];
-    }
-    trsm32_diag(a, S, c0);
-    const bool second = c0 + kTB < a.n;
-    __syncthreads();
-    if (tid < kM) trsm32_subst(a, S, r0, c0, second);
-    if (!second) {
-      __syncthreads();
-      break;
-    }
-    // intra-block product B_J1 -= W_J0 (D^-1 R)_{J0, J1}: R digits of panel J (8 KiB)
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(a.Ri + (size_t)J * oz::kSlices * kT2IPanel);
-#pragma unroll
-      for (int i = 0; i < 2; ++i) tc::cp_async16(S.bs + 16 * (tid + kTThreads * i), src + tid + kTThreads * i);
-    }
-    tc::cp_async_wait_all();
-    tc::fence_proxy_async();
-    tc::fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      const uint64_t da = tc::sw64_desc(tc::smem_u32(S.as)), db = tc::sw64_desc(tc::smem_u32(S.bs));
-#pragma unroll
-      for (int d = 0; d < oz::kLevels; ++d)   // K = 16: one K step
-        tc::mma_f16(S.tmem + (uint32_t)(d * kTB), da + (uint64_t)((d * kTAPanel) >> 4), db,
-                    tc::idesc(tc::F16, kM, kTB * (oz::kLevels - d)), d == 0 ? 0u : 1u);
-      tc::mma_commit(S.bar);
-    }
-    {
-      const bool ok = tc::mbar_wait(S.bar, S.commits & 1u);
-      ++S.commits;
-      if (__syncthreads_or(!ok)) return false;
-    }
-    tc::fence_after();
-    if (g == 1) {   // these warps hold B_J1: subtract the intra-block product, stage for the substitution
-      long long hi[kTB], lo[kTB];
-#pragma unroll
-      for (int c = 0; c < kTB; ++c) hi[c] = lo[c] = 0;
-      const uint32_t base = S.tmem + ((uint32_t)(q * 32) << 16);
-#pragma unroll 1
-      for (int L = 0; L < oz::kLevels; ++L) {
-        float f[kTB];
-        tc::tmem_ld16(base + (uint32_t)(L * kTB), f);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int c = 0; c < kTB; ++c) oz::add_level(L, f[c], hi[c], lo[c]);
-      }
-      const int Ei = S.rowXi[rr];
-#pragma unroll
-      for (int c = 0; c < kTB; ++c) {
-        const int col = c0 + kTB + c;
-        if (col < a.n && Ei != kNoEntry) {
-          const int ce = a.colEi[col];
-          const double p = (Ei == kNonfinite || ce == 2047)
-                               ? nan64()
-                               : oz::i128_to_double(hi[c], lo[c], Ei + ce - oz::kScaleBias);
-          bv[c] -= p;
-        }
-        S.Bblk[c * kM + rr] = bv[c];
-      }
-    }
-    tc::fence_before();
-    __syncthreads();
-    trsm32_diag(a, S, c0 + kTB);
-    __syncthreads();
-    if (tid < kM) trsm32_subst(a, S, r0, c0 + kTB, false);
-    __syncthreads();
-  }
-  return true;
-}
-
-#define MRCQR_TRSM32_CTA(S)                                                    \
-  extern __shared__ unsigned char smem_raw[];                                  \
-  unsigned char* smem = oz_smem(smem_raw);                                     \
-  __shared__ __align__(8) uint64_t mma_bar;                                    \
-  __shared__ uint32_t tmem_slot;                                               \
-  __shared__ int rowX_s[kM];                                                   \
-  __shared__ int rowXi_s[kM];                                                  \
-  __shared__ int eRs_s[512];                                                   \
-  __shared__ double Rd16_s[kTB][kTB + 1];                                      \
-  __shared__ double rinv16_s[kTB];                                             \
-  __shared__ uint32_t cmax_s[512];                                             \
-  if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&tmem_slot, 256);                \
-  if (threadIdx.x == 0) {                                                      \
-    tc::mbar_init(&mma_bar, 1);                                                \
-    tc::mbar_fence_init();                                                     \
-  }                                                                            \
-  tc::fence_before();                                                          \
-  __syncthreads();                                                             \
-  tc::fence_after();                                                           \
-  Trsm32Cta S;                                                                 \
-  S.as = smem;                                                                 \
-  S.bs = smem + oz::kSlices * kTAPanel;                                        \
-  S.Bblk = reinterpret_cast<double*>(S.bs + oz::kSlices * kT2BPanel);          \
-  S.bar = &mma_bar;                                                            \
-  S.tmem = tmem_slot;                                                          \
-  S.commits = 0;                                                               \
-  S.rowX = rowX_s;                                                             \
-  S.rowXi = rowXi_s;                                                           \
-  S.eRs = eRs_s;                                                               \
-  S.Rd16 = Rd16_s;                                                             \
-  S.rinv16 = rinv16_s;                                                         \
-  S.cmax = cmax_s;
-
-__device__ __forceinline__ void trsm32_cta_end(Trsm32Cta& S, bool abort, Ctl* ctl) {
-  if (abort && threadIdx.x == 0 && ctl) raise_level_status(ctl, ST_TIMEOUT);
-  tc::fence_before();
-  __syncthreads();
-  if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(S.tmem, 256);
-}
-
-__global__ void __launch_bounds__(kTThreads, 2)
-    k_trsm_oz32(Trsm32Args a, int level) {
-  if (level_inactive(a.ctl, level) || a.ctl->lvl_status != 0) return;
-  MRCQR_TRSM32_CTA(S)
-  trsm32_begin(a, S);
-  bool abort = false;
-  const int64_t nblocks = (a.m + kM - 1) / kM;
-  for (int64_t rb = blockIdx.x; rb < nblocks; rb += gridDim.x)
-    if (!trsm32_block(a, S, rb * kM)) {
-      abort = true;
-      break;
-    }
-  if (!abort) trsm32_end(a, S);
-  trsm32_cta_end(S, abort, a.ctl);
-}
-
-
-// ---------------------------------------------------------------------------
 // Grouped forms for batched plans (many problems of uneven m and n): one
 // persistent launch per kernel walks a work list of {problem, block} items
 // with a grid-stride loop; an item whose problem is not active at this
@@ -1668,64 +1222,6 @@ __global__ void __launch_bounds__(kTThreads, 2) kg_oz_trsm(Group g, int level) {
   trsm_oz_cta_end(S, abort, actl);
 }
 
-// The 32-column-block TRSM: P.oz_cole holds colE (n32), colEi (n32), e_k (n32);
-// P.oz_rd the update panels followed by the intra panels.
-__device__ __forceinline__ Trsm32Args trsm32_args_of(const Prob& P) {
-  const int n32 = (P.n + kT2B - 1) / kT2B * kT2B, nkc = (P.n + kK - 1) / kK;
-  return Trsm32Args{P.m, P.n, P.A, P.lda, P.rst, P.rinv, P.oz_cole + 2 * n32, P.oz_cole, P.oz_cole + n32, P.oz_rd,
-                    P.oz_rd + (size_t)(n32 / kT2B) * nkc * oz::kSlices * kT2BPanel, nkc, P.Q, P.ldq, P.oz_colhi, P.ctl};
-}
-
-__global__ void __launch_bounds__(256) kg_oz_row_scale32(Group g, int level) {
-  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
-    const int4 w = g.items[it];
-    const Prob& P = g.probs[w.x];
-    if (!oz_live(P, level)) continue;
-    oz_row_scale_block(P.n, P.npad, P.rst, P.oz_cole + 2 * ((P.n + kT2B - 1) / kT2B * kT2B), w.y);
-  }
-}
-
-__global__ void __launch_bounds__(256) kg_oz_prep_r32(Group g, int level) {
-  __shared__ int red[8];
-  __shared__ int bad[8];
-  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
-    const int4 w = g.items[it];
-    const Prob& P = g.probs[w.x];
-    if (!oz_live(P, level)) continue;
-    const Trsm32Args a = trsm32_args_of(P);
-    oz_prep_r32_col(P.n, P.npad, a.nkc, P.rst, a.eR, const_cast<int*>(a.colE), const_cast<int*>(a.colEi),
-                    const_cast<unsigned char*>(a.Rd), const_cast<unsigned char*>(a.Ri), P.oz_colhi, oz_nhi(P.n),
-                    w.y, red, bad);
-  }
-}
-
-__global__ void __launch_bounds__(kTThreads, 2) kg_oz_trsm32(Group g, int level) {
-  MRCQR_TRSM32_CTA(S)
-  __shared__ Trsm32Args a;   // the current problem's arguments (shared: not held in registers)
-  bool abort = false;
-  int cur = -1;
-  Ctl* actl = nullptr;
-  for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
-    const int4 w = g.items[it];
-    const Prob& P = g.probs[w.x];
-    if (!oz_live(P, level)) continue;
-    if (w.x != cur) {
-      if (cur >= 0) trsm32_end(a, S);
-      __syncthreads();
-      if (threadIdx.x == 0) a = trsm32_args_of(P);
-      trsm32_begin(a, S);
-      cur = w.x;
-    }
-    if (!trsm32_block(a, S, (int64_t)w.y * kM)) {
-      abort = true;
-      actl = P.ctl;
-      break;
-    }
-  }
-  if (!abort && cur >= 0) trsm32_end(a, S);
-  trsm32_cta_end(S, abort, actl);
-}
-
 __global__ void __launch_bounds__(kOzThreads, 1) kg_oz_syrk(Group g, int level) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = oz_smem(smem_raw);
@@ -1840,8 +1336,10 @@ void set_smem(K kernel) {
 
 }  // namespace
 
+int oz_x_cols(int n) { return (n + kN - 1) / kN * kN; }
+
 size_t oz_xs_bytes(int n) {
-  const int n64 = (n + kN - 1) / kN * kN;
+  const int n64 = oz_x_cols(n);
   return (size_t)oz::kSlices * (n64 / kN) * (n64 / kK) * kBPanel;
 }
 
@@ -1933,25 +1431,12 @@ void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, con
   { ::mrcqr::note_launch(); k_sketch_oz_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, s, colHi, idx, P, part, Y, ctl, level, tf, m); }
 }
 
-// The TRSM variant: 32-column update blocks (k_trsm_oz32) or 16-column ones
-// (k_trsm_oz).
-bool trsm_oz_wide(int n) {
-  (void)n;
-  return false;
-}
-
 size_t trsm_oz_rd_bytes(int n) {
-  const int nsub = (n + kTB - 1) / kTB, nkc = (n + kK - 1) / kK, nblk = (n + kT2B - 1) / kT2B;
-  const size_t narrow = (size_t)nsub * nkc * oz::kSlices * kTBPanel;
-  const size_t wide = (size_t)nblk * nkc * oz::kSlices * kT2BPanel + (size_t)nblk * oz::kSlices * kT2IPanel;
-  return narrow > wide ? narrow : wide;
+  const int nsub = (n + kTB - 1) / kTB, nkc = (n + kK - 1) / kK;
+  return (size_t)nsub * nkc * oz::kSlices * kTBPanel;
 }
 
-size_t trsm_oz_cole_bytes(int n) {
-  const size_t narrow = 2 * sizeof(int) * (size_t)((n + kTB - 1) / kTB * kTB);
-  const size_t wide = 3 * sizeof(int) * (size_t)((n + kT2B - 1) / kT2B * kT2B);
-  return narrow > wide ? narrow : wide;
-}
+size_t trsm_oz_cole_bytes(int n) { return 2 * sizeof(int) * (size_t)((n + kTB - 1) / kTB * kTB); }
 
 void launch_trsm_oz(int64_t m, int n, const double* A, int64_t lda, const double* RT, const double* rinv,
                     uint32_t* colE_ws, unsigned char* Rd, double* W, int64_t ldw, Ctl* ctl, int level, cudaStream_t st,
@@ -1962,19 +1447,6 @@ void launch_trsm_oz(int64_t m, int n, const double* A, int64_t lda, const double
   const int64_t nblocks = (m + kM - 1) / kM;
   const int64_t slots = 2 * (int64_t)num_sms();
   const unsigned grid = (unsigned)(nblocks < slots ? nblocks : slots);
-  if (trsm_oz_wide(n)) {
-    const int n32 = (n + kT2B - 1) / kT2B * kT2B, nblk = n32 / kT2B;
-    int* colE = reinterpret_cast<int*>(colE_ws);
-    int* colEi = colE + n32;
-    int* eR = colE + 2 * n32;
-    unsigned char* Ri = Rd + (size_t)nblk * nkc * oz::kSlices * kT2BPanel;
-    { ::mrcqr::note_launch(); k_oz_row_scale<<<(n + 7) / 8, 256, 0, st>>>(n, npad, RT, eR, ctl, level); }
-    { ::mrcqr::note_launch(); k_oz_prep_r32<<<n32, 256, 0, st>>>(n, npad, nkc, RT, eR, colE, colEi, Rd, Ri, colHiOut, nhi, ctl, level); }
-    cudaFuncSetAttribute(k_trsm_oz32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT2Smem);
-    const Trsm32Args a{m, n, A, lda, RT, rinv, eR, colE, colEi, Rd, Ri, nkc, W, ldw, colHiOut, ctl};
-    { ::mrcqr::note_launch(); k_trsm_oz32<<<grid, kTThreads, kT2Smem, st>>>(a, level); }
-    return;
-  }
   const int n16 = (n + kTB - 1) / kTB * kTB;
   int* colE = reinterpret_cast<int*>(colE_ws);
   int* eR = colE + n16;
@@ -1998,7 +1470,6 @@ void prepare_g_oz_kernels() {
   cudaFuncSetAttribute(kg_oz_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   cudaFuncSetAttribute(kg_oz_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   cudaFuncSetAttribute(kg_oz_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
-  cudaFuncSetAttribute(kg_oz_trsm32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT2Smem);
 }
 
 void launch_g_oz_colhi(const Group& g, int level, cudaStream_t st) {
@@ -2018,15 +1489,6 @@ void launch_g_oz_prep_r(const Group& g, int level, cudaStream_t st) {
 }
 void launch_g_oz_trsm(const Group& g, int level, cudaStream_t st) {
   if (g.nitems) { ::mrcqr::note_launch(); kg_oz_trsm<<<grid_oz(g.nitems, 2), kTThreads, kTSmem, st>>>(g, level); }
-}
-void launch_g_oz_row_scale32(const Group& g, int level, cudaStream_t st) {
-  if (g.nitems) { ::mrcqr::note_launch(); kg_oz_row_scale32<<<grid_oz(g.nitems, 16), 256, 0, st>>>(g, level); }
-}
-void launch_g_oz_prep_r32(const Group& g, int level, cudaStream_t st) {
-  if (g.nitems) { ::mrcqr::note_launch(); kg_oz_prep_r32<<<grid_oz(g.nitems, 16), 256, 0, st>>>(g, level); }
-}
-void launch_g_oz_trsm32(const Group& g, int level, cudaStream_t st) {
-  if (g.nitems) { ::mrcqr::note_launch(); kg_oz_trsm32<<<grid_oz(g.nitems, 2), kTThreads, kT2Smem, st>>>(g, level); }
 }
 void launch_g_oz_syrk(const Group& g, bool check, int level, cudaStream_t st) {
   (void)check;   // the item's problem record names W or Q (the Q buffer holds W before the finalize)

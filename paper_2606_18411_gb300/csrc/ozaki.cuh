@@ -110,10 +110,19 @@ __device__ __forceinline__ float small_int_to_float(int v) {
 
 // Adds one level's exact FP32 accumulator (an integer, |v| <= 2^24) into the
 // 64-bit halves of T.
+// The shift is a multiply by 2^(8 (3 - L % 4)) fused with the 64-bit add
+// (one mad.wide.s32: a sign-extended 32 x 32 -> 64-bit product plus the
+// accumulator), exact for every |v| < 2^31.
+__device__ __forceinline__ long long mad_wide_s32(int a, int b, long long c) {
+  long long r;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(b), "l"(c));
+  return r;
+}
+
 __device__ __forceinline__ void add_level(int L, float v, long long& hi, long long& lo) {
-  const long long iv = (long long)__float2int_rn(v);
-  if (L < 4) hi += iv << (8 * (3 - L));
-  else lo += iv << (8 * (7 - L));
+  const int iv = __float2int_rn(v);
+  if (L < 4) hi = mad_wide_s32(iv, 1 << (8 * (3 - L)), hi);
+  else lo = mad_wide_s32(iv, 1 << (8 * (7 - L)), lo);
 }
 
 // Signed 128-bit integer as (high word th, low word tl): two's complement.

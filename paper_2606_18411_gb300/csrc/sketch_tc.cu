@@ -13,7 +13,10 @@
 // A CTA keeps C and S (rounded to the sketch precision) in shared
 // memory for up to 256 sampled rows (one or two MMA tiles of 128) and 64
 // columns of A, and per slab:
-//   1. TMA brings the FP64 tile A[j0 : j0+T, n0 : n0+64] (3-4 stages);
+//   1. TMA brings the FP64 tile A[j0 : j0+T, n0 : n0+64] (3-4 stages); where
+//      no TMA map can describe A (base not 16-byte aligned or lda odd: the
+//      copy engine needs 16-byte strides) the converting warps load their
+//      values from global memory instead, one slab ahead, into registers;
 //   2. the tile is sign-flipped (Philox; XOR of the sign bit), scaled per
 //      column by 2^e so that max |.| lies in [2^13, 2^14), rounded once to p
 //      (fl_p) and written as a K-major SWIZZLE_128B operand -- all in 32-bit
@@ -30,6 +33,7 @@
 //
 // Every wait is bounded; on a timeout the CTA waits (bounded) for its own
 // copies in flight, frees its TMEM, raises TIMEOUT and returns.
+#include <cstring>
 #include <mutex>
 
 #include "kernels.h"
@@ -130,15 +134,19 @@ struct TcCta {
   uint32_t tmem;
   float (*colscale)[kN];
   uint32_t (*sgnmask)[Cfg<PREC, MT>::T];
-  uint32_t seq;   // slabs this CTA has run: drives every barrier phase and buffer index
+  uint32_t seq;    // slabs this CTA has run: the MMA barriers' phases and the operand/TMEM buffers
+  uint32_t tseq;   // slabs this CTA has loaded by TMA: the copy barriers' stages and phases (a
+                   // plain-copy item completes no copy-barrier phase, so it must not advance them)
 };
 
 // One work item: sampled rows s0 .. s0 + 128 MT - 1, columns n0 .. n0 + 63,
-// rows [j_begin, j_end) of A (TMA map tmap); the partial sums go to
-// out[col s + row].  False when a wait timed out (every thread together; this
-// CTA's copies and MMAs in flight are awaited first).
+// rows [j_begin, j_end) of A (TMA map tmap, or with tmap null plain copies
+// of A with leading dimension lda); the partial sums go to out[col s + row].
+// False when a wait timed out (every thread together; this CTA's copies and
+// MMAs in flight are awaited first).
 template <int PREC, int MT>
-__device__ __forceinline__ bool sketch_tc_item(const CUtensorMap* tmap, int64_t m, int n, int s,
+__device__ __forceinline__ bool sketch_tc_item(const CUtensorMap* tmap, const double* __restrict__ A, int64_t lda,
+                                               int64_t m, int n, int s,
                                                const uint32_t* __restrict__ idx, const double* __restrict__ tab,
                                                uint2 key, int64_t j_begin, int64_t j_end, int s0, int n0,
                                                double* __restrict__ out, int tf, TcCta<PREC, MT>& S) {
@@ -186,14 +194,35 @@ __device__ __forceinline__ bool sketch_tc_item(const CUtensorMap* tmap, int64_t 
   __syncthreads();
   tc::fence_after();
 
-  int issued = 0;   // TMA loads of this item issued (thread 0)
-  if (tid == 0) {
-    for (int st = 0; st < C::STAGES && st < nslabs; ++st) {
-      const int sg = (int)((S.seq + (uint32_t)st) % C::STAGES);
+  // plain loads (no TMA map): every thread copies its share of the slab's
+  // FP64 tile into the stage with 8-byte cp.async, in the layout the TMA box
+  // has ([column][row], zero outside the chunk and n), one commit group per
+  // slab; a thread waits for its own groups before the barrier that precedes
+  // the conversion
+  auto dcopy = [&](int sl, int sg) {
+    const int64_t j0 = j_begin + (int64_t)sl * T;
+    double* dst = xd + sg * (C::XD_BYTES / 8);
+    for (int e = tid; e < T * kN; e += kThreads) {
+      const int c = e / T, r = e % T;
+      const int col = n0 + c;
+      const int64_t j = j0 + r;
+      const bool ok = col < n && j < j_end;
+      tc::cp_async8_zfill(dst + e, ok ? A + j + (int64_t)col * lda : A, ok ? 8u : 0u);
+    }
+    tc::cp_async_commit();
+  };
+
+  int issued = 0;   // slab loads of this item issued (the same count in every thread)
+  const uint32_t cbase = tmap ? S.tseq : 0u;   // copy-stage index of this item's slab 0
+  for (int st = 0; st < C::STAGES && st < nslabs; ++st) {
+    const int sg = (int)((cbase + (uint32_t)st) % C::STAGES);
+    if (!tmap) {
+      dcopy(st, sg);
+    } else if (tid == 0) {
       tc::mbar_expect_tx(&tma_bar[sg], C::XD_BYTES);
       tc::tma_load_2d(xd + sg * (C::XD_BYTES / 8), tmap, (int)(j_begin + st * T), n0, &tma_bar[sg]);
-      ++issued;
     }
+    ++issued;
   }
 
   // epilogue identity
@@ -245,9 +274,10 @@ __device__ __forceinline__ bool sketch_tc_item(const CUtensorMap* tmap, int64_t 
   };
 
   for (int sl = 0; sl < nslabs; ++sl) {
-    const uint32_t u = S.seq + (uint32_t)sl;   // slab index over the CTA's items: stage, parity, buffer
-    const int stage = (int)(u % C::STAGES);
-    const uint32_t par = (u / C::STAGES) & 1u;
+    const uint32_t u = S.seq + (uint32_t)sl;   // slab index over the CTA's items: MMA parity, buffer
+    const uint32_t cu = cbase + (uint32_t)sl;   // copy stage and its barrier parity
+    const int stage = (int)(cu % C::STAGES);
+    const uint32_t par = (cu / C::STAGES) & 1u;
     const int buf = (int)(u & 1u);
     const int64_t j0 = j_begin + (int64_t)sl * T;
     prefetch_rotation((int)u);
@@ -256,7 +286,16 @@ __device__ __forceinline__ bool sketch_tc_item(const CUtensorMap* tmap, int64_t 
       sgnmask[buf][tid] = j < j_end ? (philox4x32_10(make_uint4((uint32_t)j, 0u, 0u, 0u), key).x & 1u) << 31
                                     : 0xFFFFFFFFu;   // all ones marks a row outside the chunk
     }
-    const bool ok_tma = tc::mbar_wait(&tma_bar[stage], par);
+    bool ok_tma = true;
+    if (tmap) {
+      ok_tma = tc::mbar_wait(&tma_bar[stage], par);
+    } else {   // slab sl's group complete: at most issued - sl - 1 younger groups pending
+      const int younger = issued - sl - 1;   // <= STAGES - 1 <= 3
+      if (younger >= 3) tc::cp_async_wait_group<3>();
+      else if (younger == 2) tc::cp_async_wait_group<2>();
+      else if (younger == 1) tc::cp_async_wait_group<1>();
+      else tc::cp_async_wait_group<0>();
+    }
     if (__syncthreads_or(!ok_tma)) { abort = true; break; }
     consumed = sl + 1;
     // convert the FP64 tile: warp w owns columns 4w..4w+3
@@ -301,13 +340,17 @@ __device__ __forceinline__ bool sketch_tc_item(const CUtensorMap* tmap, int64_t 
     }
     tc::fence_proxy_async();
     __syncthreads();
-    if (tid == 0) {
-      if (issued < nslabs) {   // refill the stage just consumed
+    if (issued < nslabs) {   // refill the stage just consumed
+      if (!tmap) {
+        dcopy(issued, stage);
+      } else if (tid == 0) {
         tc::mbar_expect_tx(&tma_bar[stage], C::XD_BYTES);
         tc::tma_load_2d(xd + stage * (C::XD_BYTES / 8), tmap, (int)(j_begin + (int64_t)issued * T), n0,
                         &tma_bar[stage]);
-        ++issued;
       }
+      ++issued;
+    }
+    if (tid == 0) {
       tc::fence_after();
       const uint32_t tb = tc::smem_u32(tabs), xbs = tc::smem_u32(xb);
 #pragma unroll
@@ -353,10 +396,11 @@ __device__ __forceinline__ bool sketch_tc_item(const CUtensorMap* tmap, int64_t 
   }
 
   if (abort) {
+    if (!tmap) tc::cp_async_wait_all();
     if (tid == 0) {   // this CTA's own copies and MMAs in flight land before its shared memory and TMEM go away
-      for (int v = consumed; v < issued; ++v) {
-        const uint32_t u = S.seq + (uint32_t)v;
-        tc::mbar_wait(&tma_bar[u % C::STAGES], (u / C::STAGES) & 1u, 1u << 20);
+      for (int v = consumed; v < issued && tmap; ++v) {
+        const uint32_t cu = cbase + (uint32_t)v;
+        tc::mbar_wait(&tma_bar[cu % C::STAGES], (cu / C::STAGES) & 1u, 1u << 20);
       }
       for (int v = mma_done; v < mma_issued; ++v) {
         const uint32_t u = S.seq + (uint32_t)v;
@@ -366,6 +410,7 @@ __device__ __forceinline__ bool sketch_tc_item(const CUtensorMap* tmap, int64_t 
     return false;
   }
   S.seq += (uint32_t)nslabs;
+  if (tmap) S.tseq += (uint32_t)nslabs;
 #pragma unroll
   for (int c = 0; c < C::ACC; ++c) {
     const int col = n0 + c_lo + c;
@@ -397,7 +442,7 @@ __device__ __forceinline__ bool sketch_tc_item(const CUtensorMap* tmap, int64_t 
   __syncthreads();                                                                                    \
   tc::fence_after();                                                                                  \
   TcCta<PREC, MT> S{smem + C::TAB_OFF, smem + C::XT_OFF, reinterpret_cast<double*>(smem + C::XD_OFF), \
-                    tma_bar_s,          mma_bar_s,         tmem_base, colscale_s, sgnmask_s, 0u};
+                    tma_bar_s,          mma_bar_s,         tmem_base, colscale_s, sgnmask_s, 0u, 0u};
 
 template <int PREC, int MT>
 __device__ __forceinline__ void sketch_tc_cta_end(TcCta<PREC, MT>& S, bool abort, Ctl* ctl) {
@@ -409,13 +454,15 @@ __device__ __forceinline__ void sketch_tc_cta_end(TcCta<PREC, MT>& S, bool abort
 
 template <int PREC, int MT>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_sketch_tc(const __grid_constant__ CUtensorMap tmapA, int64_t m, int n, int s, const uint32_t* __restrict__ idx,
+    k_sketch_tc(const __grid_constant__ CUtensorMap tmapA, int use_map, const double* __restrict__ A, int64_t lda,
+                int64_t m, int n, int s, const uint32_t* __restrict__ idx,
                 const double* __restrict__ tab, uint2 key, int64_t rows_per_chunk,
                 double* __restrict__ Ypart, Ctl* ctl, int level, int tf) {
   if (level_inactive(ctl, level)) return;
   MRCQR_SKETCH_TC_CTA(S)
   const int64_t j_begin = (int64_t)blockIdx.z * rows_per_chunk;
-  const bool ok = sketch_tc_item<PREC, MT>(&tmapA, m, n, s, idx, tab, key, j_begin, min(m, j_begin + rows_per_chunk),
+  const bool ok = sketch_tc_item<PREC, MT>(use_map ? &tmapA : nullptr, A, lda, m, n, s, idx, tab, key, j_begin,
+                                           min(m, j_begin + rows_per_chunk),
                                            blockIdx.x * (kM * MT), blockIdx.y * kN,
                                            Ypart + (size_t)blockIdx.z * (size_t)s * (size_t)n, tf, S);
   sketch_tc_cta_end(S, !ok, ctl);
@@ -423,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Grouped form for batched plans: items {problem, chunk, 128 MT-row sample
 // tile, 64-column block}; each problem's TMA maps (slabs of 64 and of 32 rows)
-// sit in the plan's workspace.
+// sit in the plan's workspace (null where A has no map: plain loads).
 template <int PREC, int MT>
 __global__ void __launch_bounds__(kThreads, 1) kg_sketch_tc(Group g, int level) {
   MRCQR_SKETCH_TC_CTA(S)
@@ -435,7 +482,8 @@ __global__ void __launch_bounds__(kThreads, 1) kg_sketch_tc(Group g, int level) 
     if (level_inactive(P.ctl, level)) continue;
     const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(PREC == P_FP32 ? P.tmap32 : P.tmap64);
     const int64_t j_begin = (int64_t)w.y * P.rows_per_chunk;
-    if (!sketch_tc_item<PREC, MT>(map, P.m, P.n, P.s, P.idx, P.tab, P.key, j_begin, min(P.m, j_begin + P.rows_per_chunk),
+    if (!sketch_tc_item<PREC, MT>(map, P.A, P.lda, P.m, P.n, P.s, P.idx, P.tab, P.key, j_begin,
+                                  min(P.m, j_begin + P.rows_per_chunk),
                                   w.z * (kM * MT), w.w * kN, P.ypart + (size_t)w.y * (size_t)P.s * (size_t)P.n, P.tf,
                                   S)) {
       abort = true;
@@ -466,9 +514,9 @@ EncodeFn encode_fn() {
 }
 
 template <int PREC, int MT>
-bool launch_tc(const CUtensorMap& map, int64_t m, int n, int s, const uint32_t* idx, const double* tab,
-               uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level, cudaStream_t st,
-               int tf) {
+bool launch_tc(const CUtensorMap& map, bool use_map, const double* A, int64_t lda, int64_t m, int n, int s,
+               const uint32_t* idx, const double* tab, uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level,
+               cudaStream_t st, int tf) {
   using C = Cfg<PREC, MT>;
   const size_t smem = C::SMEM + 1024;
   if (cudaFuncSetAttribute(k_sketch_tc<PREC, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -477,8 +525,8 @@ bool launch_tc(const CUtensorMap& map, int64_t m, int n, int s, const uint32_t* 
   int64_t rpc = (m + chunks - 1) / chunks;
   rpc = (rpc + 63) / 64 * 64;
   const dim3 grid((s + kM * MT - 1) / (kM * MT), (n + kN - 1) / kN, chunks);
-  { ::mrcqr::note_launch(); k_sketch_tc<PREC, MT><<<grid, kThreads, smem, st>>>(map, m, n, s, idx, tab, seed_key(seed), rpc, Ypart, ctl,
-                                                      level, tf); }
+  { ::mrcqr::note_launch(); k_sketch_tc<PREC, MT><<<grid, kThreads, smem, st>>>(map, use_map ? 1 : 0, A, lda, m, n, s, idx, tab,
+                                                                               seed_key(seed), rpc, Ypart, ctl, level, tf); }
   return true;
 }
 
@@ -486,19 +534,11 @@ template <int PREC>
 bool launch_prec(const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx, const double* tab,
                  uint64_t seed, int chunks, double* Ypart, Ctl* ctl, int level, cudaStream_t st,
                  int tf) {
-  EncodeFn enc = encode_fn();
-  if (!enc) return false;
   CUtensorMap map;
-  const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
-  const cuuint64_t strides[1] = {(cuuint64_t)lda * sizeof(double)};
-  const cuuint32_t box[2] = {(cuuint32_t)Cfg<PREC, 1>::T, (cuuint32_t)kN};
-  const cuuint32_t estr[2] = {1, 1};
-  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(A), dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return false;
-  if (s > kM) return launch_tc<PREC, 2>(map, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf);
-  return launch_tc<PREC, 1>(map, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf);
+  memset(&map, 0, sizeof(map));
+  const bool use_map = sketch_tc_encode(Cfg<PREC, 1>::T, A, lda, m, n, &map);   // else plain loads
+  if (s > kM) return launch_tc<PREC, 2>(map, use_map, A, lda, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf);
+  return launch_tc<PREC, 1>(map, use_map, A, lda, m, n, s, idx, tab, seed, chunks, Ypart, ctl, level, st, tf);
 }
 
 }  // namespace
@@ -541,9 +581,9 @@ void launch_g_sketch_tc(const Group& g, int prec, int mt, int level, cudaStream_
 }
 
 bool sketch_tc_eligible(int prec, const double* A, int64_t lda) {
+  (void)lda;   // any leading dimension: plain loads where no TMA map fits
   if (prec != P_FP16 && prec != P_BF16 && prec != P_FP32) return false;
-  if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda & 1) != 0) return false;
-  return encode_fn() != nullptr;
+  return (reinterpret_cast<uintptr_t>(A) & 7) == 0;
 }
 
 bool launch_sketch_tc(int prec, const double* A, int64_t lda, int64_t m, int n, int s, const uint32_t* idx,

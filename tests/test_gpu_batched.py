@@ -211,3 +211,31 @@ def test_grouped_heavy_phases_match_per_problem_kernels(env):
         assert O.orthogonality_error(Q)[0] <= 1e-13
         assert O.residual_error(A, Q, R)[0] <= 1e-13
     assert out[0][2]["kernels_per_execute"] < 120 < out[1][2]["kernels_per_execute"], (out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("rows_per_chunk", [2048, 8192])
+def test_batched_mixes_tma_and_plain_copy_sketches(env, rows_per_chunk):
+    # even m (TMA loads of A) and odd m (plain copies: no TMA map for an odd leading dimension) share the
+    # grouped tensor-core sketch launches, so a CTA runs items of both kinds in turn; with escalation off
+    # every FP16 / BF16 / FP32 sketch must be right the first time, and Q, R pass the oracle's checks
+    torch, M = env
+    shapes = [(16384, 32, 1e2, "fp16"), (16385, 32, 1e2, "fp16"), (20001, 48, 1e3, "fp16"), (20000, 48, 1e3, "fp16"),
+              (12289, 100, 1e2, "fp16"), (12288, 100, 1e2, "fp16"), (9999, 16, 1e1, "bf16"), (10000, 16, 1e1, "bf16"),
+              (30001, 64, 1e5, "fp32"), (30000, 64, 1e5, "fp32"), (8191, 130, 1e4, "fp32"), (8192, 130, 1e4, "fp32")]
+    mats = [inputs.make_matrix(m, n, k, seed=2100 + i) for i, (m, n, k, _) in enumerate(shapes)]
+    precs = [p for *_, p in shapes]
+    As = [M.to_colmajor(a) for a in mats]
+    Qs = [M.empty_colmajor(*a.shape) for a in mats]
+    Rs = [M.empty_colmajor(a.shape[1], a.shape[1]) for a in mats]
+    status = torch.full((len(mats),), -1, dtype=torch.int32, device="cuda")
+    plan = M.BatchedPlan(As, Qs, Rs, precs, list(range(len(mats))), status, escalate=False,
+                         rows_per_chunk=rows_per_chunk)
+    for _ in range(2):
+        plan.execute()
+    torch.cuda.synchronize()
+    plan.close()
+    assert status.cpu().tolist() == [0] * len(mats)
+    for A, Q, R in zip(mats, Qs, Rs):
+        Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
+        assert O.orthogonality_error(Qh)[0] <= 1e-13
+        assert O.residual_error(A, Qh, Rh)[0] <= 1e-13

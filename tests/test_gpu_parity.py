@@ -122,10 +122,11 @@ def test_sketch_variants_agree_and_fall_back(M):
     y_simt = _np(M.sketch(Ad, 2 * n, "fp16", seed=5, variant=1))
     assert M.last_sketch_variant() == 1
     assert _rel(y_tc, y_simt) < 5e-3
-    # odd leading dimension: no TMA, the auto choice is the SIMT kernel
+    # odd leading dimension: no TMA map; the tensor-core kernel stages A with plain copies
     Aodd = M.to_colmajor(A, ld=m + 1)
-    _ = M.sketch(Aodd, 2 * n, "fp16", seed=5)
-    assert M.last_sketch_variant() == 1
+    y_odd = _np(M.sketch(Aodd, 2 * n, "fp16", seed=5))
+    assert M.last_sketch_variant() == 2
+    np.testing.assert_array_equal(y_odd, y_tc)
     # FP64: emulated FP64 on the tensor cores unless the SIMT variant is asked for
     _ = M.sketch(Ad, 2 * n, "fp64", seed=5, variant=2)
     assert M.last_sketch_variant() == 3
@@ -162,9 +163,26 @@ def test_sketch_four_step_falls_back(M):
     B = M.to_colmajor(inputs.make_matrix(4096, 16, 1e3, seed=4))
     _ = M.sketch_transform(B, 32, "rfft", prec="fp16", seed=1, variant=4)
     assert M.last_sketch_variant() == 2
-    # odd leading dimension: no TMA at all
+    # odd leading dimension: no TMA map, so no four-step; the dense-row kernel copies A without TMA
     _ = M.sketch(M.to_colmajor(inputs.make_matrix(4096, 16, 1e3, seed=5), ld=4097), 32, "fp16", seed=1, variant=4)
-    assert M.last_sketch_variant() == 1
+    assert M.last_sketch_variant() == 2
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+@pytest.mark.parametrize("m,n,ld", [(5001, 70, 5001), (4096, 130, 4097), (777, 3, 779), (40000, 64, 40001)])
+def test_sketch_plain_copies_match_tma(M, prec, m, n, ld):
+    # the same matrix once with a TMA-describable layout (even ld) and once without (odd ld):
+    # the two staging paths feed identical tiles to the same arithmetic, so Y is bit for bit the same
+    A = inputs.make_matrix(m, n, 1e4, seed=m + n)
+    s = 2 * n
+    ld_even = ld + 1 if ld % 2 else ld
+    y_tma = _np(M.sketch(M.to_colmajor(A, ld=ld_even), s, prec, seed=23, variant=2))
+    assert M.last_sketch_variant() == 2
+    y_plain = _np(M.sketch(M.to_colmajor(A, ld=ld), s, prec, seed=23, variant=2))
+    assert M.last_sketch_variant() == 2
+    np.testing.assert_array_equal(y_plain, y_tma)
+    d, idx = O.rademacher(m, 23), O.sample_rows(m, s, 23)
+    assert _rel(y_plain, O.sketch(A, idx, d)) <= SKETCH_TOL[prec]
 
 
 def test_sketch_scale_exponent_keeps_fp16_in_range(M):
