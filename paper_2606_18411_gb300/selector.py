@@ -282,9 +282,9 @@ def evaluate_baselines(count: int, m: int, weights: str = DEFAULT_WEIGHTS, log_e
 
 
 def policy_times(count: int, m: int, seed0: int = 5, n_choices=(64, 128, 256), reps: int = 2, device="cuda"):
-    """Measured wall time of three policies over the same held-out mix (kappa_2 log-uniform in
+    """Measured wall time of four policies over the same held-out mix (kappa_2 log-uniform in
     [1, 1e16], the four spectra, n from n_choices): AUTO (the selector's FP16 sketch, features and
-    choice included), always FP32 (escalating on failure) and always FP64.  Each matrix is factored
+    choice included), always FP16 and always FP32 (each escalating on failure) and always FP64.  Each matrix is factored
     once per policy per repetition, the policies interleaved per matrix; CUDA events around each
     call.  Returns total ms per policy and the statuses."""
     rng = np.random.default_rng(seed0)
@@ -296,7 +296,7 @@ def policy_times(count: int, m: int, seed0: int = 5, n_choices=(64, 128, 256), r
         mats.append((inputs.make_matrix_torch(m, n, kappa, kind=kind, seed=seed0 * 1000003 + i, device=device),
                      (n, kappa, kind)))
     load_into_library()
-    tot = {"auto": 0.0, "fp32": 0.0, "fp64": 0.0}
+    tot = {"auto": 0.0, "fp16": 0.0, "fp32": 0.0, "fp64": 0.0}
     ok = {k: True for k in tot}
     stats = torch.zeros(8, dtype=torch.float64, device=device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -305,7 +305,7 @@ def policy_times(count: int, m: int, seed0: int = 5, n_choices=(64, 128, 256), r
             mm, n = A.shape
             Q = M.empty_colmajor(mm, n, device=device)
             R = M.empty_colmajor(n, n, device=device)
-            for pol in ("auto", "fp32", "fp64"):
+            for pol in ("auto", "fp16", "fp32", "fp64"):
                 torch.cuda.synchronize()
                 e0.record()
                 M.factor_ex(A, Q, R, prec=pol, seed=i, stats_device=stats)
@@ -316,7 +316,8 @@ def policy_times(count: int, m: int, seed0: int = 5, n_choices=(64, 128, 256), r
                     ok[pol] = ok[pol] and _lib.Stats.from_buffer_copy(stats.cpu().numpy().tobytes()).status == 0
     return {"count": count, "m": m, "n_choices": list(n_choices), "reps": reps,
             "total_ms": {k: v / reps for k, v in tot.items()}, "all_ok": ok,
-            "auto_speedup": {"vs_fp32": tot["fp32"] / tot["auto"], "vs_fp64": tot["fp64"] / tot["auto"]}}
+            "auto_speedup": {"vs_fp16": tot["fp16"] / tot["auto"], "vs_fp32": tot["fp32"] / tot["auto"],
+                             "vs_fp64": tot["fp64"] / tot["auto"]}}
 
 
 def main():
@@ -328,6 +329,7 @@ def main():
     t.add_argument("--m", type=int, default=1 << 16)
     t.add_argument("--epochs", type=int, default=40)
     t.add_argument("--n-max", type=int, default=512)
+    t.add_argument("--cost-m", type=int, default=1 << 20, help="rows of the run-cost measurement")
     t.add_argument("--out", default=DEFAULT_WEIGHTS)
     t.add_argument("--report", default=None)
     b = sub.add_parser("baselines")
@@ -350,7 +352,7 @@ def main():
                 json.dump(rep, f, indent=1)
         return
     t0 = time.time()
-    costs, times = measure_costs(m=args.m)
+    costs, times = measure_costs(m=args.cost_m)
     print(f"relative run costs fp16/fp32/fp64: {costs} ({times} ms)", flush=True)
     nr = (32, args.n_max)
     Xtr, ytr, _, v1 = make_dataset(args.count, args.m, seed0=1, n_range=nr, log_every=2000)
@@ -369,7 +371,7 @@ def main():
     a32 = sum(ladder_cost(1, int(l), costs) for l in yt)
     a64 = sum(ladder_cost(2, int(l), costs) for l in yt)
     ideal = sum(ladder_cost(int(l), int(l), costs) for l in yt)
-    rep = {"train_count": args.count, "heldout_count": args.heldout, "m": args.m,
+    rep = {"train_count": args.count, "heldout_count": args.heldout, "m": args.m, "cost_m": args.cost_m,
            "label_counts_train": np.bincount(ytr.cpu().numpy(), minlength=3).tolist(),
            "label_counts_heldout": np.bincount(yt, minlength=3).tolist(),
            "monotonicity_violations": int(v1 + v2), "relative_costs": costs, "run_ms": times,
