@@ -86,11 +86,17 @@ typedef struct mrcqr_opts {
                              by a table measured on GB300 (dense sampled rows, or the four-step
                              transform where it applies) when A is 16-byte aligned and lda is even,
                              SIMT otherwise; the FP64 sketch as emulated FP64 on the tensor cores
-                             (unless fp64_products = 1); 1: SIMT (FP64 FMA for FP64); 2: tensor-core
-                             dense sampled rows when possible; 4: the four-step transform (a radix-64
-                             DFT of the strided subsequences on the tensor cores, then only the
-                             sampled outputs) when possible -- DCT, FP16/BF16/FP32, m a multiple of
-                             1024 up to 2^22, at most 1024 sampled rows -- else as 2 */
+                             (unless fp64_products = 1) from digit planes of D A sliced once (5)
+                             where they fit, else sliced per work item (3); 1: SIMT (FP64 FMA for
+                             FP64); 2: tensor-core dense sampled rows when possible; 4: the four-step
+                             transform (a radix-64 DFT of the strided subsequences on the tensor
+                             cores, then only the sampled outputs) when possible -- DCT,
+                             FP16/BF16/FP32, m a multiple of 1024 up to 2^22, at most 1024 sampled
+                             rows -- else as 2; 3: FP64 only, the emulated sketch sliced per work
+                             item.  The digit planes take 16 bytes per entry of A: a factorization
+                             writes them into its Q buffer (Q is overwritten before stage 2 of the
+                             level), in row chunks of at most half of Q; mrcqr_sketch and
+                             mrcqr_sketch_ex hold them in their workspace. */
   double ortho_tol;   /* acceptance threshold on ||I - Q^T Q||_F (default 1e-13) */
   void* stats_device; /* optional DEVICE pointer to an mrcqr_stats_t written at the end */
   int32_t fp64_products; /* 0 (default): the FP64 sketch, the off-diagonal updates of W = A R_s^{-1},
@@ -392,7 +398,8 @@ int mrcqr_mlp_train_step(int batch, const float* X, const int32_t* y, const floa
 
 /* Sketch kernel variant used by the most recent sketch launch of this
  * process: 1 SIMT, 2 tensor-core dense sampled rows, 3 emulated FP64 on the
- * tensor cores, 4 four-step transform (0 before any). */
+ * tensor cores sliced per work item, 4 four-step transform, 5 emulated FP64
+ * from digit planes (0 before any). */
 int mrcqr_last_sketch_variant(void);
 
 /* Number of kernels this library has launched from the host in this process

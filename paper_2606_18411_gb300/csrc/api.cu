@@ -29,12 +29,15 @@ struct Plan {
   int tf = T_DCT;   // sketch transform; s counts the rows of Y (2 x bins for T_RFFT_REIM)
   size_t off_ctl = 0, off_idx = 0, off_tab = 0, off_ypart = 0, off_y = 0, off_sqr = 0, off_rs = 0, off_rst = 0,
          off_rinv = 0, off_gpart = 0, off_rc = 0, off_xt = 0, off_e = 0, off_feat = 0, off_oze = 0, off_ozx = 0,
-         off_colhi = 0, off_ozpart = 0, off_tcole = 0, off_trd = 0, total = 0;
+         off_colhi = 0, off_ozpart = 0, off_tcole = 0, off_trd = 0, off_tabd = 0, off_planes = 0, total = 0;
+  size_t ozpart_bytes = 0, planes_bytes = 0;
   SyrkOzPlan oz{};
   SketchOzPlan sk{};
 };
 
-Plan make_plan(int64_t m, int n, int s, int tf = T_DCT) {
+// planes: reserve the digit planes of the FP64 sketch in the workspace (the step-level sketch call,
+// which has no Q buffer to lend them); a factorization lends them its Q buffer.
+Plan make_plan(int64_t m, int n, int s, int tf = T_DCT, bool planes = false) {
   Plan p;
   p.tf = tf;
   p.m = m;
@@ -68,9 +71,18 @@ Plan make_plan(int64_t m, int n, int s, int tf = T_DCT) {
   p.oz = syrk_oz_plan(m, n);
   p.sk = sketch_oz_plan(m, n, s);
   p.off_colhi = take(syrk_oz_colhi_bytes(n));
-  p.off_ozpart = take(std::max(syrk_oz_part_bytes(p.oz), sketch_oz_part_bytes(p.sk)));   // used one after the other
+  // the FP64 sketch from digit planes in row chunks: at most the chunks of a Q buffer with ldq = m, or
+  // one chunk in the workspace's own planes
+  const size_t q_bytes = sizeof(double) * (size_t)m * n;
+  const int64_t mr = (m + 31) / 32 * 32;
+  if (planes) p.planes_bytes = 16ull * (size_t)n * (size_t)mr;
+  p.ozpart_bytes = std::max({syrk_oz_part_bytes(p.oz), sketch_oz_part_bytes(p.sk), sketch_ozp_part_bytes(m, n, s, q_bytes),
+                             planes ? sketch_ozp_part_bytes(m, n, s, p.planes_bytes) : size_t(0)});
+  p.off_ozpart = take(p.ozpart_bytes);   // the Gram, the check and the FP64 sketch use it one after the other
   p.off_tcole = take(trsm_oz_cole_bytes(n));
   p.off_trd = take(trsm_oz_rd_bytes(n));
+  p.off_tabd = take(16ull * (size_t)(m + 1));   // FP16 digits of the quarter-wave table
+  if (planes) p.off_planes = take(p.planes_bytes);
   p.total = o;
   return p;
 }
@@ -230,19 +242,31 @@ int make_ladder(int p, bool escalate, int* lv) {
 int g_sketch_variant_last = 0;
 
 // Sketch Y of level `lvl` (Algorithm 2 steps 2-4).  FP64: emulated FP64 on the
-// tensor cores unless the SIMT variant or FP64-FMA products are asked for.
-// Returns the variant that ran (1 SIMT, 2 tensor cores, 3 emulated FP64).
+// tensor cores unless the SIMT variant or FP64-FMA products are asked for,
+// from digit planes written into `scratch` (variant 5) where it is large and
+// aligned enough and the variant allows, else sliced per work item (3).
+// Returns the variant that ran (1 SIMT, 2 tensor-core dense rows, 3 emulated
+// FP64 sliced per item, 4 four-step, 5 emulated FP64 from digit planes).
 int enqueue_sketch(const Plan& p, void* ws, int prec, int variant, int fp64_products, const double* A, int64_t lda,
-                   uint64_t seed, double* Y, Ctl* ctl, int lvl, cudaStream_t st) {
+                   uint64_t seed, double* Y, Ctl* ctl, int lvl, cudaStream_t st, void* scratch = nullptr,
+                   size_t scratch_bytes = 0) {
   const uint32_t* idx = at<uint32_t>(ws, p.off_idx);
   const double* tab = at<double>(ws, p.off_tab);
   int used = 0;
   if (prec == P_FP64 && variant != 1 && fp64_products == 0) {
+    uint32_t* colhi = at<uint32_t>(ws, p.off_colhi);
+    long long* part = at<long long>(ws, p.off_ozpart);
+    const bool planes = variant != 3 && sketch_ozp_eligible(p.m, p.n, scratch, scratch_bytes) &&
+                        sketch_ozp_part_bytes(p.m, p.n, p.s, scratch_bytes) <= p.ozpart_bytes;
+    used = 3;
     launch(SG_SKETCH, lvl, st, [&] {
-      launch_sketch_oz(p.m, p.n, p.s, A, lda, idx, tab, seed, p.sk, at<uint32_t>(ws, p.off_colhi),
-                       at<long long>(ws, p.off_ozpart), Y, ctl, lvl, st, p.tf);
+      if (planes && launch_sketch_ozp(p.m, p.n, p.s, A, lda, idx, tab, at<uint4>(ws, p.off_tabd), seed, colhi, part,
+                                      p.ozpart_bytes, Y, scratch, scratch_bytes, ctl, lvl, st, p.tf))
+        used = 5;
+      else
+        launch_sketch_oz(p.m, p.n, p.s, A, lda, idx, tab, seed, p.sk, colhi, part, Y, ctl, lvl, st, p.tf);
     });
-    return 3;
+    return used;
   }
   double* ypart = at<double>(ws, p.off_ypart);
   int chunks = p.chunks;
@@ -371,7 +395,9 @@ int mrcqr_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, double* 
   launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, st); });
   for (int L = 0; L < nlevels; ++L) {
     double* y = at<double>(ws, p.off_y);
-    g_sketch_variant_last = enqueue_sketch(p, ws, lv[L], variant, fp64p, A, lda, seed, y, ctl, L, st);
+    // the FP64 sketch borrows the Q buffer for its digit planes (stage 2 of the level writes W there later)
+    g_sketch_variant_last = enqueue_sketch(p, ws, lv[L], variant, fp64p, A, lda, seed, y, ctl, L, st, Q,
+                                           sizeof(double) * (size_t)((n - 1) * ldq + m));
     launch(SG_SQR, L, st, [&] {
       launch_sketch_qr(lv[L], (int)n, s, y, at<void>(ws, p.off_sqr), at<double>(ws, p.off_rs),
                        at<double>(ws, p.off_rst), at<double>(ws, p.off_rinv), ctl, L, st);
@@ -452,7 +478,7 @@ int mrcqr_sketch_transform(int64_t m, int64_t n, const double* A, int64_t lda, i
   if (s < 0) return MRCQR_ERR_INVALID;
   if (sketch_prec < P_FP16 || sketch_prec > P_FP64) return MRCQR_ERR_INVALID;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const Plan p = make_plan(m, (int)n, (int)s, transform);
+  const Plan p = make_plan(m, (int)n, (int)s, transform, sketch_prec == P_FP64 && variant != 1 && variant != 3);
   void* ws = nullptr;
   if (cudaMallocAsync(&ws, p.total, st) != cudaSuccess) {
     cudaGetLastError();
@@ -464,7 +490,8 @@ int mrcqr_sketch_transform(int64_t m, int64_t n, const double* A, int64_t lda, i
   launch(SG_INIT, 0, st, [&] { { ::mrcqr::note_launch(); k_init_ctl<<<1, 1, 0, st>>>(ctl, 1, sketch_prec, P_FP64, P_FP64, P_FP64, kDefaultTol); } });
   launch(SG_SAMPLE, 0, st, [&] { launch_sample(m, (int)c, seed, idx, ctl, st, transform); });
   launch(SG_COSTAB, 0, st, [&] { launch_costab(m, tab, st); });
-  g_sketch_variant_last = enqueue_sketch(p, ws, sketch_prec, variant, 0, A, lda, seed, Y, ctl, 0, st);
+  g_sketch_variant_last = enqueue_sketch(p, ws, sketch_prec, variant, 0, A, lda, seed, Y, ctl, 0, st,
+                                         p.planes_bytes ? at<void>(ws, p.off_planes) : nullptr, p.planes_bytes);
   cudaFreeAsync(ws, st);
   return finish(st);
 }

@@ -196,6 +196,23 @@ void launch_sketch_oz(int64_t m, int n, int s, const double* A, int64_t lda, con
                       int level, cudaStream_t st, int tf = 0);
 void launch_finalize_oz(int64_t m, int n, double* Q, int64_t ldq, const double* XT, uint32_t* colE,
                         unsigned char* Xs, Ctl* ctl, int level, cudaStream_t st, uint32_t* colHiOut = nullptr);
+// column maxima of |X| (high words) into colHi, and Y from FP64-sketch partials (P.slabs row slabs)
+void launch_oz_col_hi(int64_t m, int n, const double* X, int64_t ldx, uint32_t* colHi, const Ctl* ctl, int level,
+                      cudaStream_t st);
+void launch_sketch_oz_reduce(int n, int s, const uint32_t* colHi, const uint32_t* idx, const SketchOzPlan& P,
+                             const long long* part, double* Y, Ctl* ctl, int level, cudaStream_t st, int tf,
+                             int64_t m);
+
+// --- FP64 sketch from digit planes (ozaki_planes.cu) -----------------------------
+// The planes of D A (16 bytes per entry) go to `scratch` in row chunks of sketch_ozp_chunk_rows rows
+// (0: scratch too small); tabd holds 16 (m + 1) bytes; part must hold sketch_ozp_part_bytes.  False
+// (nothing enqueued) when not eligible: scratch not 16-byte aligned or too small, no tensor-map encoder.
+int64_t sketch_ozp_chunk_rows(int64_t m, int n, size_t scratch_bytes);
+size_t sketch_ozp_part_bytes(int64_t m, int n, int s, size_t scratch_bytes);
+bool sketch_ozp_eligible(int64_t m, int n, const void* scratch, size_t scratch_bytes);
+bool launch_sketch_ozp(int64_t m, int n, int s, const double* A, int64_t lda, const uint32_t* idx, const double* tab,
+                       uint4* tabd, uint64_t seed, uint32_t* colHi, long long* part, size_t part_bytes, double* Y,
+                       void* scratch, size_t scratch_bytes, Ctl* ctl, int level, cudaStream_t st, int tf);
 
 // --- regime estimates without learning (regime.cu) -------------------------------
 // out (DEVICE double[4]) = {kappa estimate, regime 0/1/2, q, 0} from the Gram E = Q^T Q of a CholQR run,

@@ -236,7 +236,7 @@ def regime_estimate(A: torch.Tensor, method="probe", seed: int = 0, out: torch.T
 
 def sketch(A: torch.Tensor, s: int, prec="fp64", seed: int = 0, variant: int = 0, stream=None) -> torch.Tensor:
     """Y = sqrt(m/s) P F D A in precision prec (variant 0 auto, 1 SIMT, 2 tensor-core dense rows,
-    4 four-step transform)."""
+    3 emulated FP64 sliced per work item, 4 four-step transform, 5 emulated FP64 from digit planes)."""
     m, n = A.shape
     Y = empty_colmajor(s, n, device=A.device)
     check(_lib.load().mrcqr_sketch_ex(m, n, A.data_ptr(), _ld(A, "A"), s, _prec(prec), seed, variant, Y.data_ptr(),

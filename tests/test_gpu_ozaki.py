@@ -240,12 +240,14 @@ def _sketch_exact(A, idx, d, s):
     return coef[:, None] * P, coef, F
 
 
+@pytest.mark.parametrize("variant", [3, 5])
 @pytest.mark.parametrize("m,n,s", [(3000, 40, 80), (4097, 33, 66), (700, 130, 260), (257, 5, 10)])
-def test_emulated_sketch_against_exact(env, m, n, s):
+def test_emulated_sketch_against_exact(env, m, n, s, variant):
+    # 3: digits sliced per work item; 5: digit planes of D A and the table's digits
     torch, M = env
     A = inputs.make_matrix(m, n, 1e12, seed=m + n)
-    Y = M.sketch(M.to_colmajor(A), s, "fp64", seed=3).cpu().numpy()
-    assert M.last_sketch_variant() == 3
+    Y = M.sketch(M.to_colmajor(A), s, "fp64", seed=3, variant=variant).cpu().numpy()
+    assert M.last_sketch_variant() == variant
     d, idx = O.rademacher(m, 3), O.sample_rows(m, s, 3)
     ref, coef, F = _sketch_exact(A, idx, d, s)
     # the table's cos values and numpy's may differ by an ulp each: 2^-52 sum |A|
@@ -274,8 +276,11 @@ def test_emulated_sketch_odd_ld_and_nonfinite(env):
     A = inputs.make_matrix(m, n, 1e4, seed=31)
     Y0 = M.sketch(M.to_colmajor(A), 2 * n, "fp64", seed=1).cpu().numpy()
     Y1 = M.sketch(M.to_colmajor(A, ld=m + 1), 2 * n, "fp64", seed=1).cpu().numpy()   # no alignment needed
-    assert M.last_sketch_variant() == 3
+    assert M.last_sketch_variant() == 5
     np.testing.assert_array_equal(Y0, Y1)
+    Y3 = M.sketch(M.to_colmajor(A, ld=m + 1), 2 * n, "fp64", seed=1, variant=3).cpu().numpy()
+    assert M.last_sketch_variant() == 3
+    np.testing.assert_array_equal(Y0, Y3)
     A[123, 7] = np.nan
     Q = M.empty_colmajor(m, n)
     R = M.empty_colmajor(n, n)
@@ -352,3 +357,48 @@ def test_emulated_trsm_full_height_and_ld(env):
     A2 = M.to_colmajor(A, ld=len(rows) + 3)
     W2 = M.trsm(A2, M.to_colmajor(R, ld=n + 1)).cpu().numpy()
     np.testing.assert_array_equal(W2, M.trsm(M.to_colmajor(A), M.to_colmajor(R)).cpu().numpy())
+
+
+# The sketch from digit planes forms the same digits as the per-item kernel and sums the same exact
+# integers, so Y is bit for bit the same, whatever the transform, the leading dimension or the shape.
+@pytest.mark.parametrize("m,n,s,ld,transform", [(1 << 16, 128, 256, 0, "dct"), (20000, 200, 400, 20001, "dct"),
+                                                 (5000, 512, 1024, 0, "dct"), (4099, 1, 2, 4100, "dct"),
+                                                 (33333, 70, 210, 0, "rfft"), (12288, 64, 128, 12289, "rfft_reim")])
+def test_planes_sketch_bit_exact(env, m, n, s, ld, transform):
+    torch, M = env
+    A = inputs.make_matrix(m, n, 1e14, seed=100 + n)
+    Ad = M.to_colmajor(A, ld=ld or None)
+    if transform == "dct":
+        Yp = M.sketch(Ad, s, "fp64", seed=21, variant=5).cpu().numpy()
+        assert M.last_sketch_variant() == 5
+        Yi = M.sketch(Ad, s, "fp64", seed=21, variant=3).cpu().numpy()
+        assert M.last_sketch_variant() == 3
+    else:
+        c = s // 2 if transform == "rfft_reim" else s
+        Yp = M.sketch_transform(Ad, c, transform, prec="fp64", seed=21, variant=5).cpu().numpy()
+        assert M.last_sketch_variant() == 5
+        Yi = M.sketch_transform(Ad, c, transform, prec="fp64", seed=21, variant=3).cpu().numpy()
+        assert M.last_sketch_variant() == 3
+    np.testing.assert_array_equal(Yp, Yi)
+
+
+# A factorization writes the planes into its Q buffer in row chunks of at most half of Q: 2 chunks at
+# m = 2^16 with ldq = m, 3 at m = 2^16 + 1, 1 with a Q buffer of more than twice the rows; below 2048 rows the
+# per-item kernel runs.  Q and R are bit for bit those of the per-item sketch.
+@pytest.mark.parametrize("m,n,ldq,planes", [(1 << 16, 64, 0, True), ((1 << 16) + 1, 48, 0, True),
+                                             (9000, 100, 20000, True), (1500, 16, 0, False)])
+def test_factor_planes_sketch_uses_q_buffer(env, m, n, ldq, planes):
+    torch, M = env
+    A = inputs.make_matrix(m, n, 1e14, seed=300 + n)
+    Ad = M.to_colmajor(A)
+    outs = []
+    for variant in (0, 3):
+        Q = M.empty_colmajor(m, n, ld=ldq or None)
+        R = M.empty_colmajor(n, n)
+        M.factor_ex(Ad, Q, R, prec="fp64", seed=4, escalate=False, sketch_variant=variant)
+        st = M.last_status()
+        assert st["status"] == "OK" and st["ortho_fro"] <= 1e-13, st
+        assert M.last_sketch_variant() == (5 if (variant == 0 and planes) else 3)
+        outs.append((Q[:m].cpu().numpy(), R.cpu().numpy()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])

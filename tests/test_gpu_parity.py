@@ -127,11 +127,11 @@ def test_sketch_variants_agree_and_fall_back(M):
     y_odd = _np(M.sketch(Aodd, 2 * n, "fp16", seed=5))
     assert M.last_sketch_variant() == 2
     np.testing.assert_array_equal(y_odd, y_tc)
-    # FP64: emulated FP64 on the tensor cores unless the SIMT variant is asked for
+    # FP64: emulated FP64 on the tensor cores (from digit planes) unless the SIMT variant is asked for
     _ = M.sketch(Ad, 2 * n, "fp64", seed=5, variant=2)
-    assert M.last_sketch_variant() == 3
+    assert M.last_sketch_variant() == 5
     _ = M.sketch(Ad, 2 * n, "fp64", seed=5)
-    assert M.last_sketch_variant() == 3
+    assert M.last_sketch_variant() == 5
     _ = M.sketch(Ad, 2 * n, "fp64", seed=5, variant=1)
     assert M.last_sketch_variant() == 1
 
