@@ -201,12 +201,12 @@ __device__ __forceinline__ bool fin_oz_block(const FinOzArgs& a, FinOzCta& S, Oz
 
 #define MRCQR_FIN_OZ_CTA(S, P)                         \
   extern __shared__ unsigned char smem_raw[];          \
-  __shared__ __align__(8) uint64_t mma_bar;            \
+  __shared__ __align__(8) uint64_t mma_bar[2];         \
   __shared__ uint32_t tmem_slot;                       \
   __shared__ uint32_t rowE_s[kM];                      \
   __shared__ uint32_t redE_s[4][kM];                   \
   __shared__ uint32_t cmax_s[512];                     \
-  OzPipe P = oz_begin(&tmem_slot, &mma_bar);           \
+  OzPipe P = oz_begin(&tmem_slot, mma_bar);            \
   FinOzCta S{oz_smem(smem_raw), rowE_s, redE_s, cmax_s};
 
 __global__ void __launch_bounds__(kOzThreads, 1)
@@ -303,10 +303,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = oz_smem(smem_raw);
-  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t mma_bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ uint32_t colE[kM + kN];
-  OzPipe P = oz_begin(&tmem_slot, &mma_bar);
+  OzPipe P = oz_begin(&tmem_slot, mma_bar);
   bool abort = false;
   const int nitems = SP.ntiles * SP.slabs;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
@@ -361,7 +361,7 @@ __global__ void k_syrk_oz_reduce(int n, const uint32_t* __restrict__ colHi, Syrk
 __device__ __forceinline__ bool sketch_oz_item(int64_t m, int n, int s, const double* __restrict__ A, int64_t lda,
                                                const uint32_t* __restrict__ colHi, const uint32_t* __restrict__ idx,
                                                const double* __restrict__ tab, uint2 key, const SketchOzPlan& SP,
-                                               long long* __restrict__ part, int tf, OzPipe P, uint32_t& commits,
+                                               long long* __restrict__ part, int tf, OzPipe& P,
                                                unsigned char* smem, uint32_t* colE, uint32_t* sgn, int item) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint64_t four_m = 4ull * (uint64_t)m;
@@ -436,7 +436,6 @@ __device__ __forceinline__ bool sketch_oz_item(int64_t m, int n, int s, const do
   };
   if (!oz_run(P, smem, nchunks, produce, hi, lo)) return false;
   oz_store_partial(part + (size_t)item * kPartElems, P.q, P.g, lane, hi, lo);
-  commits = P.commits;
   return true;
 }
 
@@ -447,15 +446,15 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = oz_smem(smem_raw);
-  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t mma_bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ uint32_t colE[kM];
   __shared__ uint32_t sgn[2];   // Rademacher signs of a chunk's 32 rows (bit i: row r0 + i), by chunk parity
-  OzPipe P = oz_begin(&tmem_slot, &mma_bar);
+  OzPipe P = oz_begin(&tmem_slot, mma_bar);
   bool abort = false;
   const int nitems = SP.mblocks * SP.ntiles * SP.slabs;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x)
-    if (!sketch_oz_item(m, n, s, A, lda, colHi, idx, tab, key, SP, part, tf, P, P.commits, smem, colE, sgn, item)) {
+    if (!sketch_oz_item(m, n, s, A, lda, colHi, idx, tab, key, SP, part, tf, P, smem, colE, sgn, item)) {
       abort = true;
       break;
     }
@@ -921,11 +920,11 @@ __global__ void __launch_bounds__(256) kg_oz_colhi(Group g, int level) {
 __global__ void __launch_bounds__(kOzThreads, 1) kg_oz_sketch(Group g, int level) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = oz_smem(smem_raw);
-  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t mma_bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ uint32_t colE[kM];
   __shared__ uint32_t sgn[2];
-  OzPipe pipe = oz_begin(&tmem_slot, &mma_bar);
+  OzPipe pipe = oz_begin(&tmem_slot, mma_bar);
   bool abort = false;
   Ctl* actl = nullptr;
   for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
@@ -933,7 +932,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) kg_oz_sketch(Group g, int level
     const Prob& P = g.probs[w.x];
     if (!oz_live(P, level)) continue;
     if (!sketch_oz_item(P.m, P.n, P.s, P.A, P.lda, P.oz_colhi, P.idx, P.tab, P.key, P.oz_kp, P.oz_part, P.tf, pipe,
-                        pipe.commits, smem, colE, sgn, w.y)) {
+                        smem, colE, sgn, w.y)) {
       abort = true;
       actl = P.ctl;
       break;
@@ -1010,10 +1009,10 @@ __global__ void __launch_bounds__(kTThreads, 2) kg_oz_trsm(Group g, int level) {
 __global__ void __launch_bounds__(kOzThreads, 1) kg_oz_syrk(Group g, int level) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = oz_smem(smem_raw);
-  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t mma_bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ uint32_t colE[kM + kN];
-  OzPipe pipe = oz_begin(&tmem_slot, &mma_bar);
+  OzPipe pipe = oz_begin(&tmem_slot, mma_bar);
   bool abort = false;
   Ctl* actl = nullptr;
   for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
@@ -1203,6 +1202,7 @@ void launch_syrk_oz(int64_t m, int n, const double* W, int64_t ldw, const SyrkOz
   const int64_t nn = (int64_t)n * n;
   { ::mrcqr::note_launch(); k_syrk_oz_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, colHi, P, part, out, ctl, level); }
 }
+
 
 SketchOzPlan sketch_oz_plan(int64_t m, int n, int s) {
   SketchOzPlan P{};

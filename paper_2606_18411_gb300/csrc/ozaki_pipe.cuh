@@ -122,30 +122,46 @@ __device__ __forceinline__ void oz_store_cols(const double (&v)[NC / 32][2], con
 }
 
 struct OzPipe {
-  uint64_t* bar;
+  uint64_t* bar;      // [2]: MMA batches of even and odd chunks commit to bar[0] and bar[1]
   uint32_t tmem, idesc;
-  uint32_t commits;   // MMA batches committed so far (the same count in every thread)
+  uint32_t mph;       // bit b: parity of the next completion of bar[b] (the same in every thread)
+  uint32_t mopen;     // issuing thread: bit b = a batch committed to bar[b] and not yet waited for
   int tid, q, g;
 };
 
+// Waits (bounded) for the MMA batch of chunk ch (committed to bar[ch & 1]).
+__device__ __forceinline__ bool oz_wait_mma(OzPipe& P, int ch) {
+  const uint32_t b = (uint32_t)ch & 1u;
+  const bool ok = tc::mbar_wait(&P.bar[b], (P.mph >> b) & 1u);
+  if (ok) {
+    P.mph ^= 1u << b;
+    P.mopen &= ~(1u << b);
+  }
+  return ok;
+}
+
 // Runs nchunks chunks through the two stages: produce(ch, a, b) writes the
 // digit panels of chunk ch (A at a, B at b, each digit's panel contiguous
-// after the previous one).  The MMAs of chunk
-// ch overlap with the production of chunk ch + 1.  Level sums are added into
-// hi / lo after every kGroupChunks chunks and after the last.  False when a
-// wait timed out (every thread returns false together).
+// after the previous one).  Two MMA batches are in flight: the batch of
+// chunk ch is issued while that of ch - 1 still runs, and the production of
+// chunk ch + 1 (into the stage chunk ch - 1 read) waits only for ch - 1.  At
+// a group boundary (every kGroupChunks chunks, the exactness limit of the FP32
+// level sums) the pipeline drains and the level sums are added into hi / lo
+// before the next group's first batch overwrites them, and after the last
+// chunk.  False when a wait timed out (every thread returns false together).
 template <class Produce>
 __device__ __forceinline__ bool oz_run(OzPipe& P, unsigned char* smem, int nchunks, Produce&& produce, long long* hi,
                                        long long* lo) {
+  bool ok = true;
   for (int ch = 0; ch < nchunks; ++ch) {
     unsigned char* a = smem + (ch & 1) * kStage;
     unsigned char* b = a + oz::kSlices * kAPanel;
     produce(ch, a, b);   // this stage was last read by the MMAs of chunk ch - 2, already complete
     tc::fence_proxy_async();
-    bool ok = true;
-    if (ch > 0) ok = tc::mbar_wait(P.bar, (P.commits - 1) & 1u);
+    const bool gstart = ch % kGroupChunks == 0;
+    if (gstart && ch > 0) ok = oz_wait_mma(P, ch - 1) && ok;
     if (__syncthreads_or(!ok)) return false;
-    if (ch > 0 && (ch - 1) % kGroupChunks == kGroupChunks - 1) {   // group closed at ch - 1
+    if (gstart && ch > 0) {   // group closed at ch - 1
       tc::fence_after();
       oz_readout(P.tmem, P.q, P.g, hi, lo);
       tc::fence_before();
@@ -153,13 +169,14 @@ __device__ __forceinline__ bool oz_run(OzPipe& P, unsigned char* smem, int nchun
     }
     if (P.tid == 0) {
       tc::fence_after();
-      oz_issue_chunk(P.tmem, tc::smem_u32(a), tc::smem_u32(b), ch % kGroupChunks == 0);
-      tc::mma_commit(P.bar);
+      oz_issue_chunk(P.tmem, tc::smem_u32(a), tc::smem_u32(b), gstart);
+      tc::mma_commit(&P.bar[ch & 1]);
+      P.mopen |= 1u << (ch & 1);
     }
-    ++P.commits;
+    if (!gstart) ok = oz_wait_mma(P, ch - 1);   // frees the stage of chunk ch + 1
   }
   if (nchunks > 0) {
-    const bool ok = tc::mbar_wait(P.bar, (P.commits - 1) & 1u);
+    ok = oz_wait_mma(P, nchunks - 1) && ok;
     if (__syncthreads_or(!ok)) return false;
     tc::fence_after();
     oz_readout(P.tmem, P.q, P.g, hi, lo);
@@ -170,12 +187,13 @@ __device__ __forceinline__ bool oz_run(OzPipe& P, unsigned char* smem, int nchun
 }
 
 // CTA prologue / epilogue shared by the kernels: TMEM (512 columns) and the
-// MMA barrier.
+// two MMA barriers (bar: a __shared__ uint64_t[2]).
 __device__ __forceinline__ OzPipe oz_begin(uint32_t* tmem_slot, uint64_t* bar) {
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
     tc::mbar_fence_init();
   }
   tc::fence_before();
@@ -185,7 +203,8 @@ __device__ __forceinline__ OzPipe oz_begin(uint32_t* tmem_slot, uint64_t* bar) {
   P.bar = bar;
   P.tmem = *tmem_slot;
   P.idesc = tc::idesc(tc::F16, kM, kN);
-  P.commits = 0;
+  P.mph = 0;
+  P.mopen = 0;
   P.tid = tid;
   P.q = warp & 3;
   P.g = warp >> 2;
@@ -193,7 +212,12 @@ __device__ __forceinline__ OzPipe oz_begin(uint32_t* tmem_slot, uint64_t* bar) {
 }
 
 __device__ __forceinline__ void oz_end(const OzPipe& P, bool abort, Ctl* ctl) {
-  if (abort && P.tid == 0) raise_level_status(ctl, ST_TIMEOUT);
+  if (abort && P.tid == 0) {
+    raise_level_status(ctl, ST_TIMEOUT);
+    // MMA batches may still run: wait for them (bounded) before the TMEM is freed
+    for (uint32_t b = 0; b < 2; ++b)
+      if ((P.mopen >> b) & 1u) tc::mbar_wait(&P.bar[b], (P.mph >> b) & 1u, 1u << 20);
+  }
   tc::fence_before();
   __syncthreads();
   if ((P.tid >> 5) == 0) tc::tmem_dealloc(P.tmem, 512);

@@ -165,22 +165,20 @@ __device__ __forceinline__ bool sketch_ozp_item(const CUtensorMap* tmap, int64_t
       unsigned char* a = smem + st * kStage;
       S.pend |= 1u << st;
       tc::mbar_expect_tx(&S.tma_bar[st], oz::kSlices * kAPanel);
-      asm volatile(
-          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-          "[%5];" ::"r"(tc::smem_u32(a)),
-          "l"(reinterpret_cast<uint64_t>(tmap)), "r"((int)(r_begin + (int64_t)ch * kK)), "r"(c0), "r"(0),
-          "r"(tc::smem_u32(&S.tma_bar[st]))
-          : "memory");
+      tc::tma_load_3d(a, tmap, (int)(r_begin + (int64_t)ch * kK), c0, 0, &S.tma_bar[st]);
     };
-    // the stage of chunk 0 was last read by MMAs that completed before this item
+    // Two MMA batches in flight (oz_run's schedule): the batch of chunk ch is issued while that of
+    // ch - 1 runs; the copy of chunk ch + 1 and the production of its transform digits go into the
+    // stage chunk ch - 1 read, once that batch is done.  The stage of chunk 0 was last read by
+    // batches that completed before this item.
     if (tid == 0) issue_tma(0);
     gather(r_begin);
+    bool ok = true;
     for (int ch = 0; ch < nchunks; ++ch) {
       const uint32_t st = (S.gch + (uint32_t)ch) & 1u;
       unsigned char* a = smem + st * kStage;
       unsigned char* b = a + oz::kSlices * kAPanel;
-      // transform digits of chunk ch: rows 4 fg + 2 t2, + 1 of sample fi (this stage's B panels were
-      // last read by the MMAs of chunk ch - 2, complete)
+      // transform digits of chunk ch: rows 4 fg + 2 t2, + 1 of sample fi
 #pragma unroll
       for (int t2 = 0; t2 < 2; ++t2) {
         const uint4 x0 = u[2 * t2], x1 = u[2 * t2 + 1];
@@ -193,31 +191,32 @@ __device__ __forceinline__ bool sketch_ozp_item(const CUtensorMap* tmap, int64_t
       }
       if (ch + 1 < nchunks) gather(r_begin + (int64_t)(ch + 1) * kK);
       tc::fence_proxy_async();
-      bool ok = true;
-      if (ch > 0) ok = tc::mbar_wait(P.bar, (P.commits - 1) & 1u);
+      const bool gstart = ch % kGroupChunks == 0;
+      if (gstart && ch > 0) ok = oz_wait_mma(P, (int)(S.gch + ch - 1)) && ok;
       // the flag is read after the barrier, so every thread sees the issuing thread's last write
       if (__syncthreads_or(!ok) || *S.abort_flag) return false;
-      if (ch > 0 && (ch - 1) % kGroupChunks == kGroupChunks - 1) {   // group closed at ch - 1
+      if (gstart && ch > 0) {   // group closed at ch - 1: its level sums before the next group overwrites them
         tc::fence_after();
         oz_readout(P.tmem, P.q, P.g, hi, lo);
         tc::fence_before();
         __syncthreads();
       }
       if (tid == 0) {
-        if (ch + 1 < nchunks) issue_tma(ch + 1);   // its stage was last read by the MMAs of chunk ch - 1
         const bool tok = tc::mbar_wait(&S.tma_bar[st], (S.tma_phase >> st) & 1u);
         if (tok) {
           S.tma_phase ^= 1u << st;
           S.pend &= ~(1u << st);
         }
         tc::fence_after();
-        if (tok) oz_issue_chunk(P.tmem, tc::smem_u32(a), tc::smem_u32(b), ch % kGroupChunks == 0);
+        if (tok) oz_issue_chunk(P.tmem, tc::smem_u32(a), tc::smem_u32(b), gstart);
         else *S.abort_flag = 1;
-        tc::mma_commit(P.bar);   // with no MMA issued it still arrives once the earlier ones are done
+        tc::mma_commit(&P.bar[(S.gch + ch) & 1u]);   // with no MMA issued it arrives once the earlier ones are done
+        P.mopen |= 1u << ((S.gch + ch) & 1u);
       }
-      ++P.commits;
+      if (!gstart) ok = oz_wait_mma(P, (int)(S.gch + ch - 1));   // frees the stage of chunk ch + 1
+      if (tid == 0 && ok && ch + 1 < nchunks) issue_tma(ch + 1);
     }
-    const bool ok = tc::mbar_wait(P.bar, (P.commits - 1) & 1u);
+    ok = oz_wait_mma(P, (int)(S.gch + nchunks - 1)) && ok;
     if (__syncthreads_or(!ok) || *S.abort_flag) return false;
     tc::fence_after();
     oz_readout(P.tmem, P.q, P.g, hi, lo);
@@ -236,7 +235,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   if (level_inactive(ctl, level) || ctl->lvl_status != 0) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = oz_smem(smem_raw);
-  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t mma_bar[2];
   __shared__ __align__(8) uint64_t tma_bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
@@ -245,7 +244,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     tc::mbar_init(&tma_bar[1], 1);
     abort_flag = 0;
   }
-  OzPipe P = oz_begin(&tmem_slot, &mma_bar);   // initialises the MMA barrier and fences the inits
+  OzPipe P = oz_begin(&tmem_slot, mma_bar);   // initialises the MMA barriers and fences the inits
   OzpState S{tma_bar, &abort_flag, 0u, 0u, 0u};
   bool abort = false;
   const int nitems = SP.mblocks * SP.ntiles * SP.slabs;
