@@ -122,7 +122,7 @@ __device__ __forceinline__ void oz_store_cols(const double (&v)[NC / 32][2], con
 }
 
 struct OzPipe {
-  uint64_t* bar;      // [2]: MMA batches of even and odd chunks commit to bar[0] and bar[1]
+  uint64_t* bar;      // [2]: oz_run commits every batch to bar[0]; two batches in flight alternate bar[0] / bar[1]
   uint32_t tmem, idesc;
   uint32_t mph;       // bit b: parity of the next completion of bar[b] (the same in every thread)
   uint32_t mopen;     // issuing thread: bit b = a batch committed to bar[b] and not yet waited for
@@ -142,26 +142,25 @@ __device__ __forceinline__ bool oz_wait_mma(OzPipe& P, int ch) {
 
 // Runs nchunks chunks through the two stages: produce(ch, a, b) writes the
 // digit panels of chunk ch (A at a, B at b, each digit's panel contiguous
-// after the previous one).  Two MMA batches are in flight: the batch of
-// chunk ch is issued while that of ch - 1 still runs, and the production of
-// chunk ch + 1 (into the stage chunk ch - 1 read) waits only for ch - 1.  At
-// a group boundary (every kGroupChunks chunks, the exactness limit of the FP32
-// level sums) the pipeline drains and the level sums are added into hi / lo
-// before the next group's first batch overwrites them, and after the last
-// chunk.  False when a wait timed out (every thread returns false together).
+// after the previous one) while the MMAs of chunk ch - 1 run; the batch of
+// chunk ch is issued once that of ch - 1 is done (all batches commit to
+// bar[0]).  Level sums are added into hi / lo after every kGroupChunks chunks
+// (the exactness limit of the FP32 level sums) and after the last.  Issuing
+// the next batch before the previous one completes (two barriers) was measured
+// about 1% slower in these kernels, whose production overlaps the MMAs anyway.
+// False when a wait timed out (every thread returns false together).
 template <class Produce>
 __device__ __forceinline__ bool oz_run(OzPipe& P, unsigned char* smem, int nchunks, Produce&& produce, long long* hi,
                                        long long* lo) {
-  bool ok = true;
   for (int ch = 0; ch < nchunks; ++ch) {
     unsigned char* a = smem + (ch & 1) * kStage;
     unsigned char* b = a + oz::kSlices * kAPanel;
     produce(ch, a, b);   // this stage was last read by the MMAs of chunk ch - 2, already complete
     tc::fence_proxy_async();
-    const bool gstart = ch % kGroupChunks == 0;
-    if (gstart && ch > 0) ok = oz_wait_mma(P, ch - 1) && ok;
+    bool ok = true;
+    if (ch > 0) ok = oz_wait_mma(P, 0);
     if (__syncthreads_or(!ok)) return false;
-    if (gstart && ch > 0) {   // group closed at ch - 1
+    if (ch > 0 && (ch - 1) % kGroupChunks == kGroupChunks - 1) {   // group closed at ch - 1
       tc::fence_after();
       oz_readout(P.tmem, P.q, P.g, hi, lo);
       tc::fence_before();
@@ -169,14 +168,13 @@ __device__ __forceinline__ bool oz_run(OzPipe& P, unsigned char* smem, int nchun
     }
     if (P.tid == 0) {
       tc::fence_after();
-      oz_issue_chunk(P.tmem, tc::smem_u32(a), tc::smem_u32(b), gstart);
-      tc::mma_commit(&P.bar[ch & 1]);
-      P.mopen |= 1u << (ch & 1);
+      oz_issue_chunk(P.tmem, tc::smem_u32(a), tc::smem_u32(b), ch % kGroupChunks == 0);
+      tc::mma_commit(&P.bar[0]);
+      P.mopen |= 1u;
     }
-    if (!gstart) ok = oz_wait_mma(P, ch - 1);   // frees the stage of chunk ch + 1
   }
   if (nchunks > 0) {
-    ok = oz_wait_mma(P, nchunks - 1) && ok;
+    const bool ok = oz_wait_mma(P, 0);
     if (__syncthreads_or(!ok)) return false;
     tc::fence_after();
     oz_readout(P.tmem, P.q, P.g, hi, lo);
