@@ -239,3 +239,36 @@ def test_batched_mixes_tma_and_plain_copy_sketches(env, rows_per_chunk):
         Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
         assert O.orthogonality_error(Qh)[0] <= 1e-13
         assert O.residual_error(A, Qh, Rh)[0] <= 1e-13
+
+
+def test_batched_512_problem_distribution_against_oracle(env):
+    # the batched workload's own distribution: 512 problems, m uniform in [2^14, 2^18], n in
+    # {16, 32, 64, 128}, geometric spectra with kappa log-uniform in [1, 1e12], precision by rule, one
+    # grouped plan replayed as a CUDA graph; every problem must report OK with diag(R) > 0, and 16 of
+    # them (the largest and smallest m, the rest drawn) pass the oracle's double-double orthogonality
+    # and residual checks
+    torch, M = env
+    rng = np.random.default_rng(4000)
+    cnt = 512
+    ms = rng.integers(1 << 14, (1 << 18) + 1, cnt)
+    ns = rng.choice([16, 32, 64, 128], cnt)
+    kap = 10.0 ** rng.uniform(0.0, 12.0, cnt)
+    As = [inputs.make_matrix_torch(int(mm), int(nn), float(k), seed=7000 + i, device="cuda")
+          for i, (mm, nn, k) in enumerate(zip(ms, ns, kap))]
+    Qs = [M.empty_colmajor(int(mm), int(nn)) for mm, nn in zip(ms, ns)]
+    Rs = [M.empty_colmajor(int(nn), int(nn)) for nn in ns]
+    status = torch.full((cnt,), -1, dtype=torch.int32, device="cuda")
+    precs = [O.precision_rule(float(k)) for k in kap]
+    plan = M.BatchedPlan(As, Qs, Rs, precs, list(range(cnt)), status, use_graph=True)
+    plan.execute()
+    torch.cuda.synchronize()
+    plan.close()
+    assert status.cpu().tolist() == [0] * cnt
+    for R in Rs:
+        assert bool(torch.all(torch.diagonal(R) > 0))
+    pick = {int(np.argmax(ms)), int(np.argmin(ms))}
+    pick |= set(int(i) for i in rng.choice(cnt, 14, replace=False))
+    for i in sorted(pick):
+        A, Q, R = As[i].cpu().numpy(), Qs[i].cpu().numpy(), Rs[i].cpu().numpy()
+        assert O.orthogonality_error(Q)[0] <= 1e-13, (i, ms[i], ns[i], kap[i])
+        assert O.residual_error(A, Q, R)[0] <= 1e-13, (i, ms[i], ns[i], kap[i])
