@@ -176,8 +176,29 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0)
     for (; issued < F::STAGES && issued < total; ++issued) issue_tma(issued);
 
+  // step-2 sample order: the samples sorted by the U row they read (a counting sort over the 65 real
+  // rows), so a warp's samples read one or two neighbouring rows (broadcasts and distinct banks, where
+  // random rows collide on a bank about 3.5-fold); each sample is still summed by one thread in the
+  // same order, so Y does not change
+  __shared__ uint16_t sorder[kMaxS];
+  __shared__ int sbucket[66];
+  if (tid < 66) sbucket[tid] = 0;
+  __syncthreads();
+  auto row_of = [&](int e) {
+    const int r = (int)(idx[e] & 127u);
+    return r <= 64 ? r : 128 - r;
+  };
+  for (int e = tid; e < s; e += kThreads) atomicAdd(&sbucket[row_of(e) + 1], 1);
+  __syncthreads();
+  if (tid == 0)
+    for (int b = 1; b < 66; ++b) sbucket[b] += sbucket[b - 1];
+  __syncthreads();
+  for (int e = tid; e < s; e += kThreads) sorder[atomicAdd(&sbucket[row_of(e)], 1)] = (uint16_t)e;
+  __syncthreads();
+
   // step-2 identity: G thread groups share the samples when s is small (each group takes C / G of
-  // the tile's columns, so every thread works); thread t: group t / SPT, sample slots t % SPT + SPT i
+  // the tile's columns, so every thread works); thread t: group t / SPT, sample slots t % SPT + SPT i,
+  // slot v taking sample sorder[v]
   int G = 1;
   while (G < C && s * (G * 2) <= kThreads) G *= 2;
   const int SPT = kThreads / G;
@@ -190,14 +211,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t sk[kKpt], sk2[kKpt], sk32[kKpt], ph[kKpt];   // k, 2k, 32k mod 4m, phase k (2 j1_0 + 1) mod 4m
 #pragma unroll
   for (int i = 0; i < kKpt; ++i) {
-    const int si = slot + SPT * i;
+    const int sv = slot + SPT * i;
     srow_r[i] = srow_i[i] = kRows;
     ssig[i] = 0.f;
     rot_c[i] = 1.f;
     rot_s[i] = 0.f;
     sk[i] = sk2[i] = sk32[i] = ph[i] = 0u;
-    if (si < s) {
-      const uint32_t k = idx[si];
+    if (sv < s) {
+      const uint32_t k = idx[sorder[sv]];
       const int r = (int)(k & 127u);
       const int rp = r <= 64 ? r : 128 - r;
       srow_r[i] = rp;
@@ -265,10 +286,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       double* out = Ypart + (size_t)ch * (size_t)s * (size_t)n;
 #pragma unroll
       for (int i = 0; i < kKpt; ++i) {
-        const int si = slot + SPT * i;
+        const int sv = slot + SPT * i;
+        const int si = sv < s ? (int)sorder[sv] : 0;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          if (si < s && c >= cg_lo && c < cg_hi && c0 + c < n) out[(size_t)(c0 + c) * s + si] = (double)acc[i][c];
+          if (sv < s && c >= cg_lo && c < cg_hi && c0 + c < n) out[(size_t)(c0 + c) * s + si] = (double)acc[i][c];
           acc[i][c] = 0.f;
         }
       }
