@@ -304,15 +304,16 @@ int sketch_max_chunks(int64_t m, int n, int s) {
 
 // The faster tensor-core variant by measurement (dense rows V1 against the
 // four-step V2) for precision prec at n columns (s = 2n); true picks the
-// four-step.  Measured at m = 2^20 on GB300 (ms, V1 / V2): FP16 and BF16
-// n = 64: 0.51 / 0.74, 128: 0.83 / 1.36, 256: 2.78 / 2.81, 512: 19.6 / 8.1;
-// FP32 n = 64: 0.84 / 1.03, 128: 1.79 / 2.21, 256: 6.67 / 4.53,
-// 512: 49.1 / 11.8.  The dense-row variant's work grows as s n, the
-// four-step's as n; the switch points sit between the measured sizes.
+// four-step.  Measured at m = 2^20 on GB300 (ms, V1 / V2, CUDA events over
+// five calls): FP16 n = 128: 0.92 / 1.45, 192: 3.27 / 1.83, 256: 2.97 /
+// 2.50, 320: 8.16 / 3.81, 512: 19.6 / 6.78 (BF16 within 1% of FP16); FP32
+// n = 128: 1.93 / 2.16, 192: 7.80 / 3.14, 256: 7.12 / 4.24, 320: 20.1 /
+// 6.10.  The dense-row variant's work grows as s n, the four-step's as n; the
+// switch point sits between the measured sizes.
 static bool four_step_preferred(int prec, int64_t m, int n) {
   (void)m;
-  if (prec == P_FP32) return n >= 192;
-  return n >= 320;
+  (void)prec;
+  return n >= 160;
 }
 
 int launch_sketch(int prec, int variant, const double* A, int64_t lda, int64_t m, int n, int s,
