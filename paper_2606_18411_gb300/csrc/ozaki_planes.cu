@@ -167,7 +167,7 @@ __device__ __forceinline__ bool sketch_ozp_item(const CUtensorMap* tmap, int64_t
       tc::mbar_expect_tx(&S.tma_bar[st], oz::kSlices * kAPanel);
       tc::tma_load_3d(a, tmap, (int)(r_begin + (int64_t)ch * kK), c0, 0, &S.tma_bar[st]);
     };
-    // Two MMA batches in flight (oz_run's schedule): the batch of chunk ch is issued while that of
+    // Two MMA batches in flight (bar[0] / bar[1] by chunk parity): the batch of chunk ch is issued while that of
     // ch - 1 runs; the copy of chunk ch + 1 and the production of its transform digits go into the
     // stage chunk ch - 1 read, once that batch is done.  The stage of chunk 0 was last read by
     // batches that completed before this item.
