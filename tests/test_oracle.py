@@ -233,6 +233,45 @@ def test_emulated_sketch_within_precision_tolerance(prec, tol):
     assert err > O.UNIT_ROUNDOFF[prec] / 100     # really rounded
 
 
+# Exact special cases of the precision-p sketch models: where every rounding they model is exact, they
+# must give the FP64 sketch bit for bit.  Bins 0 and m/2 of the real FFT have entries 1 and (-1)^j; DCT
+# row 0 is the constant 1/sqrt(m); small-integer entries survive fl_p after the column scale 2^e; with
+# m = 128 and c = 2 bins the scale sqrt(c/m) is 1/8, with m = 64 and s = 1 the DCT scale sqrt(m/s) is 8,
+# so every product and sum is exact in FP64.  A dropped sign, scale or column exponent fails here.
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+def test_emulated_sketches_exact_where_rounding_is_exact(prec):
+    rng = np.random.default_rng(11)
+    A = rng.integers(-8, 9, size=(128, 6)).astype(np.float64)
+    A[:, 2] *= 2.0 ** 40   # column scales far from 1
+    A[:, 3] *= 2.0 ** -30
+    d = O.rademacher(128, 7)
+    bins = np.array([0, 64])
+    np.testing.assert_array_equal(O.rfft_sketch_emulated(A, bins, d, prec), O.rfft_sketch(A, bins, d))
+    B = A[:64]
+    d2 = O.rademacher(64, 3)
+    np.testing.assert_array_equal(O.sketch_emulated(B, np.array([0]), d2, prec), O.sketch(B, np.array([0]), d2))
+    # the same call without the signs D differs: the models apply them
+    assert not np.array_equal(O.rfft_sketch_emulated(A, bins, d, prec), O.rfft_sketch(A, bins, np.ones(128)))
+
+
+# With entries that do round, the real-FFT model on bins {0, m/2} equals the FP64 sketch of D A whose
+# scaled entries were rounded once to p (round_significand, pinned above against numpy and torch
+# casts): the model rounds D A 2^e, not A, and undoes the scale exactly.
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+def test_emulated_rfft_sketch_rounds_the_scaled_signed_entries(prec):
+    rng = np.random.default_rng(12)
+    m, n = 128, 5
+    A = rng.integers(-8, 9, size=(m, n)).astype(np.float64) + rng.integers(-2 ** 19, 2 ** 19, size=(m, n)) * 2.0 ** -20
+    d = O.rademacher(m, 9)
+    bins = np.array([0, m // 2])
+    e = O.column_scale_exponents(A)
+    bits = {"fp16": 11, "bf16": 8, "fp32": 24}[prec]
+    Xr = np.ldexp(O.round_significand(d[:, None] * np.ldexp(A, e[None, :]), bits), -e[None, :])
+    Y = O.rfft_sketch_emulated(A, bins, d, prec)
+    np.testing.assert_array_equal(Y, O.rfft_sketch(d[:, None] * Xr, bins, d))
+    assert not np.array_equal(Y, O.rfft_sketch(A, bins, d)) or prec == "fp32"   # the rounding is visible
+
+
 # --- SketchQR, Cholesky, substitution (Algorithm 1, Algorithm 2 steps 5-9) ----
 
 @pytest.mark.parametrize("c,n", [(8, 8), (64, 32), (300, 50)])
