@@ -157,3 +157,29 @@ def test_adamw_matches_torch_adamw_over_steps():
         opt.step()
         th, m, v = S.adamw_step(th, g, m, v, k, lr=lr, beta1=b1, beta2=b2, eps=eps, wd=wd)
     np.testing.assert_allclose(th, p.detach().numpy(), rtol=0, atol=1e-14)
+
+
+def test_mlp_loss_and_gradient_match_torch_autograd():
+    # the same definitions in a library: logits of Linear(16, 64) -> ReLU -> Linear(64, 64) -> ReLU ->
+    # Linear(64, 3) (weights stored out x in, bias after), the class-weighted cross-entropy summed over the
+    # batch and divided by the batch size, and its gradient by torch's autograd, all in float64; a
+    # transposed weight, a missing bias or ReLU, or a weight-normalised mean fails here
+    torch = pytest.importorskip("torch")
+    import torch.nn.functional as F
+    rng = np.random.default_rng(5)
+    theta = rng.standard_normal(S.NUM_PARAMS) * 0.3
+    X = rng.standard_normal((37, 16))
+    y = rng.integers(0, 3, 37)
+    w = np.array([1.0, 1.7, 3.0])
+    loss, g = S.loss_and_grad(theta, X, y, w)
+    z_or, _ = S.forward(theta, X)
+    params = [torch.tensor(p, dtype=torch.float64, requires_grad=True) for p in S.unpack(theta.copy())]
+    W1, b1, W2, b2, W3, b3 = params
+    xt = torch.from_numpy(X)
+    z = F.linear(F.relu(F.linear(F.relu(F.linear(xt, W1, b1)), W2, b2)), W3, b3)
+    lt = F.cross_entropy(z, torch.from_numpy(y), weight=torch.from_numpy(w), reduction="sum") / X.shape[0]
+    lt.backward()
+    gt = np.concatenate([p.grad.numpy().ravel() for p in params])
+    np.testing.assert_allclose(z_or, z.detach().numpy(), rtol=1e-12, atol=1e-12)
+    assert abs(loss - lt.item()) <= 1e-12 * abs(lt.item())
+    np.testing.assert_allclose(g, gt, rtol=1e-10, atol=1e-13)
